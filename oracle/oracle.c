@@ -1,0 +1,801 @@
+/*
+ * Plain FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Written for clarity, not speed: no blocking, no fusion, no reordering
+ * beyond what each cited definition or algorithm states.  Single thread.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* small vector helpers                                                */
+/* ------------------------------------------------------------------ */
+
+static double dot(int n, const double* x, const double* y) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += x[i] * y[i];
+  return s;
+}
+
+static int all_finite(int n, const double* x) {
+  for (int i = 0; i < n; ++i)
+    if (!isfinite(x[i])) return 0;
+  return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Chebyshev coefficients: Section 2.2 and Eq. thetamod, Eq. rhocheb   */
+/* ------------------------------------------------------------------ */
+
+/* theta = (beta+alpha)/2, delta = (beta-alpha)/2 (Section 2.2);
+ * theta_bar = theta (1 + xi) (Eq. thetamod); delta is kept and
+ * sigma_bar = theta_bar / delta, i.e. the polynomial is the Chebyshev
+ * polynomial of the shifted interval [theta_bar - delta, theta_bar + delta].
+ * This is the reading of the xi-modification that reproduces Table 1.
+ * rho_0 = 1/sigma_bar, rho_j = 1/(2 sigma_bar - rho_{j-1}) (Eq. rhocheb). */
+int oracle_cheb_coeffs(double alpha, double beta, double xi, int k, double* theta_bar,
+                       double* delta, double* sigma_bar, double* rho) {
+  if (!(alpha > 0.0) || !(beta > alpha) || k < 0 || xi < 0.0) return -1;
+  double theta = 0.5 * (beta + alpha);
+  double d = 0.5 * (beta - alpha);
+  double tb = theta * (1.0 + xi);
+  double sb = tb / d;
+  *theta_bar = tb;
+  *delta = d;
+  *sigma_bar = sb;
+  if (rho) {
+    rho[0] = 1.0 / sb;
+    for (int j = 1; j <= k; ++j) rho[j] = 1.0 / (2.0 * sb - rho[j - 1]);
+  }
+  return 0;
+}
+
+/* Scalar p_k(x) by the three-term recursion Eq. polycheb:
+ * p_{-1} = 0, p_0 = 1/theta, p_j = rho_j (2 sigma (1 - x/theta) p_{j-1}
+ * - rho_{j-1} p_{j-2} + 2/delta), with theta, sigma replaced by their
+ * xi-modified values. */
+double oracle_cheb_poly(double x, double alpha, double beta, double xi, int k) {
+  double tb, d, sb;
+  double* rho = (double*)malloc(sizeof(double) * (size_t)(k + 1));
+  if (oracle_cheb_coeffs(alpha, beta, xi, k, &tb, &d, &sb, rho) != 0) {
+    free(rho);
+    return NAN;
+  }
+  double pm2 = 0.0;       /* p_{j-2} */
+  double pm1 = 1.0 / tb;  /* p_{j-1}; starts as p_0 */
+  for (int j = 1; j <= k; ++j) {
+    double pj = rho[j] * (2.0 * sb * (1.0 - x / tb) * pm1 - rho[j - 1] * pm2 + 2.0 / d);
+    pm2 = pm1;
+    pm1 = pj;
+  }
+  free(rho);
+  return pm1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Linear operators                                                    */
+/* ------------------------------------------------------------------ */
+
+void oracle_spmv(int n, const int* rowptr, const int* col, const double* val, const double* x,
+                 double* y) {
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) s += val[p] * x[col[p]];
+    y[i] = s;
+  }
+}
+
+typedef struct {
+  void (*apply)(const void* ctx, const double* x, double* y);
+  const void* ctx;
+  int n;
+} op_t;
+
+typedef struct {
+  int n;
+  const int *rowptr, *col;
+  const double* val;
+} csr_t;
+
+static void csr_apply(const void* c, const double* x, double* y) {
+  const csr_t* a = (const csr_t*)c;
+  oracle_spmv(a->n, a->rowptr, a->col, a->val, x, y);
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 2 (ChebAlg): r_hat = P_m r                                */
+/* ------------------------------------------------------------------ */
+
+static int cheb_apply_op(const op_t* A, int m, double theta_bar, double delta, double sigma_bar,
+                         const double* rho, const double* r, double* out, long long* mvp) {
+  int n = A->n;
+  double* x_old = (double*)malloc(sizeof(double) * (size_t)n);
+  double* x = (double*)malloc(sizeof(double) * (size_t)n);
+  double* t = (double*)malloc(sizeof(double) * (size_t)n);
+  double* zv = (double*)malloc(sizeof(double) * (size_t)n);
+  /* step 2: x_old = r / theta (exit here when m = 0) */
+  for (int i = 0; i < n; ++i) x_old[i] = r[i] / theta_bar;
+  if (m == 0) {
+    memcpy(out, x_old, sizeof(double) * (size_t)n);
+  } else {
+    /* step 3: x = (2 rho_1 / delta) (2 r - A r / theta) (exit when m = 1) */
+    A->apply(A->ctx, r, t);
+    if (mvp) ++*mvp;
+    for (int i = 0; i < n; ++i) x[i] = (2.0 * rho[1] / delta) * (2.0 * r[i] - t[i] / theta_bar);
+    /* steps 4-8: for k = 2..m */
+    for (int k = 2; k <= m; ++k) {
+      A->apply(A->ctx, x, t);
+      if (mvp) ++*mvp;
+      for (int i = 0; i < n; ++i) zv[i] = (2.0 / delta) * (r[i] - t[i]);
+      for (int i = 0; i < n; ++i) {
+        double rhat = rho[k] * (2.0 * sigma_bar * x[i] - rho[k - 1] * x_old[i] + zv[i]);
+        x_old[i] = x[i];
+        x[i] = rhat;
+      }
+    }
+    memcpy(out, x, sizeof(double) * (size_t)n);
+  }
+  free(x_old);
+  free(x);
+  free(t);
+  free(zv);
+  return all_finite(n, out) ? 0 : -3;
+}
+
+int oracle_cheb_apply(int n, const int* rowptr, const int* col, const double* val, double alpha,
+                      double beta, double xi, int k, const double* r, double* z) {
+  double tb, d, sb;
+  double* rho = (double*)malloc(sizeof(double) * (size_t)(k + 1));
+  int rc = oracle_cheb_coeffs(alpha, beta, xi, k, &tb, &d, &sb, rho);
+  if (rc == 0) {
+    csr_t a = {n, rowptr, col, val};
+    op_t op = {csr_apply, &a, n};
+    rc = cheb_apply_op(&op, k, tb, d, sb, rho, r, z, NULL);
+  }
+  free(rho);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1 (NewtAlg): Newton-based preconditioner of level nlev    */
+/* ------------------------------------------------------------------ */
+/* zeta_0 scales the interval to be centred on 1: zeta_0 = 1/theta_bar
+ * (= 2/(alpha+beta) when xi = 0).  The lower end of the xi-shifted interval
+ * is alpha' = theta_bar - delta, so zeta_1 = 2/(1 + 2 alpha' zeta_0 -
+ * (alpha' zeta_0)^2) and zeta_i = 2/(1 + 2 zeta_{i-1} - zeta_{i-1}^2)
+ * (Eq. zetaNewt).  P_hat_0 r = zeta_0 r and P_hat_{j+1} r =
+ * zeta_{j+1} (2 P_hat_j r - P_hat_j A P_hat_j r) (Eq. newrec0), applied
+ * recursively: degree 2^nlev - 1, with 2^nlev - 1 products by A. */
+static void newton_rec(const op_t* A, const double* zeta, int j, const double* r, double* out) {
+  int n = A->n;
+  if (j == 0) {
+    for (int i = 0; i < n; ++i) out[i] = zeta[0] * r[i];
+    return;
+  }
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  double* w = (double*)malloc(sizeof(double) * (size_t)n);
+  double* v = (double*)malloc(sizeof(double) * (size_t)n);
+  newton_rec(A, zeta, j - 1, r, y);  /* y = P_hat_{j-1} r         */
+  A->apply(A->ctx, y, w);            /* w = A P_hat_{j-1} r       */
+  newton_rec(A, zeta, j - 1, w, v);  /* v = P_hat_{j-1} A P_hat_{j-1} r */
+  for (int i = 0; i < n; ++i) out[i] = zeta[j] * (2.0 * y[i] - v[i]);
+  free(y);
+  free(w);
+  free(v);
+}
+
+int oracle_newton_apply(int n, const int* rowptr, const int* col, const double* val,
+                        double alpha, double beta, double xi, int nlev, const double* r,
+                        double* z) {
+  if (nlev < 0 || !(alpha > 0.0) || !(beta > alpha) || xi < 0.0) return -1;
+  double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
+  double theta_bar = theta * (1.0 + xi);
+  double a_shift = theta_bar - delta;
+  double* zeta = (double*)malloc(sizeof(double) * (size_t)(nlev + 1));
+  zeta[0] = 1.0 / theta_bar;
+  if (nlev >= 1) {
+    double az = a_shift * zeta[0];
+    zeta[1] = 2.0 / (1.0 + 2.0 * az - az * az);
+  }
+  for (int i = 2; i <= nlev; ++i) zeta[i] = 2.0 / (1.0 + 2.0 * zeta[i - 1] - zeta[i - 1] * zeta[i - 1]);
+  csr_t a = {n, rowptr, col, val};
+  op_t op = {csr_apply, &a, n};
+  newton_rec(&op, zeta, nlev, r, z);
+  free(zeta);
+  return all_finite(n, z) ? 0 : -3;
+}
+
+/* ------------------------------------------------------------------ */
+/* Section 3: seed preconditioner W = diag(A)^{-1/2}, A_hat = W^T A W  */
+/* ------------------------------------------------------------------ */
+
+int oracle_jacobi_scale(int n, const int* rowptr, const int* col, const double* val,
+                        double* val_hat, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p)
+      if (col[p] == i) d += val[p];
+    if (!(d > 0.0)) return -2;
+    w[i] = 1.0 / sqrt(d);
+  }
+  for (int i = 0; i < n; ++i)
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) val_hat[p] = w[i] * val[p] * w[col[p]];
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Lanczos tridiagonalisation and Sturm bisection                      */
+/* ------------------------------------------------------------------ */
+
+static int lanczos_op(const op_t* A, const double* v0, int m, double* a, double* b) {
+  int n = A->n;
+  double* v = (double*)calloc((size_t)n, sizeof(double));
+  double* vp = (double*)calloc((size_t)n, sizeof(double));
+  double* w = (double*)calloc((size_t)n, sizeof(double));
+  double nv = sqrt(dot(n, v0, v0));
+  int steps = 0;
+  if (nv > 0.0) {
+    for (int i = 0; i < n; ++i) v[i] = v0[i] / nv;
+    double bprev = 0.0;
+    for (int j = 0; j < m; ++j) {
+      A->apply(A->ctx, v, w);
+      for (int i = 0; i < n; ++i) w[i] -= bprev * vp[i];
+      a[j] = dot(n, w, v);
+      for (int i = 0; i < n; ++i) w[i] -= a[j] * v[i];
+      steps = j + 1;
+      if (j == m - 1) break;
+      double bj = sqrt(dot(n, w, w));
+      if (!(bj > 1e-300)) break; /* invariant subspace found */
+      b[j] = bj;
+      for (int i = 0; i < n; ++i) {
+        vp[i] = v[i];
+        v[i] = w[i] / bj;
+      }
+      bprev = bj;
+    }
+  }
+  free(v);
+  free(vp);
+  free(w);
+  return steps;
+}
+
+int oracle_lanczos(int n, const int* rowptr, const int* col, const double* val,
+                   const double* v0, int m, double* a, double* b) {
+  csr_t c = {n, rowptr, col, val};
+  op_t op = {csr_apply, &c, n};
+  return lanczos_op(&op, v0, m, a, b);
+}
+
+/* number of eigenvalues of T (diag a, off-diag b) smaller than x */
+static int sturm_count(int m, const double* a, const double* b, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < m; ++i) {
+    double off = (i > 0) ? b[i - 1] * b[i - 1] / d : 0.0;
+    d = a[i] - x - off;
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+int oracle_tridiag_extremes(int m, const double* a, const double* b, double* lmin,
+                            double* lmax) {
+  if (m <= 0) return -1;
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    double r = 0.0;
+    if (i > 0) r += fabs(b[i - 1]);
+    if (i < m - 1) r += fabs(b[i]);
+    if (a[i] - r < lo) lo = a[i] - r;
+    if (a[i] + r > hi) hi = a[i] + r;
+  }
+  double span = hi - lo + 1e-300;
+  /* smallest eigenvalue: the point where the count goes from 0 to 1 */
+  double l = lo - 1e-12 * span, h = hi + 1e-12 * span;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (l + h);
+    if (sturm_count(m, a, b, mid) >= 1) h = mid; else l = mid;
+  }
+  *lmin = 0.5 * (l + h);
+  /* largest eigenvalue: the point where the count goes from m-1 to m */
+  l = lo - 1e-12 * span;
+  h = hi + 1e-12 * span;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (l + h);
+    if (sturm_count(m, a, b, mid) >= m) h = mid; else l = mid;
+  }
+  *lmax = 0.5 * (l + h);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* PCG with P = p_k(A) (Section 1, Algorithm 2 as the preconditioner)  */
+/* ------------------------------------------------------------------ */
+/* Standard PCG from x0: r = b - A x, z = P r, p = z; each iteration
+ * q = A p, alpha = (r,z)/(p,q), x += alpha p, r -= alpha q, stop when
+ * ||r||/||b|| <= rtol, z = P r, beta = (r,z)_new/(r,z)_old, p = z + beta p.
+ * Work per iteration: one product by A plus m inside P, and 3 inner
+ * products; the preconditioner is not applied after the last iteration,
+ * so products = iter (m + 1) and inner products = 3 iter from x0 = 0
+ * (the counts of Table 4).
+ * flexible = 1 replaces beta by (z_new, r_new - r_old)/(z_old, r_old)
+ * (flexible CG; identical in exact arithmetic for a fixed SPD P). */
+typedef struct {
+  int m;
+  double theta_bar, delta, sigma_bar;
+  const double* rho;
+} cheb_t;
+
+static int pcg_op(const op_t* A, const cheb_t* P, const double* b, double* x, int flexible,
+                  int maxit, double rtol, oracle_stats* st) {
+  int n = A->n;
+  double* r = (double*)malloc(sizeof(double) * (size_t)n);
+  double* z = (double*)malloc(sizeof(double) * (size_t)n);
+  double* p = (double*)malloc(sizeof(double) * (size_t)n);
+  double* q = (double*)malloc(sizeof(double) * (size_t)n);
+  double* r_old = flexible ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
+  long long mvp = 0, dots = 0;
+  int rc = 0, it = 0;
+  double bnorm = sqrt(dot(n, b, b));
+  int x_zero = 1;
+  for (int i = 0; i < n; ++i)
+    if (x[i] != 0.0) { x_zero = 0; break; }
+  if (x_zero) {
+    memcpy(r, b, sizeof(double) * (size_t)n);
+  } else {
+    A->apply(A->ctx, x, q);
+    ++mvp;
+    for (int i = 0; i < n; ++i) r[i] = b[i] - q[i];
+  }
+  double rel = (bnorm > 0.0) ? sqrt(dot(n, r, r)) / bnorm : 0.0;
+  if (bnorm == 0.0 || rel <= rtol) goto done;
+  rc = cheb_apply_op(A, P->m, P->theta_bar, P->delta, P->sigma_bar, P->rho, r, z, &mvp);
+  if (rc) goto done;
+  memcpy(p, z, sizeof(double) * (size_t)n);
+  double rz = dot(n, r, z);
+  ++dots;
+  if (!(rz > 0.0)) { rc = isfinite(rz) ? -2 : -3; goto done; }
+  rc = 1;
+  while (it < maxit) {
+    A->apply(A->ctx, p, q);
+    ++mvp;
+    double pq = dot(n, p, q);
+    ++dots;
+    if (!(pq > 0.0)) { rc = isfinite(pq) ? -2 : -3; break; }
+    double alpha = rz / pq;
+    if (flexible) memcpy(r_old, r, sizeof(double) * (size_t)n);
+    for (int i = 0; i < n; ++i) x[i] += alpha * p[i];
+    for (int i = 0; i < n; ++i) r[i] -= alpha * q[i];
+    ++it;
+    double rr = dot(n, r, r);
+    ++dots;
+    if (!isfinite(rr)) { rc = -3; break; }
+    rel = sqrt(rr) / bnorm;
+    if (rel <= rtol) { rc = 0; break; }
+    rc = cheb_apply_op(A, P->m, P->theta_bar, P->delta, P->sigma_bar, P->rho, r, z, &mvp);
+    if (rc) break;
+    rc = 1;
+    double rz_new = dot(n, r, z);
+    ++dots;
+    double beta;
+    if (flexible) {
+      double zr_old = dot(n, z, r_old);
+      beta = (rz_new - zr_old) / rz;
+    } else {
+      beta = rz_new / rz;
+    }
+    if (!(rz_new > 0.0)) { rc = isfinite(rz_new) ? -2 : -3; break; }
+    rz = rz_new;
+    for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+  }
+done:
+  if (st) {
+    st->iterations = it;
+    st->mvp = mvp;
+    st->dots = dots;
+    st->rel_res = rel;
+    st->status = rc;
+  }
+  free(r);
+  free(z);
+  free(p);
+  free(q);
+  free(r_old);
+  return rc;
+}
+
+static double auto_xi(double a, double b) {
+  double xi = 10.0 * a / b;
+  if (xi < 1e-6) xi = 1e-6;
+  if (xi > 1e-2) xi = 1e-2;
+  return xi;
+}
+
+static int pick_interval(const op_t* A, const double* v0, const oracle_options* opt,
+                         double* alpha, double* beta) {
+  if (opt->interval == 1) {
+    *alpha = opt->alpha;
+    *beta = opt->beta;
+    return 0;
+  }
+  int m = opt->lanczos_steps > 0 ? opt->lanczos_steps : 10;
+  double* a = (double*)calloc((size_t)m, sizeof(double));
+  double* b = (double*)calloc((size_t)m, sizeof(double));
+  int steps = lanczos_op(A, v0, m, a, b);
+  int rc = steps > 0 ? oracle_tridiag_extremes(steps, a, b, alpha, beta) : -1;
+  free(a);
+  free(b);
+  return rc;
+}
+
+int oracle_pcg_csr(int n, const int* rowptr, const int* col, const double* val,
+                   const double* b, double* x, const double* v0, const oracle_options* opt,
+                   oracle_stats* st) {
+  if (n <= 0 || opt->k < 0) return -1;
+  int nnz = rowptr[n];
+  double* vh = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  double* w = (double*)malloc(sizeof(double) * (size_t)n);
+  double* bh = (double*)malloc(sizeof(double) * (size_t)n);
+  double* xh = (double*)malloc(sizeof(double) * (size_t)n);
+  double* rho = (double*)malloc(sizeof(double) * (size_t)(opt->k + 1));
+  int rc = 0;
+  if (opt->seed_scaling == 1) {
+    rc = oracle_jacobi_scale(n, rowptr, col, val, vh, w);
+  } else {
+    memcpy(vh, val, sizeof(double) * (size_t)nnz);
+    for (int i = 0; i < n; ++i) w[i] = 1.0;
+  }
+  if (rc == 0) {
+    csr_t ah = {n, rowptr, col, vh};
+    op_t A = {csr_apply, &ah, n};
+    /* A_hat x_hat = b_hat with b_hat = W b, x = W x_hat */
+    for (int i = 0; i < n; ++i) bh[i] = w[i] * b[i];
+    for (int i = 0; i < n; ++i) xh[i] = x[i] / w[i];
+    double alpha, beta;
+    rc = pick_interval(&A, v0, opt, &alpha, &beta);
+    if (rc == 0) {
+      double xi = opt->xi >= 0.0 ? opt->xi : auto_xi(alpha, beta);
+      cheb_t P;
+      P.m = opt->k;
+      P.rho = rho;
+      rc = oracle_cheb_coeffs(alpha, beta, xi, opt->k, &P.theta_bar, &P.delta, &P.sigma_bar, rho);
+      if (rc == 0) rc = pcg_op(&A, &P, bh, xh, opt->flexible, opt->maxit, opt->rtol, st);
+      if (st) {
+        st->alpha_hat = alpha;
+        st->beta_hat = beta;
+        st->xi = xi;
+      }
+      for (int i = 0; i < n; ++i) x[i] = w[i] * xh[i];
+      if (st) {
+        double* t = (double*)malloc(sizeof(double) * (size_t)n);
+        oracle_spmv(n, rowptr, col, val, x, t);
+        double num = 0.0;
+        for (int i = 0; i < n; ++i) num += (b[i] - t[i]) * (b[i] - t[i]);
+        double bn = sqrt(dot(n, b, b));
+        st->true_rel_res = bn > 0.0 ? sqrt(num) / bn : 0.0;
+        free(t);
+      }
+    }
+  }
+  if (st) st->status = rc;
+  free(vh);
+  free(w);
+  free(bh);
+  free(xh);
+  free(rho);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Section 4.2: the DFN Schur complement                               */
+/* ------------------------------------------------------------------ */
+/* A is block diagonal (one SPD block per fracture).  As in the paper, its
+ * exact Cholesky factor L_A (block diagonal, fill confined to the band of
+ * each block) is computed once; A^{-1} v = L_A^{-T} L_A^{-1} v. */
+
+struct oracle_schur {
+  oracle_dfn d;
+  int* bw;          /* per-fracture half bandwidth          */
+  long long* boff;  /* offset of each block's band storage  */
+  double* L;        /* band storage: L[boff + i*(bw+1) + (i-j)] */
+};
+
+oracle_schur* oracle_schur_create(const oracle_dfn* d) {
+  oracle_schur* s = (oracle_schur*)calloc(1, sizeof(oracle_schur));
+  s->d = *d;
+  int nf = d->n_f;
+  s->bw = (int*)calloc((size_t)nf, sizeof(int));
+  s->boff = (long long*)calloc((size_t)nf + 1, sizeof(long long));
+  for (int f = 0; f < nf; ++f) {
+    long long o = d->offset[f], e = d->offset[f + 1];
+    int bw = 0;
+    for (long long i = o; i < e; ++i)
+      for (int p = d->A_rowptr[i]; p < d->A_rowptr[i + 1]; ++p) {
+        long long j = d->A_col[p];
+        int dist = (int)(i > j ? i - j : j - i);
+        if (dist > bw) bw = dist;
+      }
+    s->bw[f] = bw;
+    s->boff[f + 1] = s->boff[f] + (e - o) * (long long)(bw + 1);
+  }
+  s->L = (double*)calloc((size_t)s->boff[nf], sizeof(double));
+  for (int f = 0; f < nf; ++f) {
+    long long o = d->offset[f];
+    int nloc = (int)(d->offset[f + 1] - o), bw = s->bw[f];
+    double* L = s->L + s->boff[f];
+#define LB(i, j) L[(long long)(i) * (bw + 1) + ((i) - (j))]
+    /* copy the lower band of the block */
+    for (int i = 0; i < nloc; ++i)
+      for (int p = d->A_rowptr[o + i]; p < d->A_rowptr[o + i + 1]; ++p) {
+        int j = (int)(d->A_col[p] - o);
+        if (j <= i) LB(i, j) = d->A_val[p];
+      }
+    /* banded Cholesky, column by column */
+    for (int j = 0; j < nloc; ++j) {
+      int k0 = j - bw > 0 ? j - bw : 0;
+      double sj = LB(j, j);
+      for (int k = k0; k < j; ++k) sj -= LB(j, k) * LB(j, k);
+      if (!(sj > 0.0)) {
+        oracle_schur_free(s);
+        return NULL;
+      }
+      double ljj = sqrt(sj);
+      LB(j, j) = ljj;
+      int iend = j + bw < nloc - 1 ? j + bw : nloc - 1;
+      for (int i = j + 1; i <= iend; ++i) {
+        int kk = i - bw > 0 ? i - bw : 0;
+        double sij = LB(i, j);
+        for (int k = kk; k < j; ++k) sij -= LB(i, k) * LB(j, k);
+        LB(i, j) = sij / ljj;
+      }
+    }
+#undef LB
+  }
+  return s;
+}
+
+void oracle_schur_free(oracle_schur* s) {
+  if (!s) return;
+  free(s->bw);
+  free(s->boff);
+  free(s->L);
+  free(s);
+}
+
+/* y = A_f^{-1} v on one block: forward (L u = v) then backward (L^T y = u). */
+static void block_solve(const oracle_schur* s, int f, const double* v, double* y) {
+  long long o = s->d.offset[f];
+  int nloc = (int)(s->d.offset[f + 1] - o), bw = s->bw[f];
+  const double* L = s->L + s->boff[f];
+#define LB(i, j) L[(long long)(i) * (bw + 1) + ((i) - (j))]
+  for (int i = 0; i < nloc; ++i) {
+    double t = v[o + i];
+    int k0 = i - bw > 0 ? i - bw : 0;
+    for (int k = k0; k < i; ++k) t -= LB(i, k) * y[o + k];
+    y[o + i] = t / LB(i, i);
+  }
+  for (int i = nloc - 1; i >= 0; --i) {
+    double t = y[o + i];
+    int k1 = i + bw < nloc - 1 ? i + bw : nloc - 1;
+    for (int k = i + 1; k <= k1; ++k) t -= LB(k, i) * y[o + k];
+    y[o + i] = t / LB(i, i);
+  }
+#undef LB
+}
+
+int oracle_ainv(const oracle_schur* s, const double* v, double* y) {
+  for (int f = 0; f < s->d.n_f; ++f) block_solve(s, f, v, y);
+  return 0;
+}
+
+static void rect_spmv(int nrows, const int* rp, const int* ci, const double* va, const double* x,
+                      double* y) {
+  for (int i = 0; i < nrows; ++i) {
+    double acc = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) acc += va[p] * x[ci[p]];
+    y[i] = acc;
+  }
+}
+
+/* Algorithm 3, y = S_u r, with the regularisation parameter alpha kept in
+ * the products by B^T and C^T as in the expansion
+ * S_u = G^u - alpha B^T A^{-1} C - alpha C^T A^{-1} B + C^T A^{-1} G^h A^{-1} C
+ * (alpha = 1 gives the algorithm as printed). */
+int oracle_schur_apply(const oracle_schur* s, const double* r, double* y) {
+  const oracle_dfn* d = &s->d;
+  int nh = d->n_h, nu = d->n_u;
+  double* v = (double*)calloc((size_t)nh, sizeof(double));
+  double* z = (double*)calloc((size_t)nh, sizeof(double));
+  double* t = (double*)calloc((size_t)nh, sizeof(double));
+  double* w = (double*)calloc((size_t)nh, sizeof(double));
+  double* zu = (double*)calloc((size_t)nu, sizeof(double));
+  double* tmp = (double*)calloc((size_t)nu, sizeof(double));
+  rect_spmv(nh, d->C_rowptr, d->C_col, d->C_val, r, v);           /* v = C r            */
+  rect_spmv(nh, d->B_rowptr, d->B_col, d->B_val, r, z);           /* z = B r            */
+  oracle_ainv(s, v, t);                                            /* t = A^{-1} v       */
+  oracle_ainv(s, z, w);                                            /* w = A^{-1} z       */
+  rect_spmv(nu, d->Gu_rowptr, d->Gu_col, d->Gu_val, r, zu);       /* z = G^u r          */
+  rect_spmv(nu, d->BT_rowptr, d->BT_col, d->BT_val, t, tmp);      /*   - alpha B^T t    */
+  for (int i = 0; i < nu; ++i) zu[i] -= d->alpha_reg * tmp[i];
+  rect_spmv(nu, d->CT_rowptr, d->CT_col, d->CT_val, w, tmp);      /*   - alpha C^T w    */
+  for (int i = 0; i < nu; ++i) zu[i] -= d->alpha_reg * tmp[i];
+  rect_spmv(nh, d->Gh_rowptr, d->Gh_col, d->Gh_val, t, v);        /* v = G^h t          */
+  oracle_ainv(s, v, w);                                            /* w = A^{-1} v       */
+  rect_spmv(nu, d->CT_rowptr, d->CT_col, d->CT_val, w, tmp);      /* y = z + C^T w      */
+  for (int i = 0; i < nu; ++i) y[i] = zu[i] + tmp[i];
+  free(v);
+  free(z);
+  free(t);
+  free(w);
+  free(zu);
+  free(tmp);
+  return all_finite(nu, y) ? 0 : -3;
+}
+
+/* Algorithm 4: Z = A^{-1} C, T = G^h Z - 2 alpha B, (D_S)_i = G^u_ii + z_i^T t_i.
+ * Column i of C touches one fracture, and A^{-1} is block diagonal, so z_i
+ * is obtained by solving that fracture's block only; z_i^T t_i then only
+ * involves the rows of that block. */
+int oracle_schur_diag(const oracle_schur* s, double* ds) {
+  const oracle_dfn* d = &s->d;
+  int nh = d->n_h, nu = d->n_u;
+  /* column access to C and B through their transposes CT, BT */
+  double* c = (double*)calloc((size_t)nh, sizeof(double));
+  double* zc = (double*)calloc((size_t)nh, sizeof(double));
+  double* ghz = (double*)calloc((size_t)nh, sizeof(double));
+  double* bcol = (double*)calloc((size_t)nh, sizeof(double));
+  for (int i = 0; i < nu; ++i) {
+    int f = -1;
+    for (int p = d->CT_rowptr[i]; p < d->CT_rowptr[i + 1]; ++p) {
+      long long row = d->CT_col[p];
+      c[row] = d->CT_val[p];
+      int ff = 0;
+      while (d->offset[ff + 1] <= row) ++ff;
+      if (f >= 0 && ff != f) return -1; /* C must be fracture-local */
+      f = ff;
+    }
+    double gii = 0.0;
+    for (int p = d->Gu_rowptr[i]; p < d->Gu_rowptr[i + 1]; ++p)
+      if (d->Gu_col[p] == i) gii += d->Gu_val[p];
+    double acc = 0.0;
+    if (f >= 0) {
+      long long o = d->offset[f], e = d->offset[f + 1];
+      block_solve(s, f, c, zc);
+      for (long long row = o; row < e; ++row) {
+        double g = 0.0;
+        for (int p = d->Gh_rowptr[row]; p < d->Gh_rowptr[row + 1]; ++p) g += d->Gh_val[p] * zc[d->Gh_col[p]];
+        ghz[row] = g;
+      }
+      for (int p = d->BT_rowptr[i]; p < d->BT_rowptr[i + 1]; ++p) bcol[d->BT_col[p]] += d->BT_val[p];
+      for (long long row = o; row < e; ++row) acc += zc[row] * (ghz[row] - 2.0 * d->alpha_reg * bcol[row]);
+      for (int p = d->BT_rowptr[i]; p < d->BT_rowptr[i + 1]; ++p) bcol[d->BT_col[p]] = 0.0;
+      for (long long row = o; row < e; ++row) zc[row] = 0.0;
+    }
+    for (int p = d->CT_rowptr[i]; p < d->CT_rowptr[i + 1]; ++p) c[d->CT_col[p]] = 0.0;
+    ds[i] = gii + acc;
+  }
+  free(c);
+  free(zc);
+  free(ghz);
+  free(bcol);
+  return all_finite(nu, ds) ? 0 : -3;
+}
+
+/* r = W^T M^{-1} f_1 with f_1 = [q; 0] (Eq. schur):
+ * M^{-1} f_1 = [A^{-1} q; -A^{-1} G^h A^{-1} q], W^T = [alpha B^T, C^T]. */
+int oracle_schur_rhs(const oracle_schur* s, const double* q, double* r) {
+  const oracle_dfn* d = &s->d;
+  int nh = d->n_h, nu = d->n_u;
+  double* a1 = (double*)calloc((size_t)nh, sizeof(double));
+  double* g = (double*)calloc((size_t)nh, sizeof(double));
+  double* a2 = (double*)calloc((size_t)nh, sizeof(double));
+  double* tmp = (double*)calloc((size_t)nu, sizeof(double));
+  oracle_ainv(s, q, a1);
+  rect_spmv(nh, d->Gh_rowptr, d->Gh_col, d->Gh_val, a1, g);
+  oracle_ainv(s, g, a2);
+  rect_spmv(nu, d->BT_rowptr, d->BT_col, d->BT_val, a1, r);
+  rect_spmv(nu, d->CT_rowptr, d->CT_col, d->CT_val, a2, tmp);
+  for (int i = 0; i < nu; ++i) r[i] = d->alpha_reg * r[i] - tmp[i];
+  free(a1);
+  free(g);
+  free(a2);
+  free(tmp);
+  return all_finite(nu, r) ? 0 : -3;
+}
+
+/* h = A^{-1}(q + C u), p = A^{-1}(alpha B u - G^h h) (Section 4.2, with
+ * alpha kept as in the first block row of the permuted system). */
+int oracle_schur_recover(const oracle_schur* s, const double* q, const double* u, double* h,
+                         double* p) {
+  const oracle_dfn* d = &s->d;
+  int nh = d->n_h;
+  double* t = (double*)calloc((size_t)nh, sizeof(double));
+  double* g = (double*)calloc((size_t)nh, sizeof(double));
+  rect_spmv(nh, d->C_rowptr, d->C_col, d->C_val, u, t);
+  for (int i = 0; i < nh; ++i) t[i] += q[i];
+  oracle_ainv(s, t, h);
+  rect_spmv(nh, d->B_rowptr, d->B_col, d->B_val, u, t);
+  rect_spmv(nh, d->Gh_rowptr, d->Gh_col, d->Gh_val, h, g);
+  for (int i = 0; i < nh; ++i) t[i] = d->alpha_reg * t[i] - g[i];
+  oracle_ainv(s, t, p);
+  free(t);
+  free(g);
+  return 0;
+}
+
+/* S_hat = D_S^{-1/2} S_u D_S^{-1/2} (end of Section 4.3) */
+typedef struct {
+  const oracle_schur* s;
+  const double* w; /* D_S^{-1/2} */
+  double* tmp;
+  double* tmp2;
+} schur_scaled_t;
+
+static void schur_scaled_apply(const void* c, const double* x, double* y) {
+  const schur_scaled_t* ss = (const schur_scaled_t*)c;
+  int nu = ss->s->d.n_u;
+  for (int i = 0; i < nu; ++i) ss->tmp[i] = ss->w[i] * x[i];
+  oracle_schur_apply(ss->s, ss->tmp, ss->tmp2);
+  for (int i = 0; i < nu; ++i) y[i] = ss->w[i] * ss->tmp2[i];
+}
+
+int oracle_pcg_schur(const oracle_schur* s, const double* ds, const double* r, double* u,
+                     const double* v0, const oracle_options* opt, oracle_stats* st) {
+  int nu = s->d.n_u;
+  double* w = (double*)malloc(sizeof(double) * (size_t)nu);
+  double* rh = (double*)malloc(sizeof(double) * (size_t)nu);
+  double* uh = (double*)malloc(sizeof(double) * (size_t)nu);
+  double* rho = (double*)malloc(sizeof(double) * (size_t)(opt->k + 1));
+  schur_scaled_t ss = {s, w, (double*)malloc(sizeof(double) * (size_t)nu),
+                       (double*)malloc(sizeof(double) * (size_t)nu)};
+  int rc = 0;
+  for (int i = 0; i < nu; ++i) {
+    if (!(ds[i] > 0.0)) rc = -2;
+    w[i] = 1.0 / sqrt(ds[i]);
+  }
+  if (rc == 0) {
+    op_t A = {schur_scaled_apply, &ss, nu};
+    for (int i = 0; i < nu; ++i) rh[i] = w[i] * r[i];
+    for (int i = 0; i < nu; ++i) uh[i] = u[i] / w[i];
+    double alpha, beta;
+    rc = pick_interval(&A, v0, opt, &alpha, &beta);
+    if (rc == 0) {
+      double xi = opt->xi >= 0.0 ? opt->xi : auto_xi(alpha, beta);
+      cheb_t P;
+      P.m = opt->k;
+      P.rho = rho;
+      rc = oracle_cheb_coeffs(alpha, beta, xi, opt->k, &P.theta_bar, &P.delta, &P.sigma_bar, rho);
+      if (rc == 0) rc = pcg_op(&A, &P, rh, uh, opt->flexible, opt->maxit, opt->rtol, st);
+      if (st) {
+        st->alpha_hat = alpha;
+        st->beta_hat = beta;
+        st->xi = xi;
+      }
+      for (int i = 0; i < nu; ++i) u[i] = w[i] * uh[i];
+      if (st) {
+        double* t = (double*)malloc(sizeof(double) * (size_t)nu);
+        oracle_schur_apply(s, u, t);
+        double num = 0.0, bn = 0.0;
+        for (int i = 0; i < nu; ++i) {
+          num += (r[i] - t[i]) * (r[i] - t[i]);
+          bn += r[i] * r[i];
+        }
+        st->true_rel_res = bn > 0.0 ? sqrt(num / bn) : 0.0;
+        free(t);
+      }
+    }
+  }
+  if (st) st->status = rc;
+  free(w);
+  free(rh);
+  free(uh);
+  free(rho);
+  free(ss.tmp);
+  free(ss.tmp2);
+  return rc;
+}
