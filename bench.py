@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark: PCG time-to-rtol with the Chebyshev polynomial preconditioner.
+
+One step = one full solve A x = b to rtol 1e-8 (PCG, P = W p_k(W^T A W) W^T,
+Algorithm 2 applied by fused SpMV+recurrence kernels) on a matrix already
+set up and resident in HBM (seed scaling, SELL layout, Lanczos interval and
+coefficients done once before timing).  Default workload: 3-D 7-point
+variable-coefficient diffusion on a 192^3 grid, lognormal(0, 2)
+conductivities (seed 1), harmonic faces, N(0,1) right-hand side, FP64,
+SELL-C-sigma, k = 20, 10 Lanczos steps, xi = clip(10 alpha/beta, 1e-6, 1e-2).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "diffusion192": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=20, lanczos=10, fmt="sell", prec="f64"),
+    "diffusion192_f32": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=20, lanczos=10, fmt="sell", prec="f32",
+                             flexible=1),
+    "diffusion192_bf16": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=20, lanczos=10, fmt="sell", prec="bf16",
+                              flexible=1),
+    "poisson32": dict(N=32, sigma=0.0, seed=0, rhs="ones_noise", k=20, lanczos=10, fmt="csr", prec="f64"),
+}
+METRIC = "PCG time-to-rtol-1e-8 (s) and polyprec_apply HBM GB/s vs plain FP64, 1 GB300"
+VAL_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
+VEC_BYTES = {"f64": 8, "f32": 4, "bf16": 4}
+
+
+def build_problem(w):
+    from paper_2208_01339_gb300 import inputs as I
+
+    if w["sigma"] == 0.0:
+        A = I.poisson3d(w["N"])
+    else:
+        A = I.diffusion3d(w["N"], w["sigma"], seed=w["seed"])
+    if w["rhs"] == "normal":
+        b = I.rhs_normal(A.n, w["seed"])
+    else:
+        b = I.rhs_ones_plus_noise(A, w["seed"])
+    return A, b
+
+
+def bytes_per_step_launch(nnz: int, n: int, k: int, prec: str) -> float:
+    """Algorithmic bytes of one fused degree step, averaged over the k steps
+    of one application: every step streams the matrix once (value + int32
+    column index per nonzero) and touches n-vectors: step 1 reads r and
+    writes y (2), step 2 reads x, r and writes y (3; x_old = r/theta is not
+    stored), steps 3..k read x, x_old, r and write y (4).  Gathered x
+    entries are counted once (L2 reuse); padding is excluded."""
+    sa, sv = VAL_BYTES[prec], VEC_BYTES[prec]
+    if k <= 0:
+        return 0.0
+    vec_passes = 2 if k == 1 else 2 + 3 + 4 * (k - 2)
+    return (k * nnz * (sa + 4) + n * sv * vec_passes) / k
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2208_01339_gb300", "csrc")
+    for f in ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_f64.cu", "step_lp.cu"):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            j = json.load(fh)
+        if j.get("hbm_gbs"):
+            return float(j["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy)"
+    return 6800.0, "fallback (6.8 TB/s)"
+
+
+def traffic_from_profile(workload: str, k: int, prec: str):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        j = json.load(fh)
+    e = j.get(f"{workload}/k{k}/{prec}")
+    if not e or e.get("source_sha") != source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pp_clocks_{os.getpid()}.csv")
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_iterations(workload: str, k: int):
+    p = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        return json.load(fh).get(f"{workload}/k{k}")
+
+
+def cpu_sample(A, b, w, k, alpha, beta, xi):
+    """Oracle seconds per PCG iteration on the full workload: one p_k apply
+    (Algorithm 2, k products) plus one product by A_hat, single thread."""
+    import oracle as O
+
+    vh, wgt = O.jacobi_scale(A)
+    from paper_2208_01339_gb300.inputs import CSR
+
+    Ah = CSR(A.n, A.rowptr, A.col, vh)
+    r = wgt * b
+    t0 = time.perf_counter()
+    z = O.cheb_apply(Ah, alpha, beta, xi, k, r)
+    O.spmv(Ah, z)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, w, rank):
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    from paper_2208_01339_gb300 import inputs as I
+
+    A, b = build_problem(w)
+    k = args.k if args.k is not None else w["k"]
+    vh, _ = O.jacobi_scale(A)
+    a, bb = O.lanczos(A, I.lanczos_start(A.n, 0), w["lanczos"], val=vh)
+    alpha, beta = O.tridiag_extremes(a, bb)
+    xi = min(max(10 * alpha / beta, 1e-6), 1e-2)
+    iters = oracle_iterations(args.workload, k)
+    src = "oracle's own count (tests/golden/oracle_iterations.json)"
+    if iters is None:
+        iters, src = None, "unknown"
+    for _ in range(args.warmup):
+        cpu_sample(A, b, w, k, alpha, beta, xi)
+    per_it = []
+    for _ in range(args.steps):
+        per_it.append(cpu_sample(A, b, w, k, alpha, beta, xi))
+    t_it = statistics.median(per_it)
+    value = t_it * iters if iters else None
+    sample = (f"1 PCG iteration's operator work (p_{k} apply + 1 product by A_hat) on the full {A.n}-row matrix, "
+              f"single thread, x {iters} iterations ({src})")
+    out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_it * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "k": k},
+           "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="diffusion192", choices=list(WORKLOADS))
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--graphs", type=int, default=0)
+    ap.add_argument("--check-every", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, w, rank)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: PLC0415
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    from paper_2208_01339_gb300 import build as B
+    from paper_2208_01339_gb300 import polyprec as P
+
+    B.build()
+    A, b = build_problem(w)
+    k = args.k if args.k is not None else w["k"]
+    opts = dict(k=k, lanczos_steps=w["lanczos"], format=w["fmt"], apply_prec=w["prec"], rtol=1e-8,
+                check_every=args.check_every, use_graphs=args.graphs, flexible=w.get("flexible", 0))
+    S = P.Solver.from_host(A, device=dev, **opts)
+    info = S.info()
+    bt = torch.as_tensor(b, device=dev)
+    x = torch.zeros_like(bt)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(3, args.warmup)):
+        S.solve(bt, x)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0)) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, st = S.solve(bt, x)
+            stats.append(st)
+        ev1.record(stream)
+        barrier()
+    clocks = clk.summary()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end: pinned host b -> device, solve, device -> pinned host x
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.empty(A.n, dtype=torch.float64, pin_memory=True)
+        hb.copy_(torch.as_tensor(b))
+        hx = torch.empty(A.n, dtype=torch.float64, pin_memory=True)
+        db = torch.empty_like(bt)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            db.copy_(hb, non_blocking=True)
+            xs, _ = S.solve(db)
+            hx.copy_(xs, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        e_ms = e0.elapsed_time(e1) / args.steps
+        if dist is not None:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": A.n * 8, "d2h_bytes_per_step": A.n * 8}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    it = [s["iterations"] for s in stats]
+    t_apply = sum(s["t_apply_ms"] for s in stats)
+    n_launch = sum(s["apply_launches"] for s in stats)
+    bpl = bytes_per_step_launch(A.nnz, A.n, k, w["prec"])
+    roof = None
+    if n_launch > 0 and t_apply > 0:
+        avg_s = t_apply / 1e3 / n_launch
+        peak, peak_src = measured_peak()
+        ach = bpl / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": traffic_from_profile(args.workload, k, w["prec"]), "peak_source": peak_src,
+                "kernel": f"sell_step_kernel ({w['prec']}, C={info['sell_C']})" if info["format"] == 2 else
+                f"csr_step_kernel ({w['prec']})",
+                "algorithmic_bytes_per_launch": int(bpl), "avg_launch_us": round(avg_s * 1e6, 2)}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle as O
+
+        O.build()
+        t_it = cpu_sample(A, b, w, k, info["alpha_hat"], info["beta_hat"], info["xi"])
+        oi = oracle_iterations(args.workload, k)
+        its = oi if oi else statistics.median(it)
+        src = "oracle's own iteration count" if oi else "the GPU iteration count"
+        cpu = {"value": t_it * its, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"1 PCG iteration's operator work (p_{k} apply + 1 product) on the full {A.n}-row matrix, "
+                         f"single thread, extrapolated x {its} iterations ({src})"}
+    out = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": w["prec"], "data": "synthetic",
+        "config": {"workload": args.workload, "grid": f"{w['N']}^3", "n": A.n, "nnz": A.nnz, "k": k,
+                   "sigma_ln": w["sigma"], "format": "SELL" if info["format"] == 2 else "CSR",
+                   "sell_C": info["sell_C"], "lanczos_steps": w["lanczos"], "rtol": 1e-8,
+                   "l2": "inputs larger than L2 (matrix >> 129 MB)" if A.nnz * 12 > 129e6 else "L2-resident inputs",
+                   "graphs": args.graphs, "parallelism": f"replicas x{world}"},
+        "iterations": int(statistics.median(it)), "setup_ms": round(info["t_setup_ms"], 2),
+        "alpha_hat": info["alpha_hat"], "beta_hat": info["beta_hat"], "xi": info["xi"],
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * polyprec -- GB300 (sm_103a) polynomial-preconditioned Conjugate Gradient.
+ *
+ * C ABI of libpolyprec.so.  Method: Bergamaschi, Ferronato, Isotton, Janna &
+ * Martinez, "Parallel matrix-free polynomial preconditioners with application
+ * to flow simulations in discrete fracture networks" (arXiv 2208.01339).
+ *
+ * The library solves A x = b, A sparse SPD (Section 1), by PCG with the
+ * preconditioner P = W p_k(W^T A W) W^T (Section 3), where W is the seed
+ * preconditioner (identity or diag(A)^{-1/2}) and p_k is the xi-modified
+ * Chebyshev polynomial of degree k (Section 2.2, Eq. polycheb, Eq. rhocheb,
+ * Eq. thetamod) applied by the three-term recurrence of Algorithm 2.  The
+ * same solver runs on the matrix-free Schur complement S_u of the fracture-
+ * network system (Section 4.2, Eq. schur, Algorithm 3) with the diagonal
+ * seed D_S = diag(S_u) of Algorithm 4.
+ *
+ * Conventions shared by every entry point
+ *  - Device pointers are CUDA device addresses owned by the caller; the
+ *    library never allocates device memory.  Scratch memory comes from one
+ *    caller-allocated workspace of the size the *_workspace_size query
+ *    returns; it must stay allocated, untouched, until pp_destroy().
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is ordered on that stream.  Calls on one context must
+ *    not overlap (they share the workspace).
+ *  - Host pointers are marked "host".  Vectors are dense FP64 with unit
+ *    stride; a block of nrhs vectors is column-major (vector j starts at
+ *    j*n).
+ *  - Every call returns a status (PP_OK = 0).  After a failure the message
+ *    is available from pp_last_error(ctx) (or pp_last_error(NULL) when no
+ *    context exists).  Invalid arguments are reported before any work is
+ *    enqueued; CUDA launch failures are returned as PP_ECUDA.
+ */
+#ifndef POLYPREC_H
+#define POLYPREC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PP_OK 0
+#define PP_MAXIT 1          /* not converged within maxit; result valid      */
+#define PP_EINVAL (-1)      /* invalid argument                               */
+#define PP_EBREAKDOWN (-2)  /* (p,Ap) <= 0 or (r,z) <= 0: operator/precond.
+                               not SPD (e.g. lambda_max >= 2 theta_bar)      */
+#define PP_ENONFINITE (-3)  /* NaN/Inf met in a reduction                     */
+#define PP_ECUDA (-4)       /* CUDA runtime error                             */
+#define PP_ETIMEOUT (-5)    /* bounded device wait expired                    */
+#define PP_EUNSUPPORTED (-6)/* unsupported format / precision / shape         */
+
+/* ---- enums ------------------------------------------------------------ */
+#define PP_INTERVAL_LANCZOS 0 /* [alpha,beta] = extreme Ritz values of
+                                 lanczos_steps Lanczos steps on W^T A W       */
+#define PP_INTERVAL_GIVEN 1   /* [alpha,beta] taken from the options          */
+#define PP_SEED_NONE 0        /* W = I                                         */
+#define PP_SEED_JACOBI 1      /* W = diag(A)^{-1/2}; D_S^{-1/2} for S_u        */
+#define PP_FMT_AUTO 0
+#define PP_FMT_CSR 1          /* CSR kernel (row groups of lanes)              */
+#define PP_FMT_SELL 2         /* SELL-C-sigma kernel (warp per slice)          */
+#define PP_PREC_F64 0         /* p_k applied in FP64                           */
+#define PP_PREC_F32 1         /* p_k applied with FP32 values and vectors      */
+#define PP_PREC_BF16 2        /* p_k applied with BF16 values, FP32 vectors    */
+
+typedef struct pp_ctx pp_ctx; /* opaque; host memory + the caller's workspace */
+
+/* Square sparse matrix in CSR on the device: row i holds entries
+ * [rowptr[i], rowptr[i+1]) of col/val; int32 indices; the diagonal entry of
+ * every row must be present when seed_scaling = PP_SEED_JACOBI. */
+typedef struct {
+  int n;
+  long long nnz;
+  const int* rowptr; /* device, n+1 */
+  const int* col;    /* device, nnz */
+  const double* val; /* device, nnz */
+} pp_csr;
+
+typedef struct {
+  int k;              /* polynomial degree (number of products by A in P)  */
+  double xi;          /* Eq. thetamod scaling; < 0: xi = clip(10 a/b, 1e-6, 1e-2) */
+  int interval;       /* PP_INTERVAL_*                                      */
+  double alpha, beta; /* spectral interval of W^T A W when interval = GIVEN */
+  int lanczos_steps;  /* steps of the Lanczos estimate (default 10)         */
+  unsigned long long seed; /* seed of the Lanczos start vector (SplitMix64,
+                              stream 3, U[-1,1) in the caller's row order)  */
+  int seed_scaling;   /* PP_SEED_*                                          */
+  int format;         /* PP_FMT_*                                           */
+  int sell_C;         /* SELL chunk (rows per slice): 32, 64 or 128; 0 auto */
+  int sell_sigma;     /* sort window (multiple of sell_C); 0 or C: no sort  */
+  int apply_prec;     /* PP_PREC_*                                          */
+  int flexible;       /* 1: flexible CG (beta = -(z,q)/(p,q)), FCG(1)       */
+  int maxit;          /* PCG iteration limit                                */
+  double rtol;        /* stop when ||r||/||b|| <= rtol (seed-scaled system) */
+  int zero_guess;     /* 1: x is ignored on input and the solve starts at 0 */
+  int check_every;    /* PCG iterations enqueued between host convergence
+                         reads (>= 1); results do not depend on it          */
+  int use_graphs;     /* 1: replay each block of check_every iterations as
+                         one captured CUDA graph                            */
+} pp_options;
+
+typedef struct {
+  int iterations;
+  long long mvp;      /* products by the operator (Table 4 convention)     */
+  long long dots;     /* inner products, 3 per iteration (Table 4)         */
+  double rel_res;     /* recursive ||r||/||b|| of the scaled system at exit */
+  double alpha_hat, beta_hat, xi, theta_bar, delta, sigma_bar;
+  double t_solve_ms;  /* device time of the whole solve (CUDA events)      */
+  double t_apply_ms;  /* device time spent inside p_k applications         */
+  long long apply_launches; /* recurrence-step launches inside those       */
+  long long kernel_launches; /* all kernel launches the solve enqueued
+                                (including those that returned at once
+                                after convergence)                         */
+  int status;
+} pp_stats;
+
+typedef struct {
+  int n;              /* operator size                                     */
+  int format;         /* PP_FMT_CSR / PP_FMT_SELL actually used            */
+  int sell_C, sell_sigma;
+  long long nnz, nnz_padded;
+  double alpha_hat, beta_hat, xi, theta_bar, delta, sigma_bar;
+  int k, apply_prec, lanczos_steps_done;
+  double t_setup_ms;
+  int grid_blocks;    /* blocks of the persistent step kernels             */
+} pp_info;
+
+/* Fill *opt with defaults: k=20, xi=-1 (auto), Lanczos with 10 steps, seed 0,
+ * Jacobi seed, automatic format, FP64 apply, plain PCG, maxit 10000,
+ * rtol 1e-8, zero_guess 1, check_every 4, use_graphs 0. */
+void pp_options_default(pp_options* opt);
+
+/* Chebyshev coefficients (host, pure).  Section 2.2 and Eq. thetamod:
+ * theta = (beta+alpha)/2, delta = (beta-alpha)/2, theta_bar = theta (1+xi),
+ * sigma_bar = theta_bar/delta (delta kept: the xi-shift moves the interval
+ * to [theta_bar - delta, theta_bar + delta]); Eq. rhocheb: rho_0 =
+ * 1/sigma_bar, rho_j = 1/(2 sigma_bar - rho_{j-1}), j = 1..k.
+ * rho (host) has k+1 entries (may be NULL).  PP_EINVAL unless
+ * 0 < alpha < beta, xi >= 0, k >= 0. */
+int polyprec_coeffs(double alpha, double beta, double xi, int k, double* theta_bar,
+                    double* delta, double* sigma_bar, double* rho);
+
+/* Workspace bytes pcg_setup needs for A under opt (reads A->rowptr from the
+ * device to plan the SELL layout; synchronous). */
+int pp_workspace_size(const pp_csr* A, const pp_options* opt, size_t* bytes);
+
+/* Build a solver context: seed scaling (Section 3), the scaled matrix in the
+ * chosen format inside the workspace, the spectral interval (Lanczos or
+ * given), xi and the coefficients.  A may be freed after it returns.
+ * workspace: device, >= pp_workspace_size bytes, 256-byte aligned.
+ * Synchronous with respect to the host. */
+int pcg_setup(pp_ctx** ctx, const pp_csr* A, const pp_options* opt, void* workspace,
+              size_t ws_bytes, void* stream);
+
+/* z = P r for nrhs vectors (device, n x nrhs column-major), P = W p_k(A_hat)
+ * W^T by Algorithm 2: k products by A_hat, each fused with its recurrence
+ * update into one pass over the matrix.  Asynchronous. */
+int polyprec_apply(pp_ctx* ctx, const double* r, double* z, int nrhs, void* stream);
+
+/* y = A x with the operator of the context (unscaled A, or S_u for a Schur
+ * context), nrhs columns.  Asynchronous. */
+int pp_operator_apply(pp_ctx* ctx, const double* x, double* y, int nrhs, void* stream);
+
+/* Solve A x = b (or S_u u = r for a Schur context) by PCG (Section 1) with
+ * P = W p_k(A_hat) W^T: standard Hestenes-Stiefel PCG on the seed-scaled
+ * system, 1 + k operator products and 3 inner products per iteration, stop
+ * when ||r_hat||/||b_hat|| <= rtol.  b, x: device, n.  x is read as the
+ * initial guess unless zero_guess.  stats: host, may be NULL.  Returns
+ * PP_OK, PP_MAXIT, PP_EBREAKDOWN or PP_ENONFINITE (x holds the last
+ * iterate).  Synchronous with respect to the host. */
+int pcg_solve(pp_ctx* ctx, const double* b, double* x, pp_stats* stats, void* stream);
+
+/* Context facts (host struct). */
+int pp_get_info(const pp_ctx* ctx, pp_info* info);
+
+/* Release the context (host memory only; the workspace stays the caller's). */
+int pp_destroy(pp_ctx* ctx);
+
+/* Last error message of ctx (or of the calling thread when ctx is NULL). */
+const char* pp_last_error(const pp_ctx* ctx);
+
+/* ---- fracture-network Schur complement (Section 4.2) ------------------- */
+
+/* Blocks of the saddle-point system Eq. sys.  A is block diagonal with
+ * A_f = T[f] * (2-D 5-point Laplacian, Dirichlet on all four sides) on an
+ * nx[f] x ny[f] grid of interior nodes (x fastest), unknowns
+ * [offset[f], offset[f+1]); the fast exact solver used for A_f^{-1}
+ * requires this uniform rectangular form.  C, B: n_h x n_u CSR; CT, BT:
+ * their transposes (n_u x n_h); Gh: n_h x n_h; Gu: n_u x n_u.  nx, ny, T,
+ * offset are host arrays; all CSR arrays are device arrays that must stay
+ * valid until pp_destroy. */
+typedef struct {
+  int n_f, n_h, n_u;
+  const int* nx;            /* host, n_f */
+  const int* ny;            /* host, n_f */
+  const double* T;          /* host, n_f */
+  const long long* offset;  /* host, n_f + 1 */
+  const int *C_rowptr, *C_col; const double* C_val;
+  const int *B_rowptr, *B_col; const double* B_val;
+  const int *CT_rowptr, *CT_col; const double* CT_val;
+  const int *BT_rowptr, *BT_col; const double* BT_val;
+  const int *Gh_rowptr, *Gh_col; const double* Gh_val;
+  const int *Gu_rowptr, *Gu_col; const double* Gu_val;
+  double alpha_reg;         /* regularisation parameter alpha of Eq. func_psi */
+} pp_dfn;
+
+int pp_schur_workspace_size(const pp_dfn* d, const pp_options* opt, size_t* bytes);
+
+/* Schur context: D_S = diag(S_u) by Algorithm 4 (restricted to the trace
+ * rows that C, B and G^h touch), the scaling S_hat = D_S^{-1/2} S_u
+ * D_S^{-1/2}, the Lanczos interval of S_hat and the coefficients.
+ * Synchronous. */
+int schur_setup(pp_ctx** ctx, const pp_dfn* d, const pp_options* opt, void* workspace,
+                size_t ws_bytes, void* stream);
+
+/* y = S_u r (Algorithm 3; r, y device n_u; unscaled).  Asynchronous. */
+int schur_apply(pp_ctx* ctx, const double* r, double* y, void* stream);
+
+/* ds (device, n_u) = diag(S_u) computed at setup (Algorithm 4). */
+int schur_diag(pp_ctx* ctx, double* ds, void* stream);
+
+/* Right-hand side of Eq. schur: r = W^T M^{-1} [q; 0] =
+ * alpha B^T A^{-1} q - C^T A^{-1} G^h A^{-1} q (q device n_h, r device n_u). */
+int schur_rhs(pp_ctx* ctx, const double* q, double* r, void* stream);
+
+/* Recovery of h and p from u (Section 4.2): h = A^{-1}(q + C u),
+ * p = A^{-1}(alpha B u - G^h h).  Device arrays. */
+int schur_recover(pp_ctx* ctx, const double* q, const double* u, double* h, double* p,
+                  void* stream);
+
+/* y = A^{-1} v for the block-diagonal fracture matrix (device, n_h). */
+int schur_ainv(pp_ctx* ctx, const double* v, double* y, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLYPREC_H */

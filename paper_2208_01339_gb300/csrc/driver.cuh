@@ -1,0 +1,81 @@
+// Host-side driver state shared by the C-ABI translation units (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/polyprec.h"
+#include "kernels.cuh"
+
+namespace pp {
+
+constexpr int kMaxGrid = 152 * 16;   // upper bound on blocks of any reducing kernel
+constexpr int kMaxCheck = 64;        // upper bound on iterations per host check
+
+struct SellPlan {
+  int C = 32, sigma = 32;
+  long long nslices = 0, n_pad = 0, nnz_pad = 0;
+  bool has_perm = false;
+  std::vector<long long> sptr;
+  std::vector<int> perm;
+};
+
+struct SchurImpl;  // schur.cu
+
+int fail(pp_ctx* c, int code, const std::string& msg);
+int cuda_fail(pp_ctx* c, cudaError_t e, const char* where);
+double auto_xi(double a, double b);
+void tridiag_extremes_jacobi(const std::vector<double>& a, const std::vector<double>& b, double* lmin,
+                             double* lmax);
+int validate_options(pp_ctx* c, const pp_options* o);
+int num_sms();
+
+// solve.cu
+int setup_interval_and_coeffs(pp_ctx* c, cudaStream_t s);
+cudaError_t op_step(pp_ctx* c, bool apply_matrix, const StepParams& p, const Scalars* skip, unsigned int* counter,
+                    cudaStream_t s);
+void destroy_ctx_resources(pp_ctx* c);
+
+// schur.cu
+cudaError_t schur_scaled_step(pp_ctx* c, const StepParams& p, const Scalars* skip, unsigned int* counter,
+                              cudaStream_t s);
+void schur_free(SchurImpl* s);
+
+}  // namespace pp
+
+struct pp_ctx {
+  int kind = 0;  // 0: sparse matrix, 1: fracture-network Schur complement
+  pp_options opt{};
+  int n = 0;
+  long long n_pad = 0, nnz = 0, nnz_pad = 0;
+  pp::MatDesc A64{};  // seed-scaled operator in FP64 (outer products, FP64 apply)
+  pp::MatDesc Ap{};   // same layout in the apply precision
+  bool mixed = false;
+  void* mixed_val = nullptr;
+  double* w = nullptr;  // internal seed weights (W, or D_S^{-1/2})
+  int* perm = nullptr;  // internal row i = caller row perm[i] (SELL sorting)
+  int* iperm = nullptr;
+  double *xh = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *t1 = nullptr, *t2 = nullptr,
+         *bh = nullptr;
+  float *r32 = nullptr, *u32 = nullptr, *v32 = nullptr, *z32 = nullptr;
+  void* vec_begin = nullptr;
+  void* vec_end = nullptr;
+  pp::Scalars* sc = nullptr;
+  double* partials = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int num_sms = 152, grid_step = 1, grid_vec = 1;
+  double alpha_hat = 0, beta_hat = 0, xi = 0, theta_bar = 0, delta = 0, sigma_bar = 0;
+  std::vector<double> rho;
+  int lanczos_steps_done = 0;
+  double t_setup_ms = 0;
+  std::string err;
+  std::vector<cudaEvent_t> events;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_block = 0;
+  pp::SchurImpl* schur = nullptr;
+  int op_launches = 1;  // kernel launches per operator step (1 for a matrix)
+};

@@ -1,0 +1,116 @@
+// Internal launch interface between the C-ABI driver (api.cu) and the
+// kernel translation units.  Nothing here is exported from the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace pp {
+
+enum Prec { kF64 = 0, kF32 = 1, kBF16 = 2 };
+
+// One fused pass of a degree step (or a plain product) over the matrix:
+//   kSpmv    y = A x
+//   kResid   y = r - A x
+//   kCheb1   y = ca (2 r - ce (A r))                   (Algorithm 2, step 3; x = r)
+//   kCheb2   y = ca (cb x - cc ce r + cd (r - A x))    (first loop pass, x_old = r/theta)
+//   kChebK   y = ca (cb x - cc x_old + cd (r - A x))   (Algorithm 2 loop body)
+//   kLanczos y = A x - sqrt(*dev_coef) x_old           (Lanczos three-term step)
+// Optional fused inner products (ndot = 0, 1 or 2), written by the last block:
+//   kSpmv: (x, y)   kResid: (y, y), (r, r)   kCheb*: (r, y), (aux, y)   kLanczos: (y, x)
+enum StepMode { kSpmv = 0, kResid = 1, kCheb1 = 2, kCheb2 = 3, kChebK = 4, kLanczos = 5 };
+
+struct MatDesc {
+  int format;  // 1 CSR, 2 SELL
+  int n;
+  long long n_pad;
+  // SELL-C-sigma: slice s holds rows [s*C, (s+1)*C); element j of row r of
+  // the slice sits at slice_ptr[s] + j*C + (r - s*C).
+  int C;
+  long long nslices;
+  const long long* slice_ptr;
+  const int* col;        // SELL or CSR column indices
+  const void* val;       // values in `prec`
+  const int* rowptr;     // CSR only
+  int csr_group;         // CSR: lanes per row (1, 4, 8, 32)
+  int prec;
+};
+
+struct StepParams {
+  int mode = kSpmv;
+  int ndot = 0;
+  const void* x = nullptr;
+  const void* xold = nullptr;
+  const void* r = nullptr;
+  void* y = nullptr;
+  const double* aux = nullptr;
+  const double* dev_coef = nullptr;
+  double ca = 0, cb = 0, cc = 0, cd = 0, ce = 0;
+  double* dot_out0 = nullptr;
+  double* dot_out1 = nullptr;
+};
+
+// Launchers (step.cu).  grid = number of blocks (persistent, grid-stride);
+// partials must hold 2*grid doubles.
+cudaError_t launch_step(const MatDesc& A, const StepParams& p, const Scalars* sc, double* partials,
+                        unsigned int* counter, int grid, cudaStream_t s);
+int step_max_blocks_per_sm(const MatDesc& A, int mode, int ndot);
+
+// Vector kernels (vec.cu).  All use grid-stride loops over a fixed grid.
+struct VecLaunch {
+  int grid;
+  double* partials;
+  cudaStream_t s;
+};
+// out[i] = w[i] * in[perm ? perm[i] : i] (i < n), 0 for n <= i < n_pad; out FP64 or FP32.
+// Optional ||out||^2 -> *dot_out.
+cudaError_t vec_scale_in(const VecLaunch& L, long long n, long long n_pad, const double* w, const int* perm,
+                         const double* in, void* out, int out_prec, double* dot_out, unsigned int* counter);
+// out[perm ? perm[i] : i] = w[i] * in[i] (divide = 0) or in[i] / w[i] (divide = 1); in FP64 or FP32.
+cudaError_t vec_scale_out(const VecLaunch& L, long long n, const double* w, const int* perm, const void* in,
+                          int in_prec, double* out, int divide);
+// xh[i] = x[perm ? perm[i] : i] / w[i]
+cudaError_t vec_unscale_in(const VecLaunch& L, long long n, long long n_pad, const double* w, const int* perm,
+                           const double* x, double* xh);
+// PCG updates (device scalars in sc).
+cudaError_t vec_update_xr(const VecLaunch& L, long long n, Scalars* sc, double* x, double* r, const double* p,
+                          const double* q);
+cudaError_t vec_update_p(const VecLaunch& L, long long n, Scalars* sc, const double* z, double* p, int first);
+cudaError_t pcg_init(Scalars* sc, double rtol, int maxit, int flexible, cudaStream_t s);
+// z = double(z32); (r, z) -> sc->rz_new, (q, z) -> sc->zq when q != nullptr.
+cudaError_t vec_from32_dot(const VecLaunch& L, long long n, const Scalars* skip, const float* z32, double* z,
+                           const double* r, const double* q, double* rz_out, double* zq_out, unsigned int* counter);
+// z = r * inv_theta (degree 0), optional dots as above; prec of r/z FP64 or FP32.
+cudaError_t vec_scale_dot(const VecLaunch& L, long long n, const Scalars* skip, const void* r, void* z, int prec,
+                          double inv_theta, const double* rd, const double* q, double* rz_out, double* zq_out,
+                          unsigned int* counter);
+cudaError_t vec_convert(const VecLaunch& L, long long n, const void* in, int in_prec, void* out, int out_prec,
+                        const Scalars* skip = nullptr);
+// Lanczos helpers.
+cudaError_t lanczos_start(const VecLaunch& L, long long n, long long n_pad, uint64_t key, const int* perm,
+                          double* v, double* nrm2_out, unsigned int* counter);
+cudaError_t vec_scale_by_rsqrt(const VecLaunch& L, long long n, double* v, const double* nrm2);
+// w -= a v, ||w||^2 -> b2_out
+cudaError_t lanczos_orth(const VecLaunch& L, long long n, double* w, const double* v, const double* a,
+                         double* b2_out, unsigned int* counter);
+cudaError_t vec_dot(const VecLaunch& L, long long n, const double* x, const double* y, double* out,
+                    unsigned int* counter);
+cudaError_t vec_axpby(const VecLaunch& L, long long n, double a, const double* x, double b, double* y);
+// w_int[i] = w_orig ? w_orig[perm ? perm[i] : i] : 1 for i < n, 1 on the padding.
+cudaError_t gather_weights(const VecLaunch& L, long long n, long long n_pad, const double* w_orig, const int* perm,
+                           double* w_int);
+
+// Setup kernels (setup.cu).
+cudaError_t csr_jacobi_weights(int n, const int* rowptr, const int* col, const double* val, double* w,
+                               int* bad_row, cudaStream_t s);
+cudaError_t sell_fill(const MatDesc& dst, const int* perm, const int* iperm, const int* rowptr, const int* col,
+                      const double* val, const double* w, void* out_val, int out_prec, cudaStream_t s);
+cudaError_t csr_fill(int n, const int* rowptr, const int* col, const double* val, const double* w, int* out_rowptr,
+                     int* out_col, void* out_val, int out_prec, long long nnz, cudaStream_t s);
+cudaError_t sell_convert_values(long long nnz_pad, const double* in, void* out, int out_prec, cudaStream_t s);
+
+}  // namespace pp

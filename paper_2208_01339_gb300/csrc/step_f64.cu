@@ -1,0 +1,23 @@
+// FP64 instantiations of the fused step kernels (see step_impl.cuh).
+#include "step_impl.cuh"
+
+namespace pp {
+
+cudaError_t launch_step_f64(const MatDesc& A, const StepParams& p, const Scalars* sc, double* partials,
+                            unsigned int* counter, int grid, cudaStream_t s) {
+  return dispatch_mode<double, double>(A, p, sc, partials, counter, grid, s);
+}
+
+int step_blocks_per_sm_f64(const MatDesc& A) {
+  int nb = 0;
+  cudaError_t e;
+  if (A.format == 2 && A.C == 64)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sell_step_kernel<double, double, 2, kChebK, 0>, kBlock, 0);
+  else if (A.format == 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sell_step_kernel<double, double, 1, kChebK, 0>, kBlock, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, csr_step_kernel<double, double, 8, kChebK, 0>, kBlock, 0);
+  return (e == cudaSuccess && nb > 0) ? nb : 4;
+}
+
+}  // namespace pp

@@ -1,0 +1,337 @@
+"""Python binding of libpolyprec (argument marshalling only).
+
+Every step of the method runs inside the CUDA library declared in
+include/polyprec.h; this module passes device pointers (PyTorch tensors),
+sizes and the current CUDA stream through ctypes.  There is no CPU or
+PyTorch fallback: if the library is missing, importing ``lib()`` raises.
+
+Entry points mirror the C ABI: ``polyprec_coeffs``, ``Solver`` (pcg_setup /
+polyprec_apply / pp_operator_apply / pcg_solve / pp_destroy) and
+``SchurSolver`` (schur_setup / schur_apply / schur_diag / schur_rhs /
+schur_recover / pcg_solve).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpolyprec.so")
+
+PP_OK, PP_MAXIT, PP_EINVAL, PP_EBREAKDOWN, PP_ENONFINITE, PP_ECUDA, PP_ETIMEOUT, PP_EUNSUPPORTED = 0, 1, -1, -2, -3, -4, -5, -6
+INTERVAL = {"lanczos": 0, "given": 1}
+FORMAT = {"auto": 0, "csr": 1, "sell": 2}
+PREC = {"f64": 0, "f32": 1, "bf16": 2}
+SEED = {"none": 0, "jacobi": 1}
+
+_vp = ctypes.c_void_p
+
+
+class PolyPrecError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libpolyprec status {status}: {msg}")
+        self.status = status
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nnz", ctypes.c_longlong), ("rowptr", _vp), ("col", _vp), ("val", _vp)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("xi", ctypes.c_double), ("interval", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("lanczos_steps", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("seed_scaling", ctypes.c_int), ("format", ctypes.c_int),
+                ("sell_C", ctypes.c_int), ("sell_sigma", ctypes.c_int), ("apply_prec", ctypes.c_int),
+                ("flexible", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("zero_guess", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("mvp", ctypes.c_longlong), ("dots", ctypes.c_longlong),
+                ("rel_res", ctypes.c_double), ("alpha_hat", ctypes.c_double), ("beta_hat", ctypes.c_double),
+                ("xi", ctypes.c_double), ("theta_bar", ctypes.c_double), ("delta", ctypes.c_double),
+                ("sigma_bar", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("t_apply_ms", ctypes.c_double),
+                ("apply_launches", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("format", ctypes.c_int), ("sell_C", ctypes.c_int), ("sell_sigma", ctypes.c_int),
+                ("nnz", ctypes.c_longlong), ("nnz_padded", ctypes.c_longlong), ("alpha_hat", ctypes.c_double),
+                ("beta_hat", ctypes.c_double), ("xi", ctypes.c_double), ("theta_bar", ctypes.c_double),
+                ("delta", ctypes.c_double), ("sigma_bar", ctypes.c_double), ("k", ctypes.c_int),
+                ("apply_prec", ctypes.c_int), ("lanczos_steps_done", ctypes.c_int), ("t_setup_ms", ctypes.c_double),
+                ("grid_blocks", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_DFN_MATS = ("C", "B", "CT", "BT", "Gh", "Gu")
+
+
+class Dfn(ctypes.Structure):
+    _fields_ = [("n_f", ctypes.c_int), ("n_h", ctypes.c_int), ("n_u", ctypes.c_int), ("nx", _vp), ("ny", _vp),
+                ("T", _vp), ("offset", _vp)] + [
+        (f"{m}_{p}", _vp) for m in _DFN_MATS for p in ("rowptr", "col", "val")] + [("alpha_reg", ctypes.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported function of include/polyprec.h
+SIGNATURES = [
+    ("pp_options_default", None, [ctypes.POINTER(Options)]),
+    ("polyprec_coeffs", ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    ("pp_workspace_size", ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_size_t)]),
+    ("pcg_setup", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(Csr), ctypes.POINTER(Options), _vp,
+                                 ctypes.c_size_t, _vp]),
+    ("polyprec_apply", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    ("pp_operator_apply", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    ("pcg_solve", ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(Stats), _vp]),
+    ("pp_get_info", ctypes.c_int, [_vp, ctypes.POINTER(Info)]),
+    ("pp_destroy", ctypes.c_int, [_vp]),
+    ("pp_last_error", ctypes.c_char_p, [_vp]),
+    ("pp_schur_workspace_size", ctypes.c_int, [ctypes.POINTER(Dfn), ctypes.POINTER(Options),
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    ("schur_setup", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(Dfn), ctypes.POINTER(Options), _vp,
+                                   ctypes.c_size_t, _vp]),
+    ("schur_apply", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("schur_diag", ctypes.c_int, [_vp, _vp, _vp]),
+    ("schur_rhs", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("schur_recover", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("schur_ainv", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+]
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree libpolyprec.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpolyprec.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _err(ctx=None) -> str:
+    m = lib().pp_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def _check(rc: int, ctx=None, allow=(PP_OK,)) -> int:
+    if rc not in allow:
+        raise PolyPrecError(rc, _err(ctx))
+    return rc
+
+
+def polyprec_coeffs(alpha: float, beta: float, xi: float, k: int):
+    """(theta_bar, delta, sigma_bar, rho[0..k]) -- host-side coefficient table."""
+    tb, d, sb = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rho = np.zeros(k + 1)
+    rc = lib().polyprec_coeffs(alpha, beta, xi, k, ctypes.byref(tb), ctypes.byref(d), ctypes.byref(sb),
+                               rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    _check(rc)
+    return tb.value, d.value, sb.value, rho
+
+
+def make_options(**kw) -> Options:
+    o = Options()
+    lib().pp_options_default(ctypes.byref(o))
+    for key, v in kw.items():
+        if key == "interval":
+            v = INTERVAL[v] if isinstance(v, str) else v
+        elif key == "format":
+            v = FORMAT[v] if isinstance(v, str) else v
+        elif key == "apply_prec":
+            v = PREC[v] if isinstance(v, str) else v
+        elif key == "seed_scaling":
+            v = SEED[v] if isinstance(v, str) else (1 if v is True else (0 if v is False else v))
+        elif isinstance(v, bool):
+            v = int(v)
+        if not hasattr(o, key):
+            raise KeyError(f"unknown option {key}")
+        setattr(o, key, v)
+    return o
+
+
+def _torch():
+    import torch  # noqa: PLC0415  (device memory and streams only)
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _ptr(t) -> _vp:
+    return _vp(t.data_ptr())
+
+
+def to_device_csr(A, device="cuda"):
+    """Upload a host CSR (rowptr/col int32, val float64) to device tensors."""
+    torch = _torch()
+    rp = torch.as_tensor(np.ascontiguousarray(A.rowptr, dtype=np.int32), device=device)
+    ci = torch.as_tensor(np.ascontiguousarray(A.col, dtype=np.int32), device=device)
+    va = torch.as_tensor(np.ascontiguousarray(A.val, dtype=np.float64), device=device)
+    return rp, ci, va
+
+
+class Solver:
+    """PCG with P = W p_k(W^T A W) W^T on one sparse SPD matrix (device CSR)."""
+
+    def __init__(self, rowptr, col, val, n: int, stream=None, **options):
+        torch = _torch()
+        self.n = int(n)
+        self.opts = make_options(**options)
+        self._keep = (rowptr, col, val)
+        csr = Csr(self.n, int(val.numel()), _ptr(rowptr), _ptr(col), _ptr(val))
+        nbytes = ctypes.c_size_t()
+        _check(lib().pp_workspace_size(ctypes.byref(csr), ctypes.byref(self.opts), ctypes.byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=val.device)
+        ctx = _vp()
+        s = _stream(stream)
+        _check(lib().pcg_setup(ctypes.byref(ctx), ctypes.byref(csr), ctypes.byref(self.opts),
+                               _ptr(self.workspace), self.workspace.numel(), s))
+        self.ctx = ctx
+        self.device = val.device
+
+    @classmethod
+    def from_host(cls, A, device="cuda", **options):
+        rp, ci, va = to_device_csr(A, device)
+        return cls(rp, ci, va, A.n, **options)
+
+    def info(self) -> dict:
+        i = Info()
+        _check(lib().pp_get_info(self.ctx, ctypes.byref(i)), self.ctx)
+        return i.as_dict()
+
+    def apply(self, r, z=None, stream=None):
+        """z = P r; r is (n,) or (nrhs, n) FP64 on the device."""
+        torch = _torch()
+        r = r.contiguous()
+        nrhs = 1 if r.dim() == 1 else r.shape[0]
+        if z is None:
+            z = torch.empty_like(r)
+        _check(lib().polyprec_apply(self.ctx, _ptr(r), _ptr(z), nrhs, _stream(stream)), self.ctx)
+        return z
+
+    def operator(self, x, y=None, stream=None):
+        torch = _torch()
+        x = x.contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().pp_operator_apply(self.ctx, _ptr(x), _ptr(y), nrhs, _stream(stream)), self.ctx)
+        return y
+
+    def solve(self, b, x=None, stream=None, allow=(PP_OK, PP_MAXIT)):
+        """Solve A x = b; returns (x, stats dict).  Statuses outside `allow` raise."""
+        torch = _torch()
+        if x is None:
+            x = torch.zeros_like(b)
+        st = Stats()
+        rc = lib().pcg_solve(self.ctx, _ptr(b), _ptr(x), ctypes.byref(st), _stream(stream))
+        _check(rc, self.ctx, allow)
+        d = st.as_dict()
+        d["status"] = rc
+        return x, d
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().pp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SchurSolver(Solver):
+    """PCG on the D_S-scaled Schur complement S_u of a fracture network."""
+
+    def __init__(self, net, device="cuda", stream=None, **options):  # noqa: D401
+        torch = _torch()
+        self.n = int(net.n_u)
+        self.opts = make_options(**options)
+        keep = []
+
+        def dev(a, dt):
+            t = torch.as_tensor(np.ascontiguousarray(a, dtype=dt), device=device)
+            keep.append(t)
+            return _ptr(t)
+
+        def host(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return _vp(a.ctypes.data)
+
+        d = Dfn()
+        d.n_f, d.n_h, d.n_u = net.n_f, net.n_h, net.n_u
+        d.nx = host(net.nx, np.int32)
+        d.ny = host(net.ny, np.int32)
+        d.T = host(net.T, np.float64)
+        d.offset = host(net.offset, np.int64)
+        for m in _DFN_MATS:
+            M = getattr(net, m)
+            setattr(d, f"{m}_rowptr", dev(M.rowptr, np.int32))
+            setattr(d, f"{m}_col", dev(M.col, np.int32))
+            setattr(d, f"{m}_val", dev(M.val, np.float64))
+        d.alpha_reg = float(net.alpha)
+        self._keep = keep
+        self._dfn = d
+        nbytes = ctypes.c_size_t()
+        _check(lib().pp_schur_workspace_size(ctypes.byref(d), ctypes.byref(self.opts), ctypes.byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=device)
+        ctx = _vp()
+        _check(lib().schur_setup(ctypes.byref(ctx), ctypes.byref(d), ctypes.byref(self.opts), _ptr(self.workspace),
+                                 self.workspace.numel(), _stream(stream)))
+        self.ctx = ctx
+        self.n_h = int(net.n_h)
+        self.device = torch.device(device)
+
+    def schur_apply(self, r, y=None, stream=None):
+        torch = _torch()
+        y = torch.empty_like(r) if y is None else y
+        _check(lib().schur_apply(self.ctx, _ptr(r), _ptr(y), _stream(stream)), self.ctx)
+        return y
+
+    def diag(self, stream=None):
+        torch = _torch()
+        ds = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        _check(lib().schur_diag(self.ctx, _ptr(ds), _stream(stream)), self.ctx)
+        return ds
+
+    def rhs(self, q, stream=None):
+        torch = _torch()
+        r = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        _check(lib().schur_rhs(self.ctx, _ptr(q), _ptr(r), _stream(stream)), self.ctx)
+        return r
+
+    def recover(self, q, u, stream=None):
+        torch = _torch()
+        h = torch.empty(self.n_h, dtype=torch.float64, device=self.device)
+        p = torch.empty(self.n_h, dtype=torch.float64, device=self.device)
+        _check(lib().schur_recover(self.ctx, _ptr(q), _ptr(u), _ptr(h), _ptr(p), _stream(stream)), self.ctx)
+        return h, p
+
+    def ainv(self, v, stream=None):
+        torch = _torch()
+        y = torch.empty_like(v)
+        _check(lib().schur_ainv(self.ctx, _ptr(v), _ptr(y), _stream(stream)), self.ctx)
+        return y

@@ -1,0 +1,124 @@
+"""GPU parity of polyprec_apply (Algorithm 2), the Lanczos interval and the
+operator product against the FP64 CPU oracle, through the C ABI.
+
+Tolerance: FP64 apply, relative 2-norm error <= 1e-12 (k fused steps of a
+stable three-term recurrence; the GPU and the oracle differ only in the
+rounding order of each row sum and in FMA contraction).
+"""
+import numpy as np
+import pytest
+
+from helpers import oracle_apply, oracle_interval, rel, to_np
+from paper_2208_01339_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2208_01339_gb300.polyprec")
+
+APPLY_TOL = 1e-12
+
+MATS = {
+    "poisson5": lambda: I.poisson3d(5),
+    "diff11": lambda: I.diffusion3d(11, 2.0, seed=1),
+    "diff23": lambda: I.diffusion3d(23, 1.0, seed=3),
+}
+LAYOUTS = [
+    dict(format="csr"),
+    dict(format="sell", sell_C=32),
+    dict(format="sell", sell_C=64),
+    dict(format="sell", sell_C=64, sell_sigma=256),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("mat", list(MATS))
+@pytest.mark.parametrize("layout", range(len(LAYOUTS)))
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 8, 25])
+def test_apply_matches_oracle(mat, layout, k):
+    A = MATS[mat]()
+    alpha, beta, xi = 0.05, 1.95, 1e-3
+    S = P.Solver.from_host(A, k=k, interval="given", alpha=alpha, beta=beta, xi=xi, **LAYOUTS[layout])
+    r = I.rhs_normal(A.n, 7)
+    z = S.apply(torch.as_tensor(r, device="cuda"))
+    torch.cuda.synchronize()
+    ref = oracle_apply(A, r, alpha, beta, xi, k)
+    assert rel(to_np(z), ref) <= APPLY_TOL
+
+
+@pytest.mark.parametrize("layout", range(len(LAYOUTS)))
+def test_apply_without_seed_scaling(layout):
+    A = I.diffusion3d(9, 0.5, seed=2)
+    S = P.Solver.from_host(A, k=5, interval="given", alpha=0.5, beta=14.0, xi=0.0, seed_scaling=False,
+                           **LAYOUTS[layout])
+    r = I.rhs_normal(A.n, 1)
+    z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
+    assert rel(z, oracle_apply(A, r, 0.5, 14.0, 0.0, 5, seed_scaling=False)) <= APPLY_TOL
+
+
+def test_apply_multiple_rhs():
+    A = I.diffusion3d(10, 1.0, seed=4)
+    S = P.Solver.from_host(A, k=6, interval="given", alpha=0.1, beta=1.9, xi=1e-3, format="sell")
+    R = np.stack([I.rhs_normal(A.n, s) for s in range(3)])
+    Z = to_np(S.apply(torch.as_tensor(R, device="cuda")))
+    for j in range(3):
+        assert rel(Z[j], oracle_apply(A, R[j], 0.1, 1.9, 1e-3, 6)) <= APPLY_TOL
+
+
+@pytest.mark.parametrize("layout", range(len(LAYOUTS)))
+@pytest.mark.parametrize("steps", [10, 30])
+def test_lanczos_interval_matches_oracle(layout, steps):
+    A = I.diffusion3d(12, 2.0, seed=1)
+    S = P.Solver.from_host(A, k=4, lanczos_steps=steps, seed=5, **LAYOUTS[layout])
+    info = S.info()
+    lo, hi = oracle_interval(A, 5, steps)
+    assert info["lanczos_steps_done"] == steps
+    assert info["alpha_hat"] == pytest.approx(lo, rel=1e-9)
+    assert info["beta_hat"] == pytest.approx(hi, rel=1e-9)
+    assert info["xi"] == pytest.approx(min(max(10 * lo / hi, 1e-6), 1e-2), rel=1e-12)
+
+
+def test_lanczos_start_vector_bits():
+    """The device SplitMix64 stream equals the shared generator bit for bit:
+    with n Lanczos steps on a tiny diagonal matrix the Ritz values are exact,
+    and the first step's alpha_1 = v^T A v / v^T v depends on every bit."""
+    A = I.diagonal(50)
+    S = P.Solver.from_host(A, k=1, lanczos_steps=1, seed=11, seed_scaling=False)
+    v = I.lanczos_start(50, 11)
+    a1 = float(v @ (np.arange(1, 51) * v) / (v @ v))
+    assert S.info()["alpha_hat"] == pytest.approx(a1, rel=1e-14)
+
+
+@pytest.mark.parametrize("layout", range(len(LAYOUTS)))
+def test_operator_product(layout):
+    A = I.diffusion3d(13, 2.0, seed=3)
+    S = P.Solver.from_host(A, k=2, **LAYOUTS[layout])
+    x = I.rhs_normal(A.n, 3)
+    y = to_np(S.operator(torch.as_tensor(x, device="cuda")))
+    assert rel(y, A.matvec(x)) <= 1e-13
+
+
+def test_ragged_sizes_and_tiny():
+    for n in (1, 2, 63, 65, 127, 129):
+        A = I.diagonal(n)
+        for fmt in ("csr", "sell"):
+            S = P.Solver.from_host(A, k=3, interval="given", alpha=1.0, beta=float(n) + 1.0, xi=0.0,
+                                   seed_scaling=False, format=fmt)
+            r = I.rhs_uniform(n, 2)
+            z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
+            assert rel(z, oracle_apply(A, r, 1.0, float(n) + 1.0, 0.0, 3, seed_scaling=False)) <= APPLY_TOL
+
+
+def test_invalid_setup_reports_error():
+    A = I.poisson3d(3)
+    with pytest.raises(P.PolyPrecError) as ei:
+        P.Solver.from_host(A, k=3, interval="given", alpha=2.0, beta=1.0)
+    assert ei.value.status == P.PP_EINVAL
+    B = I.dense_to_csr(np.diag([1.0, -1.0, 2.0]))
+    with pytest.raises(P.PolyPrecError):
+        P.Solver.from_host(B, k=3)
