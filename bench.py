@@ -34,6 +34,7 @@ WORKLOADS = {
                              flexible=1),
     "diffusion192_bf16": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=20, lanczos=10, fmt="sell", prec="bf16",
                               flexible=1),
+    "diffusion128": dict(N=128, sigma=2.0, seed=1, rhs="normal", k=20, lanczos=10, fmt="sell", prec="f64"),
     "poisson32": dict(N=32, sigma=0.0, seed=0, rhs="ones_noise", k=20, lanczos=10, fmt="csr", prec="f64"),
 }
 METRIC = "PCG time-to-rtol-1e-8 (s) and polyprec_apply HBM GB/s vs plain FP64, 1 GB300"
