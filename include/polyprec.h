@@ -231,6 +231,32 @@ int schur_recover(pp_ctx* ctx, const double* q, const double* u, double* h, doub
 /* y = A^{-1} v for the block-diagonal fracture matrix (device, n_h). */
 int schur_ainv(pp_ctx* ctx, const double* v, double* y, void* stream);
 
+/* ---- workspace-free apply (no counterpart in the paper) ---------------- */
+
+/* z = p_k(A) r for a CSR matrix on the device, without a workspace and
+ * without allocating anything.  For callers that may not call cudaMalloc:
+ * a component running inside a host application that owns every device
+ * allocation (its device memory comes only from the host's own pool), or a
+ * latency-critical loop where the device synchronization an allocation can
+ * cause is not allowed.  The caller passes only inputs and outputs (rowptr,
+ * col, val, r: device, read; z: device, n, written); the two rotating
+ * vectors of the recurrence live in one static device array of
+ * 2 x 262,144 doubles (4 MiB) that every GPU using the library keeps until
+ * the process exits.  The polynomial is the one polyprec_apply uses with
+ * seed_scaling = PP_SEED_NONE, format = PP_FMT_CSR and a given interval:
+ * coefficients from polyprec_coeffs(alpha, beta, xi, k), k products by A.
+ * n > 262,144 returns PP_EINVAL with a message; so do other bad arguments.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on one device share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race
+ * and corrupt each other's results, so serialize them.  The array keeps
+ * the previous call's contents; every entry a call reads it writes first.
+ * Asynchronous on `stream`. */
+int polyprec_apply_csr_static(int n, long long nnz, const int* rowptr, const int* col,
+                              const double* val, double alpha, double beta, double xi, int k,
+                              const double* r, double* z, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

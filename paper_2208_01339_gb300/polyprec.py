@@ -107,6 +107,8 @@ SIGNATURES = [
     ("schur_rhs", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("schur_recover", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("schur_ainv", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("polyprec_apply_csr_static", ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp]),
 ]
 
 
@@ -188,6 +190,19 @@ def to_device_csr(A, device="cuda"):
     ci = torch.as_tensor(np.ascontiguousarray(A.col, dtype=np.int32), device=device)
     va = torch.as_tensor(np.ascontiguousarray(A.val, dtype=np.float64), device=device)
     return rp, ci, va
+
+
+def apply_csr_static(rowptr, col, val, n: int, alpha: float, beta: float, xi: float, k: int, r, z=None,
+                     stream=None):
+    """z = p_k(A) r without a workspace (polyprec_apply_csr_static): for
+    callers that cannot allocate device memory; n <= 262,144."""
+    torch = _torch()
+    if z is None:
+        z = torch.empty_like(r)
+    rc = lib().polyprec_apply_csr_static(int(n), int(val.numel()), _ptr(rowptr), _ptr(col), _ptr(val), alpha, beta,
+                                         xi, int(k), _ptr(r), _ptr(z), _stream(stream))
+    _check(rc)
+    return z
 
 
 class Solver:
