@@ -223,6 +223,9 @@ def main():
     ap.add_argument("--workload", default="diffusion192", choices=list(WORKLOADS))
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--graphs", type=int, default=0)
+    ap.add_argument("--sell-variant", type=int, default=0, help="0 auto, 1 direct loads, 2 TMA-staged")
+    ap.add_argument("--sell-C", type=int, default=0)
+    ap.add_argument("--sell-sigma", type=int, default=0)
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -253,7 +256,8 @@ def main():
     A, b = build_problem(w)
     k = args.k if args.k is not None else w["k"]
     opts = dict(k=k, lanczos_steps=w["lanczos"], format=w["fmt"], apply_prec=w["prec"], rtol=1e-8,
-                check_every=args.check_every, use_graphs=args.graphs, flexible=w.get("flexible", 0))
+                check_every=args.check_every, use_graphs=args.graphs, flexible=w.get("flexible", 0),
+                sell_variant=args.sell_variant, sell_C=args.sell_C, sell_sigma=args.sell_sigma)
     S = P.Solver.from_host(A, device=dev, **opts)
     info = S.info()
     bt = torch.as_tensor(b, device=dev)
@@ -349,7 +353,8 @@ def main():
                    "sigma_ln": w["sigma"], "format": "SELL" if info["format"] == 2 else "CSR",
                    "sell_C": info["sell_C"], "lanczos_steps": w["lanczos"], "rtol": 1e-8,
                    "l2": "inputs larger than L2 (matrix >> 129 MB)" if A.nnz * 12 > 129e6 else "L2-resident inputs",
-                   "graphs": args.graphs, "parallelism": f"replicas x{world}"},
+                   "graphs": args.graphs, "sell_variant": "direct" if args.sell_variant == 1 else "tma",
+                   "parallelism": f"replicas x{world}"},
         "iterations": int(statistics.median(it)), "setup_ms": round(info["t_setup_ms"], 2),
         "alpha_hat": info["alpha_hat"], "beta_hat": info["beta_hat"], "xi": info["xi"],
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

@@ -47,7 +47,8 @@ extern "C" {
                                not SPD (e.g. lambda_max >= 2 theta_bar)      */
 #define PP_ENONFINITE (-3)  /* NaN/Inf met in a reduction                     */
 #define PP_ECUDA (-4)       /* CUDA runtime error                             */
-#define PP_ETIMEOUT (-5)    /* bounded device wait expired                    */
+#define PP_ETIMEOUT (-5)    /* bounded device wait expired (reported by the
+                               next pcg_solve on the context)                */
 #define PP_EUNSUPPORTED (-6)/* unsupported format / precision / shape         */
 
 /* ---- enums ------------------------------------------------------------ */
@@ -97,6 +98,8 @@ typedef struct {
                          reads (>= 1); results do not depend on it          */
   int use_graphs;     /* 1: replay each block of check_every iterations as
                          one captured CUDA graph                            */
+  int sell_variant;   /* SELL kernel: 0 auto, 1 direct global loads,
+                         2 slices staged in shared memory by TMA bulk copies */
 } pp_options;
 
 typedef struct {

@@ -147,6 +147,7 @@ int validate_options(pp_ctx* c, const pp_options* o) {
   if (!(o->rtol >= 0.0)) return fail(c, PP_EINVAL, "rtol must be >= 0");
   if (o->check_every < 0 || o->check_every > kMaxCheck) return fail(c, PP_EINVAL, "check_every must be in [0, 64]");
   if (o->sell_sigma < 0) return fail(c, PP_EINVAL, "sell_sigma must be >= 0");
+  if (o->sell_variant < 0 || o->sell_variant > 2) return fail(c, PP_EINVAL, "sell_variant must be 0, 1 or 2");
   return PP_OK;
 }
 
@@ -249,6 +250,7 @@ void init_desc(pp_ctx* c, const pp_csr* A, const SellPlan& P) {
   if (c->A64.format == PP_FMT_SELL) {
     c->A64.C = P.C;
     c->A64.nslices = P.nslices;
+    c->A64.tma = c->opt.sell_variant != 1;
     c->n_pad = P.n_pad;
     c->nnz_pad = P.nnz_pad;
   } else {

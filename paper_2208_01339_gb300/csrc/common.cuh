@@ -30,7 +30,8 @@ struct Scalars {
   int maxit;
   int flexible;
   int lan_steps;   // Lanczos steps completed without breakdown
-  int pad_[2];
+  int dev_error;   // 1: a bounded wait inside a kernel expired (PP_ETIMEOUT)
+  int pad_;
   unsigned int counters[8];
   double lan_a[kMaxLanczos];
   double lan_b2[kMaxLanczos];

@@ -28,16 +28,17 @@ struct MatDesc {
   int format;  // 1 CSR, 2 SELL
   int n;
   long long n_pad;
-  // SELL-C-sigma: slice s holds rows [s*C, (s+1)*C); element j of row r of
-  // the slice sits at slice_ptr[s] + j*C + (r - s*C).
+  // SELL-C-sigma: slice s holds rows [s*C, (s+1)*C), C = 32*VW; entry j of
+  // row s*C + e*32 + l (lane l, e < VW) sits at slice_ptr[s] + j*C + l*VW + e.
   int C;
   long long nslices;
   const long long* slice_ptr;
   const int* col;        // SELL or CSR column indices
   const void* val;       // values in `prec`
   const int* rowptr;     // CSR only
-  int csr_group;         // CSR: lanes per row (1, 4, 8, 32)
+  int csr_group;         // CSR: lanes per row (1, 8, 32)
   int prec;
+  int tma;               // SELL: stage slices through shared memory with cp.async.bulk
 };
 
 struct StepParams {
@@ -52,6 +53,7 @@ struct StepParams {
   double ca = 0, cb = 0, cc = 0, cd = 0, ce = 0;
   double* dot_out0 = nullptr;
   double* dot_out1 = nullptr;
+  int* err = nullptr;  // set to 1 when a bounded device wait expires
 };
 
 // Launchers (step.cu).  grid = number of blocks (persistent, grid-stride);

@@ -32,9 +32,9 @@ __device__ __forceinline__ float to_val<float>(double v) { return (float)v; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_val<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 
-// One thread per internal row (padding rows included).  Element j of the
-// row goes to slice_ptr[s] + j*C + l; padding entries point at the row
-// itself (or column 0 for padding rows) with value 0.
+// One thread per internal row (padding rows included).  Row s*C + e*32 + l
+// puts entry j at slice_ptr[s] + j*C + l*VW + e (VW = C/32); padding entries
+// point at the row itself (or column 0 for padding rows) with value 0.
 template <typename TV>
 __global__ void sell_fill_kernel(int n, long long n_pad, int C, const long long* __restrict__ sptr,
                                  const int* __restrict__ perm, const int* __restrict__ iperm,
@@ -44,7 +44,9 @@ __global__ void sell_fill_kernel(int n, long long n_pad, int C, const long long*
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad;
        i += (long long)gridDim.x * blockDim.x) {
     const long long s = i / C;
-    const int l = (int)(i - s * C);
+    const int within = (int)(i - s * C);
+    const int vw = C / 32;
+    const int l = (within % 32) * vw + within / 32;  // position inside one entry column
     const long long base = sptr[s];
     const int wd = (int)((sptr[s + 1] - base) / C);
     int j = 0;

@@ -22,7 +22,9 @@ namespace pp {
 cudaError_t op_step(pp_ctx* c, bool apply_matrix, const StepParams& p, const Scalars* skip, unsigned int* counter,
                     cudaStream_t s) {
   if (c->kind == 1) return schur_scaled_step(c, p, skip, counter, s);
-  return launch_step(apply_matrix ? c->Ap : c->A64, p, skip, c->partials, counter, c->grid_step, s);
+  StepParams q = p;
+  q.err = &c->sc->dev_error;
+  return launch_step(apply_matrix ? c->Ap : c->A64, q, skip, c->partials, counter, c->grid_step, s);
 }
 
 namespace {
@@ -338,7 +340,7 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
   const long long k = c->opt.k;
   const long long pre = k == 0 ? 1 : (c->mixed ? k * c->op_launches + 2 : k * c->op_launches);
   long long launches = 1 + (c->opt.zero_guess ? 0 : 1 + c->op_launches) + 1 + pre + 1;
-  int host[4] = {0, 0, 0, 0};  // done, status, iter, maxit
+  int host[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // done, status, iter, maxit, flexible, lan_steps, dev_error, pad
   double t_apply = 0.0;
   long long applies = 0;
   bool first_block = true;
@@ -379,7 +381,7 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bb, &sc->bb, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pcg_solve finish");
-  const int status = host[1];
+  const int status = host[6] ? PP_ETIMEOUT : host[1];
   const int iters = host[2];
   if (st) {
     std::memset(st, 0, sizeof(*st));
@@ -402,7 +404,9 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
     st->status = status;
   }
   if (status < 0) {
-    const char* why = status == PP_EBREAKDOWN ? "breakdown: (p,Ap) <= 0 or (r,z) <= 0" : "non-finite value in PCG";
+    const char* why = status == PP_EBREAKDOWN   ? "breakdown: (p,Ap) <= 0 or (r,z) <= 0"
+                      : status == PP_ETIMEOUT ? "a bounded device wait expired (staged copy did not arrive)"
+                                              : "non-finite value in PCG";
     fail(c, status, why);
   }
   return status;

@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
                 ("seed", ctypes.c_ulonglong), ("seed_scaling", ctypes.c_int), ("format", ctypes.c_int),
                 ("sell_C", ctypes.c_int), ("sell_sigma", ctypes.c_int), ("apply_prec", ctypes.c_int),
                 ("flexible", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
-                ("zero_guess", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("zero_guess", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("sell_variant", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -25,10 +25,27 @@ MATS = {
 }
 LAYOUTS = [
     dict(format="csr"),
-    dict(format="sell", sell_C=32),
-    dict(format="sell", sell_C=64),
-    dict(format="sell", sell_C=64, sell_sigma=256),
+    dict(format="sell", sell_C=32, sell_variant=1),
+    dict(format="sell", sell_C=64, sell_variant=1),
+    dict(format="sell", sell_C=32, sell_variant=2),
+    dict(format="sell", sell_C=64, sell_variant=2),
+    dict(format="sell", sell_C=64, sell_sigma=256, sell_variant=1),
+    dict(format="sell", sell_C=64, sell_sigma=256, sell_variant=2),
 ]
+
+
+def width8_matrix(n=1024):
+    """SPD matrix with offsets 0, +-1, +-2, +-3 and one partner i ^ 64: eight
+    entries in interior rows (the widest slice staged through shared memory)."""
+    D = np.zeros((n, n))
+    for i in range(n):
+        for d, v in ((1, -1.0), (2, -0.5), (3, -0.25)):
+            if i + d < n:
+                D[i, i + d] = D[i + d, i] = v
+        D[i, i ^ 64] = -0.3
+    np.fill_diagonal(D, 0.0)
+    np.fill_diagonal(D, np.abs(D).sum(axis=1) + 1.0)
+    return I.dense_to_csr(D)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -59,6 +76,18 @@ def test_apply_without_seed_scaling(layout):
     r = I.rhs_normal(A.n, 1)
     z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
     assert rel(z, oracle_apply(A, r, 0.5, 14.0, 0.0, 5, seed_scaling=False)) <= APPLY_TOL
+
+
+@pytest.mark.parametrize("layout", range(len(LAYOUTS)))
+@pytest.mark.parametrize("which", ["w8", "dense60"])
+def test_apply_wide_slices(layout, which):
+    """Slices of width 8 (straight-line path) and 60 (wider than the shared
+    memory staging buffer: direct-load fallback inside the TMA kernel)."""
+    A = width8_matrix() if which == "w8" else I.dense_to_csr(I.random_spd(60, seed=3, cond=30.0))
+    S = P.Solver.from_host(A, k=6, interval="given", alpha=0.05, beta=1.95, xi=1e-3, **LAYOUTS[layout])
+    r = I.rhs_normal(A.n, 2)
+    z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
+    assert rel(z, oracle_apply(A, r, 0.05, 1.95, 1e-3, 6)) <= APPLY_TOL
 
 
 def test_apply_multiple_rhs():

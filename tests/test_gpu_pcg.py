@@ -68,12 +68,13 @@ def test_tight_solve_matches_dense():
     assert rel(xg, np.linalg.solve(A.to_dense(), b)) <= 1e-10
 
 
-@pytest.mark.parametrize("fmt,C,sigma", [("csr", 0, 0), ("sell", 32, 0), ("sell", 64, 0), ("sell", 64, 512)])
-def test_fixed_iterations_iterates(fmt, C, sigma):
+@pytest.mark.parametrize("fmt,C,sigma,var", [("csr", 0, 0, 0), ("sell", 32, 0, 1), ("sell", 64, 0, 1),
+                                             ("sell", 32, 0, 2), ("sell", 64, 0, 2), ("sell", 64, 512, 2)])
+def test_fixed_iterations_iterates(fmt, C, sigma, var):
     A = I.diffusion3d(20, 2.0, seed=1)
     b = I.rhs_normal(A.n, 1)
     opts = dict(k=12, lanczos_steps=10, rtol=0.0, maxit=3)
-    xg, sg, _ = gpu_solve(A, b, format=fmt, sell_C=C, sell_sigma=sigma, **opts)
+    xg, sg, _ = gpu_solve(A, b, format=fmt, sell_C=C, sell_sigma=sigma, sell_variant=var, **opts)
     xo, so = oracle_solve(A, b, **opts)
     assert sg["status"] == P.PP_MAXIT and so["status"] == 1
     assert sg["iterations"] == 3
