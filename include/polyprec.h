@@ -87,7 +87,7 @@ typedef struct {
                               stream 3, U[-1,1) in the caller's row order)  */
   int seed_scaling;   /* PP_SEED_*                                          */
   int format;         /* PP_FMT_*                                           */
-  int sell_C;         /* SELL chunk (rows per slice): 32, 64 or 128; 0 auto */
+  int sell_C;         /* SELL chunk (rows per slice): 32, 64 or 128; 0: 64  */
   int sell_sigma;     /* sort window (multiple of sell_C); 0 or C: no sort  */
   int apply_prec;     /* PP_PREC_*                                          */
   int flexible;       /* 1: flexible CG (beta = -(z,q)/(p,q)), FCG(1)       */

@@ -217,10 +217,7 @@ int choose_format(const pp_options& o, int n) {
 }
 
 int choose_C(const pp_options& o) {
-  int C = (o.sell_C == 32 || o.sell_C == 64 || o.sell_C == 128) ? o.sell_C : (o.apply_prec == PP_PREC_F64 ? 64 : 128);
-  // FP64 vectors use at most 16-byte loads per lane (VW <= 2).
-  if (o.apply_prec == PP_PREC_F64 && C == 128) C = 64;
-  return C;
+  return (o.sell_C == 32 || o.sell_C == 64 || o.sell_C == 128) ? o.sell_C : 64;
 }
 
 int read_rowptr(const pp_csr* A, std::vector<int>& h, cudaStream_t s, pp_ctx* c) {

@@ -12,7 +12,12 @@ int step_blocks_per_sm_f64(const MatDesc& A) {
   int nb = 0;
   cudaError_t e;
   if (A.format == 2 && A.tma) {
-    if (A.C == 64) {
+    if (A.C == 128) {
+      using S = TmaStage<double, double, 4, kChebK>;
+      auto k = sell_step_tma_kernel<double, double, 4, kChebK, 0>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBlockBytes);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, S::kBlockBytes);
+    } else if (A.C == 64) {
       using S = TmaStage<double, double, 2, kChebK>;
       auto k = sell_step_tma_kernel<double, double, 2, kChebK, 0>;
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBlockBytes);
@@ -23,6 +28,8 @@ int step_blocks_per_sm_f64(const MatDesc& A) {
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBlockBytes);
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, S::kBlockBytes);
     }
+  } else if (A.format == 2 && A.C == 128) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sell_step_kernel<double, double, 4, kChebK, 0>, kBlock, 0);
   } else if (A.format == 2 && A.C == 64) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sell_step_kernel<double, double, 2, kChebK, 0>, kBlock, 0);
   } else if (A.format == 2) {

@@ -56,6 +56,25 @@ struct ValLd<double, 2, TA> {
   }
 };
 template <typename TA>
+struct ValLd<double, 4, TA> {
+  __device__ static void ld(const double* p, TA (&o)[4]) {
+    double2 t0 = __ldcs(reinterpret_cast<const double2*>(p));
+    double2 t1 = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = (TA)t0.x;
+    o[1] = (TA)t0.y;
+    o[2] = (TA)t1.x;
+    o[3] = (TA)t1.y;
+  }
+  __device__ static void lds(const double* p, TA (&o)[4]) {
+    double2 t0 = *reinterpret_cast<const double2*>(p);
+    double2 t1 = *(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = (TA)t0.x;
+    o[1] = (TA)t0.y;
+    o[2] = (TA)t1.x;
+    o[3] = (TA)t1.y;
+  }
+};
+template <typename TA>
 struct ValLd<float, 1, TA> {
   __device__ static void ld(const float* p, TA (&o)[1]) { o[0] = (TA)__ldcs(p); }
   __device__ static void lds(const float* p, TA (&o)[1]) { o[0] = (TA)*p; }
@@ -668,9 +687,7 @@ cudaError_t dispatch_fmt(const MatDesc& A, const StepParams& p, const Scalars* s
       const int vw = A.C / 32;
       if (vw == 1) return go_sell<TV, TX, 1, MODE, NDOT>(A, p, sc, partials, cnt, grid, s);
       if (vw == 2) return go_sell<TV, TX, 2, MODE, NDOT>(A, p, sc, partials, cnt, grid, s);
-      if constexpr (!std::is_same<TX, double>::value) {
-        if (vw == 4) return go_sell<TV, TX, 4, MODE, NDOT>(A, p, sc, partials, cnt, grid, s);
-      }
+      if (vw == 4) return go_sell<TV, TX, 4, MODE, NDOT>(A, p, sc, partials, cnt, grid, s);
       return cudaErrorInvalidValue;
     }
     switch (A.csr_group) {
