@@ -37,6 +37,7 @@ WORKLOADS = {
     "diffusion128": dict(N=128, sigma=2.0, seed=1, rhs="normal", k=20, lanczos=10, fmt="sell", prec="f64"),
     "poisson32": dict(N=32, sigma=0.0, seed=0, rhs="ones_noise", k=20, lanczos=10, fmt="csr", prec="f64"),
     "dfn200": dict(dfn=True, seed=2, k=40, lanczos=10, prec="f64"),
+    "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32"),
 }
 METRIC = "PCG time-to-rtol-1e-8 (s) and polyprec_apply HBM GB/s vs plain FP64, 1 GB300"
 VAL_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
@@ -48,6 +49,9 @@ def build_problem(w):
 
     if w.get("dfn"):
         return I.fracture_network(seed=w["seed"]), None
+    if w.get("batch"):
+        specs = I.batch_specs(w["count"], seed=w["seed"], nmax=w.get("nmax", 160))
+        return specs, None
 
     if w["sigma"] == 0.0:
         A = I.poisson3d(w["N"])
@@ -218,6 +222,71 @@ def run_reference(args, w, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args, w, specs, k, dev, world, rank):
+    """Config-5 shape: many uneven instances with several RHS each, solved by
+    the batched solver (FP32 p_k, FP64 flexible CG, CUDA graphs) and, for
+    comparison, one column at a time by the plain FP64 single-instance solver."""
+    import torch
+
+    from paper_2208_01339_gb300 import inputs as I
+    from paper_2208_01339_gb300 import polyprec as P
+
+    mats = [I.batch_instance(s) for s in specs]
+    rhs = [I.batch_rhs(s) for s in specs]
+    S = P.BatchSolver(mats, [s.nrhs for s in specs], device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8,
+                      apply_prec=w["prec"], flexible=1, use_graphs=1, check_every=10, maxit=5000)
+    bt = S.pack(rhs)
+    for _ in range(max(3, args.warmup)):
+        S.solve(bt)
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        x, it, stv, st = S.solve(bt)
+        stats.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    xs = S.unpack(x)
+    # plain FP64 one column at a time (same k, Lanczos interval per instance)
+    t_seq = 0.0
+    err = 0.0
+    its64 = []
+    for i, (A, Bm) in enumerate(zip(mats, rhs)):
+        S64 = P.Solver.from_host(A, device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8, seed=i)
+        for r in range(Bm.shape[1]):
+            b = torch.as_tensor(np.ascontiguousarray(Bm[:, r]), device=dev)
+            S64.solve(b)  # warm
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x64, st64 = S64.solve(b)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t_seq += e0.elapsed_time(e1) / 1e3
+            its64.append(st64["iterations"])
+            xr = x64.cpu().numpy()
+            err = max(err, float(np.linalg.norm(xs[i][:, r] - xr) / np.linalg.norm(xr)))
+        S64.close()
+        del S64
+    rows = sum(s.N ** 3 for s in specs)
+    if rank == 0:
+        out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+               "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None, "dtype": w["prec"], "data": "synthetic",
+               "config": {"workload": args.workload, "instances": len(specs), "rows": rows,
+                          "columns": int(sum(s.nrhs for s in specs)), "k": k, "apply": w["prec"],
+                          "outer": "f64 flexible CG", "graphs": 1},
+               "iterations_max": int(max(stats[-1]["iterations"], 0)),
+               "sequential_f64_s": t_seq, "speedup_vs_sequential_f64": t_seq / (ms / 1e3),
+               "max_rel_diff_vs_f64": err, "iterations_f64_max": int(max(its64)),
+               "setup_ms": S.info_setup_ms if hasattr(S, "info_setup_ms") else None,
+               "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
+        print(json.dumps(out), flush=True)
+
+
 def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
     """Fracture-network Schur complement: PCG on S_hat to rtol 1e-8."""
     import torch
@@ -267,8 +336,14 @@ def main():
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=0, help="override the batched workload's instance count")
+    ap.add_argument("--batch-nmax", type=int, default=0, help="override the batched workload's largest grid")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.batch_count:
+        w["count"] = args.batch_count
+    if args.batch_nmax:
+        w["nmax"] = args.batch_nmax
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -293,6 +368,8 @@ def main():
     B.build()
     A, b = build_problem(w)
     k = args.k if args.k is not None else w["k"]
+    if w.get("batch"):
+        return run_batch(args, w, A, k, dev, world, rank)
     if w.get("dfn"):
         net = A
         S = P.SchurSolver(net, device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8, check_every=args.check_every,

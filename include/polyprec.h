@@ -234,6 +234,56 @@ int schur_recover(pp_ctx* ctx, const double* q, const double* u, double* h, doub
 /* y = A^{-1} v for the block-diagonal fracture matrix (device, n_h). */
 int schur_ainv(pp_ctx* ctx, const double* v, double* y, void* stream);
 
+/* ---- batched solves (many instances, many right-hand sides) ------------- */
+
+/* One SPD instance of a batch: CSR on the device (kept valid during
+ * pp_batch_setup only) and its number of right-hand sides (1..8). */
+typedef struct {
+  int n;
+  long long nnz;
+  const int* rowptr;
+  const int* col;
+  const double* val;
+  int nrhs;
+} pp_batch_item;
+
+#define PP_BATCH_NFEAT 8 /* features per instance from pp_batch_features */
+
+int pp_batch_workspace_size(const pp_batch_item* items, int count, const pp_options* opt,
+                            size_t* bytes);
+
+/* Batch context: every instance in SELL-32 with the Jacobi seed (Section 3),
+ * all instances' slices in one global list walked by single persistent
+ * launches, right-hand sides of one instance sharing each matrix load.
+ * Interval per instance: interval = LANCZOS runs opt->lanczos_steps Lanczos
+ * steps on every instance (start vector SplitMix64 seed opt->seed + i,
+ * stream 3, U[-1,1), for instance i); GIVEN uses opt->alpha/beta for all.
+ * xi < 0 selects clip(10 alpha/beta, 1e-6, 1e-2) per instance.  apply_prec
+ * F64 or F32 (FP32 values and vectors); the outer CG is FP64.  Synchronous. */
+int pp_batch_setup(pp_ctx** ctx, const pp_batch_item* items, int count, const pp_options* opt,
+                   void* workspace, size_t ws_bytes, void* stream);
+
+/* Read (abx_out) and/or replace (abx_in) the spectral interval and xi of
+ * every global column: 3 doubles (alpha, beta, xi) per column, columns of
+ * instance i first, in right-hand-side order.  Host arrays; either may be
+ * NULL.  Replacing recomputes every column's coefficients (Eq. thetamod,
+ * Eq. rhocheb). */
+int pp_batch_intervals(pp_ctx* ctx, double* abx_out, const double* abx_in);
+
+/* PP_BATCH_NFEAT cheap statistics per instance (host array count x 8):
+ * log10 n, mean and std of log diag(A), Gershgorin upper and lower bounds of
+ * the seed-scaled matrix, log10 of the Lanczos extreme Ritz values and of
+ * their ratio (zeros when the interval was given). */
+int pp_batch_features(const pp_ctx* ctx, double* feat);
+
+/* Solve every instance for all its right-hand sides by PCG with its own
+ * p_k: b, x device arrays, instance i's block of n_i x nrhs_i values in
+ * row-major [row][rhs] order, blocks concatenated in item order.  iters,
+ * status: host arrays with one entry per global column (may be NULL).
+ * Returns the worst status.  Synchronous. */
+int pp_batch_solve(pp_ctx* ctx, const double* b, double* x, int* iters, int* status,
+                   pp_stats* stats, void* stream);
+
 /* ---- workspace-free apply (no counterpart in the paper) ---------------- */
 
 /* z = p_k(A) r for a CSR matrix on the device, without a workspace and

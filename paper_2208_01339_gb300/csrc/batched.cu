@@ -1,0 +1,1155 @@
+// Batched polynomial-preconditioned CG: many independent SPD instances of
+// uneven size, each with 1..8 right-hand sides, solved together.
+//
+// Layout.  Every instance is stored in SELL-32 (one warp per 32-row slice,
+// lane = row), and the slices of all instances form one global list, so a
+// single persistent launch per Chebyshev step walks every instance
+// (work item = slice).  Vectors of instance i are row-major [row][rhs] at
+// voff[i], so one matrix entry is loaded once and applied to all the
+// instance's right-hand sides (SpMM-style reuse).  Each global column
+// g = cbase[i] + r has its own Chebyshev coefficients (theta_bar, delta,
+// sigma_bar, rho_0..rho_k) and its own PCG scalars; converged columns are
+// masked, and slices of fully converged instances are skipped.
+//
+// Reductions are deterministic: every slice stores per-column partial sums,
+// then one block per global column adds its instance's partials in slice
+// order (b_seg_reduce), and its epilogue updates that column's scalars.
+// Iterations therefore run without host round trips and a block of them can
+// be replayed as one captured CUDA graph until no column is active.
+//
+// The preconditioner p_k (Algorithm 2) is applied in FP64 or in FP32 (FP32
+// values and vectors, FP32 accumulate); the outer CG is always FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "driver.cuh"
+
+namespace pp {
+
+constexpr int kBR = 8;  // maximum right-hand sides per instance
+
+struct BatchDev {
+  int nb = 0;             // instances
+  int ncols = 0;          // global columns
+  long long nslices = 0;  // global slices
+  int k = 0;
+  const int* s_inst = nullptr;      // instance of each slice
+  const long long* s_row0 = nullptr;  // instance-local first row of each slice
+  const long long* sptr = nullptr;  // global entry offsets
+  const int* col = nullptr;         // instance-local column indices
+  const double* val64 = nullptr;
+  const float* val32 = nullptr;
+  const int* n = nullptr;           // rows per instance
+  const int* R = nullptr;           // right-hand sides per instance
+  const long long* voff = nullptr;  // vector offset (elements) per instance
+  const long long* uoff = nullptr;  // offset of the instance in the caller's b / x
+  const int* cbase = nullptr;       // first global column per instance
+  const long long* sbase = nullptr; // first global slice per instance (nb+1)
+  const int* ccol_inst = nullptr;   // instance of each global column
+  const double* w = nullptr;        // Jacobi seed weights, per instance row (voff1 layout)
+  const long long* woff = nullptr;  // weight offset per instance
+  // per-column coefficients
+  const double* theta_bar = nullptr;
+  const double* delta = nullptr;
+  const double* sigma_bar = nullptr;
+  const double* rho = nullptr;      // [g][k+1]
+};
+
+struct BatchCols {
+  double *rz, *rz_new, *pq, *zq, *rr, *bb, *rtol2;
+  int *done, *iter, *status;
+  int* n_active;
+  int maxit, flexible;
+  double rtol;
+};
+
+}  // namespace pp
+
+struct pp_batch_state {
+  pp::BatchDev d;
+  pp::BatchCols c;
+  std::vector<int> n_h, R_h, cbase_h;
+  std::vector<long long> voff_h, woff_h;
+  long long vec_elems = 0, rows_pad = 0;
+  int apply_prec = 0;
+  // vectors (elements = vec_elems)
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *t1 = nullptr, *t2 = nullptr;
+  float *r32 = nullptr, *u32 = nullptr, *v32 = nullptr, *z32 = nullptr;
+  double* part0 = nullptr;  // [slice][kBR]
+  double* part1 = nullptr;
+  double* lan_a = nullptr;   // [inst][m]
+  double* lan_b2 = nullptr;  // [inst][m]
+  double* nrm = nullptr;     // [inst]
+  double *theta_bar = nullptr, *delta = nullptr, *sigma_bar = nullptr, *rho = nullptr;
+  double* feat = nullptr;    // [inst][4] device feature sums
+  std::vector<double> abx;   // host (alpha, beta, xi) per column
+  std::vector<double> ritz;  // host: per instance, lanczos Ritz extremes and more
+  int lanczos_steps = 0;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap = nullptr;
+  int graph_block = 0;
+};
+
+namespace pp {
+namespace {
+
+__device__ __forceinline__ long long bgw() { return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ long long bnw() { return ((long long)gridDim.x * blockDim.x) >> 5; }
+
+template <typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+  return *p;
+}
+
+// ------------------------------------------------------------- products ---
+// FP64 product over all slices: y = A x (kSpmv, partial (x, y)) or the
+// Lanczos step y = A x - sqrt(b2_prev) x_old on column 0 (partial (y, x)).
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) b_spmv64_kernel(BatchDev d, const double* __restrict__ x,
+                                                          const double* __restrict__ xold, double* __restrict__ y,
+                                                          const int* __restrict__ done, const double* b2prev, int lan_j,
+                                                          double* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const int R = MODE == kLanczos ? 1 : d.R[i];
+    const int RS = d.R[i];
+    const int g0 = d.cbase[i];
+    bool act[kBR];
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) {
+      act[r] = r < R && (MODE == kLanczos || !done[g0 + r]);
+      any |= act[r];
+    }
+    if (!any) continue;
+    const long long row = d.s_row0[s] + lane;
+    const bool in = row < d.n[i];
+    const long long base = d.sptr[s];
+    const int w = (int)((d.sptr[s + 1] - base) / 32);
+    const double* xi = x + d.voff[i];
+    double acc[kBR];
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) acc[r] = 0.0;
+    for (int j = 0; j < w; ++j) {
+      const double v = __ldcs(d.val64 + base + (long long)j * 32 + lane);
+      const long long c = __ldcs(d.col + base + (long long)j * 32 + lane);
+#pragma unroll
+      for (int r = 0; r < kBR; ++r)
+        if (act[r]) acc[r] = fma(v, __ldg(xi + c * RS + r), acc[r]);
+    }
+    double coef = 0.0;
+    if (MODE == kLanczos && lan_j > 0) coef = sqrt(b2prev[(long long)i * kMaxLanczos + lan_j - 1]);
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) {
+      double pr = 0.0;
+      if (act[r]) {
+        const long long e = d.voff[i] + row * RS + r;
+        double yv = acc[r];
+        if (MODE == kLanczos && lan_j > 0) yv -= coef * xold[e];
+        y[e] = yv;
+        if (in) pr = x[e] * yv;
+      }
+      pr = warp_sum(pr);
+      if (lane == 0 && r < R) part[s * kBR + r] = pr;
+    }
+  }
+}
+
+// FP64 / FP32 Chebyshev degree step j (modes as in the single-instance kernels)
+// with per-column coefficients.
+template <typename TV, typename TX, int MODE>
+__global__ void __launch_bounds__(kBlock) b_cheb_kernel(BatchDev d, const TV* __restrict__ val, const TX* __restrict__ x,
+                                                        const TX* __restrict__ xold, const TX* __restrict__ rin,
+                                                        TX* __restrict__ y, const int* __restrict__ done, int j) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const int R = d.R[i];
+    const int g0 = d.cbase[i];
+    bool act[kBR];
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) {
+      act[r] = r < R && !done[g0 + r];
+      any |= act[r];
+    }
+    if (!any) continue;
+    const long long row = d.s_row0[s] + lane;
+    const long long base = d.sptr[s];
+    const int w = (int)((d.sptr[s + 1] - base) / 32);
+    const TX* xi = x + d.voff[i];
+    TX acc[kBR];
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) acc[r] = (TX)0;
+    for (int jj = 0; jj < w; ++jj) {
+      const TX v = (TX)__ldcs(val + base + (long long)jj * 32 + lane);
+      const long long c = __ldcs(d.col + base + (long long)jj * 32 + lane);
+#pragma unroll
+      for (int r = 0; r < kBR; ++r)
+        if (act[r]) acc[r] = fma(v, __ldg(xi + c * R + r), acc[r]);
+    }
+    const int kp1 = d.k + 1;
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) {
+      if (!act[r]) continue;
+      const int g = g0 + r;
+      const double rho_j = d.rho[(long long)g * kp1 + j];
+      const double rho_m = d.rho[(long long)g * kp1 + j - 1];
+      const double dl = d.delta[g], tb = d.theta_bar[g], sb = d.sigma_bar[g];
+      const long long e = d.voff[i] + row * R + r;
+      const TX rs = rin[e];
+      TX yv;
+      if (MODE == kCheb1) {
+        yv = (TX)(2.0 * rho_j / dl) * ((TX)2 * rs - acc[r] * (TX)(1.0 / tb));
+      } else if (MODE == kCheb2) {
+        yv = (TX)rho_j * ((TX)(2.0 * sb) * x[e] - (TX)rho_m * (rs * (TX)(1.0 / tb)) + (TX)(2.0 / dl) * (rs - acc[r]));
+      } else {
+        yv = (TX)rho_j * ((TX)(2.0 * sb) * x[e] - (TX)rho_m * xold[e] + (TX)(2.0 / dl) * (rs - acc[r]));
+      }
+      y[e] = yv;
+    }
+  }
+}
+
+// ------------------------------------------------------------ vectors -----
+// Per-element loops walk slices too (lane = row, r < R) so that partial sums
+// line up with the product kernels.
+enum BVec { kBScaleIn = 0, kBUpdXR = 1, kBTo32 = 2, kBFrom32 = 3, kBUpdP = 4, kBScaleOut = 5, kBZtoP = 6,
+            kBDeg0 = 7 };
+
+template <int OP>
+__global__ void __launch_bounds__(kBlock) b_vec_kernel(BatchDev d, BatchCols cc, const double* __restrict__ bin,
+                                                       double* __restrict__ xout, double* x, double* r, double* z,
+                                                       double* p, const double* q, float* r32, const float* z32,
+                                                       double* __restrict__ part0, double* __restrict__ part1,
+                                                       int first) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const int R = d.R[i];
+    const int g0 = d.cbase[i];
+    const long long row = d.s_row0[s] + lane;
+    const bool in = row < d.n[i];
+    const double wr = in ? d.w[d.woff[i] + row] : 1.0;
+#pragma unroll 1
+    for (int rr = 0; rr < R; ++rr) {
+      const int g = g0 + rr;
+      const long long e = d.voff[i] + row * R + rr;
+      double p0 = 0.0, p1 = 0.0;
+      const bool act = OP == kBScaleIn || OP == kBScaleOut || !cc.done[g];
+      if (act) {
+        if (OP == kBScaleIn) {
+          const double v = in ? wr * bin[d.uoff[i] + row * R + rr] : 0.0;
+          r[e] = v;
+          x[e] = 0.0;
+          p0 = v * v;
+        } else if (OP == kBScaleOut) {
+          if (in) xout[d.uoff[i] + row * R + rr] = wr * x[e];
+        } else if (OP == kBUpdXR) {
+          const double pq = cc.pq[g];
+          if (pq > 0.0 && isfinite(pq)) {
+            const double al = cc.rz[g] / pq;
+            x[e] += al * p[e];
+            const double rv = r[e] - al * q[e];
+            r[e] = rv;
+            p0 = rv * rv;
+          }
+        } else if (OP == kBTo32) {
+          r32[e] = (float)r[e];
+        } else if (OP == kBFrom32 || OP == kBDeg0) {
+          const double zv = OP == kBFrom32 ? (double)z32[e] : r[e] / d.theta_bar[g];
+          z[e] = zv;
+          p0 = r[e] * zv;
+          p1 = q[e] * zv;
+        } else if (OP == kBUpdP) {
+          double beta = 0.0;
+          if (!first) beta = cc.flexible ? -cc.zq[g] / cc.pq[g] : cc.rz_new[g] / cc.rz[g];
+          p[e] = z[e] + beta * p[e];
+        } else if (OP == kBZtoP) {
+          p0 = r[e] * z[e];
+          p1 = q[e] * z[e];
+        }
+      }
+      if (OP == kBScaleIn || OP == kBUpdXR || OP == kBFrom32 || OP == kBZtoP || OP == kBDeg0) {
+        p0 = warp_sum(in ? p0 : 0.0);
+        p1 = warp_sum(in ? p1 : 0.0);
+        if (lane == 0) {
+          part0[s * kBR + rr] = p0;
+          if (part1) part1[s * kBR + rr] = p1;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------ segmented reduce --
+enum BRed { kRedBB = 0, kRedPQ = 1, kRedRR = 2, kRedRZ = 3, kRedLanA = 4, kRedLanB = 5, kRedNrm = 6 };
+
+// One block per global column (or per instance for the Lanczos values):
+// adds the partials of the instance's slices in slice order.
+template <int OP>
+__global__ void __launch_bounds__(kBlock) b_reduce_kernel(BatchDev d, BatchCols cc, const double* __restrict__ part0,
+                                                          const double* __restrict__ part1, double* lan_out,
+                                                          int lan_j) {
+  const int nitems = (OP == kRedLanA || OP == kRedLanB || OP == kRedNrm) ? d.nb : d.ncols;
+  for (int g = blockIdx.x; g < nitems; g += gridDim.x) {
+    int i, r;
+    if (OP == kRedLanA || OP == kRedLanB || OP == kRedNrm) {
+      i = g;
+      r = 0;
+    } else {
+      i = d.ccol_inst[g];
+      r = g - d.cbase[i];
+    }
+    if (OP != kRedBB && OP != kRedLanA && OP != kRedLanB && OP != kRedNrm && cc.done[g]) continue;
+    const long long s0 = d.sbase[i], s1 = d.sbase[i + 1];
+    double v[2] = {0.0, 0.0};
+    for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+      v[0] += part0[s * kBR + r];
+      if (OP == kRedRZ) v[1] += part1[s * kBR + r];
+    }
+    block_sum<2>(v);
+    if (threadIdx.x == 0) {
+      if (OP == kRedBB) {
+        cc.bb[g] = v[0];
+        cc.rr[g] = v[0];
+        cc.rtol2[g] = cc.rtol * cc.rtol * v[0];
+        cc.iter[g] = 0;
+        cc.status[g] = 1;
+        cc.done[g] = 0;
+        if (!isfinite(v[0])) {
+          cc.status[g] = -3;
+          cc.done[g] = 1;
+        } else if (v[0] == 0.0) {
+          cc.status[g] = 0;
+          cc.done[g] = 1;
+        }
+        if (cc.done[g]) atomicSub(cc.n_active, 1);
+      } else if (OP == kRedPQ) {
+        cc.rz[g] = cc.rz_new[g];
+        cc.pq[g] = v[0];
+        if (!(v[0] > 0.0)) {
+          cc.status[g] = isfinite(v[0]) ? -2 : -3;
+          cc.done[g] = 1;
+          atomicSub(cc.n_active, 1);
+        }
+      } else if (OP == kRedRR) {
+        cc.rr[g] = v[0];
+        cc.iter[g] += 1;
+        int st = 1;
+        bool fin = false;
+        if (!isfinite(v[0])) {
+          st = -3;
+          fin = true;
+        } else if (v[0] <= cc.rtol2[g]) {
+          st = 0;
+          fin = true;
+        } else if (cc.iter[g] >= cc.maxit) {
+          st = 1;
+          fin = true;
+        }
+        if (fin) {
+          cc.status[g] = st;
+          cc.done[g] = 1;
+          atomicSub(cc.n_active, 1);
+        }
+      } else if (OP == kRedRZ) {
+        cc.rz_new[g] = v[0];
+        cc.zq[g] = v[1];
+        if (!(v[0] > 0.0)) {
+          cc.status[g] = isfinite(v[0]) ? -2 : -3;
+          cc.done[g] = 1;
+          atomicSub(cc.n_active, 1);
+        }
+      } else {
+        lan_out[(long long)i * kMaxLanczos + lan_j] = v[0];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ Lanczos -----
+__global__ void __launch_bounds__(kBlock) b_lan_start_kernel(BatchDev d, unsigned long long seed, double* v,
+                                                             double* part) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const int R = d.R[i];
+    const long long row = d.s_row0[s] + lane;
+    const bool in = row < d.n[i];
+    const uint64_t key = splitmix_key(seed + (unsigned long long)i, 3);
+    const double x = in ? 2.0 * splitmix_uniform(key, (uint64_t)row) - 1.0 : 0.0;
+    v[d.voff[i] + row * R] = x;
+    const double pr = warp_sum(x * x);
+    if (lane == 0) part[s * kBR] = pr;
+  }
+}
+
+// OP 0: v /= sqrt(nrm[i]); OP 1: w -= a_j v with partial ||w||^2
+template <int OP>
+__global__ void __launch_bounds__(kBlock) b_lan_vec_kernel(BatchDev d, double* a, const double* v, const double* coef,
+                                                           int j, double* part) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const int R = d.R[i];
+    const long long row = d.s_row0[s] + lane;
+    const bool in = row < d.n[i];
+    const long long e = d.voff[i] + row * R;
+    double pr = 0.0;
+    if (OP == 0) {
+      const double nv = sqrt(coef[(long long)i * kMaxLanczos + j]);
+      if (in) a[e] = a[e] / nv;
+    } else {
+      if (in) {
+        const double wv = a[e] - coef[(long long)i * kMaxLanczos + j] * v[e];
+        a[e] = wv;
+        pr = wv * wv;
+      }
+      pr = warp_sum(pr);
+      if (lane == 0) part[s * kBR] = pr;
+    }
+  }
+}
+
+// Per-instance feature sums of the seed-scaled matrix: sum log diag(A),
+// sum (log diag)^2, Gershgorin max of row sums of |A_hat|, min of
+// (A_hat_ii - off-diagonal sum).
+__global__ void __launch_bounds__(kBlock) b_feature_kernel(BatchDev d, const double* __restrict__ diag_log,
+                                                           double* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const long long row = d.s_row0[s] + lane;
+    const bool in = row < d.n[i];
+    const long long base = d.sptr[s];
+    const int w = (int)((d.sptr[s + 1] - base) / 32);
+    double off = 0.0, dg = 0.0;
+    for (int j = 0; j < w; ++j) {
+      const double v = d.val64[base + (long long)j * 32 + lane];
+      const long long c = d.col[base + (long long)j * 32 + lane];
+      if (c == row) dg += v; else off += fabs(v);
+    }
+    const double dl = in ? diag_log[d.woff[i] + row] : 0.0;
+    double a0 = warp_sum(dl), a1 = warp_sum(dl * dl);
+    double mx = in ? dg + off : 0.0, mn = in ? dg - off : 1e300;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+      mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    }
+    if (lane == 0) {
+      part[s * kBR + 0] = a0;
+      part[s * kBR + 1] = a1;
+      part[s * kBR + 2] = mx;
+      part[s * kBR + 3] = mn;
+    }
+  }
+}
+
+__global__ void b_feature_reduce_kernel(BatchDev d, const double* part, double* feat) {
+  for (int i = blockIdx.x; i < d.nb; i += gridDim.x) {
+    if (threadIdx.x != 0) continue;
+    double a0 = 0, a1 = 0, mx = 0, mn = 1e300;
+    for (long long s = d.sbase[i]; s < d.sbase[i + 1]; ++s) {
+      a0 += part[s * kBR + 0];
+      a1 += part[s * kBR + 1];
+      mx = fmax(mx, part[s * kBR + 2]);
+      mn = fmin(mn, part[s * kBR + 3]);
+    }
+    feat[i * 4 + 0] = a0;
+    feat[i * 4 + 1] = a1;
+    feat[i * 4 + 2] = mx;
+    feat[i * 4 + 3] = mn;
+  }
+}
+
+// ------------------------------------------------------------- setup ------
+__global__ void b_fill_kernel(BatchDev d, const int* const* rowptrs, const int* const* cols,
+                              const double* const* vals, double* __restrict__ w, double* __restrict__ diag_log,
+                              int* __restrict__ ocol, double* __restrict__ oval, int* bad) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const long long row = d.s_row0[s] + lane;
+    const bool in = row < d.n[i];
+    const long long base = d.sptr[s];
+    const int wd = (int)((d.sptr[s + 1] - base) / 32);
+    int j = 0;
+    if (in) {
+      const int* rp = rowptrs[i];
+      const int* ci = cols[i];
+      const double* va = vals[i];
+      for (int p = rp[row]; p < rp[row + 1]; ++p, ++j) {
+        ocol[base + (long long)j * 32 + lane] = ci[p];
+        oval[base + (long long)j * 32 + lane] = va[p];
+      }
+    }
+    for (; j < wd; ++j) {
+      ocol[base + (long long)j * 32 + lane] = in ? (int)row : 0;
+      oval[base + (long long)j * 32 + lane] = 0.0;
+    }
+    if (in) {
+      double dg = 0.0;
+      const int* rp = rowptrs[i];
+      for (int p = rp[row]; p < rp[row + 1]; ++p)
+        if (cols[i][p] == row) dg += vals[i][p];
+      if (!(dg > 0.0)) atomicExch(bad, 1);
+      w[d.woff[i] + row] = dg > 0.0 ? 1.0 / sqrt(dg) : 1.0;
+      diag_log[d.woff[i] + row] = dg > 0.0 ? log(dg) : 0.0;
+    }
+  }
+}
+
+// A_hat = W A W in place (needs all weights of the instance first).
+__global__ void b_scale_kernel(BatchDev d, double* __restrict__ oval, float* __restrict__ val32) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const long long row = d.s_row0[s] + lane;
+    const bool in = row < d.n[i];
+    const long long base = d.sptr[s];
+    const int wd = (int)((d.sptr[s + 1] - base) / 32);
+    const double wr = in ? d.w[d.woff[i] + row] : 1.0;
+    for (int j = 0; j < wd; ++j) {
+      const long long e = base + (long long)j * 32 + lane;
+      const double v = in ? (wr * oval[e]) * d.w[d.woff[i] + d.col[e]] : 0.0;
+      oval[e] = v;
+      if (val32) val32[e] = (float)v;
+    }
+  }
+}
+
+int grid_b(long long nslices) {
+  long long g = (nslices * 32 + kBlock - 1) / kBlock;
+  return (int)std::max(1LL, std::min<long long>(g, 152LL * 8));
+}
+
+}  // namespace
+}  // namespace pp
+
+// ===========================================================================
+// host side
+// ===========================================================================
+namespace pp {
+namespace {
+
+struct BBump {
+  uintptr_t base, off = 0;
+  explicit BBump(void* b) : base((uintptr_t)b) {}
+  template <typename T>
+  T* take(long long count) {
+    off = (off + 255) & ~(uintptr_t)255;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += (uintptr_t)(count > 0 ? count : 1) * sizeof(T);
+    return p;
+  }
+};
+
+struct BPlan {
+  int nb = 0, ncols = 0;
+  long long nslices = 0, nnz_pad = 0, vec_elems = 0, rows_pad = 0;
+  std::vector<int> s_inst, n, R, cbase, ccol_inst;
+  std::vector<long long> s_row0, sptr, voff, woff, uoff, sbase;
+};
+
+int plan_batch(const pp_batch_item* items, int count, BPlan& P, cudaStream_t s) {
+  P.nb = count;
+  P.sbase.assign(count + 1, 0);
+  P.sptr.push_back(0);
+  long long vo = 0, wo = 0, uo = 0;
+  int cb = 0;
+  for (int i = 0; i < count; ++i) {
+    const pp_batch_item& it = items[i];
+    std::vector<int> rp((size_t)it.n + 1);
+    cudaError_t e = cudaMemcpyAsync(rp.data(), it.rowptr, sizeof(int) * (it.n + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "pp_batch: reading rowptr");
+    if (rp[0] != 0 || rp[it.n] != it.nnz) return fail(nullptr, PP_EINVAL, "pp_batch: rowptr[0] != 0 or rowptr[n] != nnz");
+    const long long ns = ((long long)it.n + 31) / 32;
+    for (long long sl = 0; sl < ns; ++sl) {
+      int wmax = 0;
+      for (long long r = sl * 32; r < std::min<long long>(it.n, sl * 32 + 32); ++r) wmax = std::max(wmax, rp[r + 1] - rp[r]);
+      P.s_inst.push_back(i);
+      P.s_row0.push_back(sl * 32);
+      P.sptr.push_back(P.sptr.back() + (long long)wmax * 32);
+    }
+    P.sbase[i + 1] = P.sbase[i] + ns;
+    P.n.push_back(it.n);
+    P.R.push_back(it.nrhs);
+    P.cbase.push_back(cb);
+    for (int r = 0; r < it.nrhs; ++r) P.ccol_inst.push_back(i);
+    cb += it.nrhs;
+    P.voff.push_back(vo);
+    P.woff.push_back(wo);
+    P.uoff.push_back(uo);
+    vo += ns * 32 * it.nrhs;
+    wo += ns * 32;
+    uo += (long long)it.n * it.nrhs;
+  }
+  P.ncols = cb;
+  P.nslices = (long long)P.s_inst.size();
+  P.nnz_pad = P.sptr.back();
+  P.vec_elems = vo;
+  P.rows_pad = wo;
+  return PP_OK;
+}
+
+size_t layout_batch(pp_ctx* c, pp_batch_state* B, const BPlan& P, void* base) {
+  BBump M(base);
+  const int k = c->opt.k;
+  c->sc = M.take<Scalars>(1);
+  BatchDev& d = B->d;
+  d.nb = P.nb;
+  d.ncols = P.ncols;
+  d.nslices = P.nslices;
+  d.k = k;
+  d.s_inst = M.take<int>(P.nslices);
+  d.s_row0 = M.take<long long>(P.nslices);
+  d.sptr = M.take<long long>(P.nslices + 1);
+  d.col = M.take<int>(P.nnz_pad);
+  d.val64 = M.take<double>(P.nnz_pad);
+  d.val32 = B->apply_prec == PP_PREC_F32 ? M.take<float>(P.nnz_pad) : nullptr;
+  d.n = M.take<int>(P.nb);
+  d.R = M.take<int>(P.nb);
+  d.voff = M.take<long long>(P.nb);
+  d.uoff = M.take<long long>(P.nb);
+  d.cbase = M.take<int>(P.nb);
+  d.sbase = M.take<long long>(P.nb + 1);
+  d.ccol_inst = M.take<int>(P.ncols);
+  d.w = M.take<double>(P.rows_pad);
+  d.woff = M.take<long long>(P.nb);
+  B->theta_bar = M.take<double>(P.ncols);
+  B->delta = M.take<double>(P.ncols);
+  B->sigma_bar = M.take<double>(P.ncols);
+  B->rho = M.take<double>((long long)P.ncols * (k + 1));
+  d.theta_bar = B->theta_bar;
+  d.delta = B->delta;
+  d.sigma_bar = B->sigma_bar;
+  d.rho = B->rho;
+  BatchCols& cc = B->c;
+  cc.rz = M.take<double>(P.ncols);
+  cc.rz_new = M.take<double>(P.ncols);
+  cc.pq = M.take<double>(P.ncols);
+  cc.zq = M.take<double>(P.ncols);
+  cc.rr = M.take<double>(P.ncols);
+  cc.bb = M.take<double>(P.ncols);
+  cc.rtol2 = M.take<double>(P.ncols);
+  cc.done = M.take<int>(P.ncols);
+  cc.iter = M.take<int>(P.ncols);
+  cc.status = M.take<int>(P.ncols);
+  cc.n_active = M.take<int>(1);
+  B->part0 = M.take<double>(P.nslices * kBR);
+  B->part1 = M.take<double>(P.nslices * kBR);
+  B->lan_a = M.take<double>((long long)P.nb * kMaxLanczos);
+  B->lan_b2 = M.take<double>((long long)P.nb * kMaxLanczos);
+  B->nrm = M.take<double>((long long)P.nb * kMaxLanczos);
+  B->feat = M.take<double>((long long)P.nb * 4);
+  B->x = M.take<double>(P.vec_elems);
+  B->r = M.take<double>(P.vec_elems);
+  B->z = M.take<double>(P.vec_elems);
+  B->p = M.take<double>(P.vec_elems);
+  B->q = M.take<double>(P.vec_elems);
+  B->t1 = M.take<double>(P.vec_elems);
+  B->t2 = M.take<double>(P.vec_elems);
+  if (B->apply_prec == PP_PREC_F32) {
+    B->r32 = M.take<float>(P.vec_elems);
+    B->u32 = M.take<float>(P.vec_elems);
+    B->v32 = M.take<float>(P.vec_elems);
+    B->z32 = M.take<float>(P.vec_elems);
+  }
+  c->partials = M.take<double>(P.rows_pad);  // diag logs during setup
+  return M.off + 256;
+}
+
+struct BLaunch {
+  int grid;
+  cudaStream_t s;
+};
+
+cudaError_t b_reduce(pp_batch_state* B, int op, double* lan_out, int j, cudaStream_t s) {
+  const BatchDev& d = B->d;
+  const int items = (op == kRedLanA || op == kRedLanB || op == kRedNrm) ? d.nb : d.ncols;
+  const int g = std::max(1, std::min(items, 152 * 8));
+  switch (op) {
+    case kRedBB: b_reduce_kernel<kRedBB><<<g, kBlock, 0, s>>>(d, B->c, B->part0, B->part1, lan_out, j); break;
+    case kRedPQ: b_reduce_kernel<kRedPQ><<<g, kBlock, 0, s>>>(d, B->c, B->part0, B->part1, lan_out, j); break;
+    case kRedRR: b_reduce_kernel<kRedRR><<<g, kBlock, 0, s>>>(d, B->c, B->part0, B->part1, lan_out, j); break;
+    case kRedRZ: b_reduce_kernel<kRedRZ><<<g, kBlock, 0, s>>>(d, B->c, B->part0, B->part1, lan_out, j); break;
+    case kRedLanA: b_reduce_kernel<kRedLanA><<<g, kBlock, 0, s>>>(d, B->c, B->part0, B->part1, lan_out, j); break;
+    case kRedLanB: b_reduce_kernel<kRedLanB><<<g, kBlock, 0, s>>>(d, B->c, B->part0, B->part1, lan_out, j); break;
+    default: b_reduce_kernel<kRedNrm><<<g, kBlock, 0, s>>>(d, B->c, B->part0, B->part1, lan_out, j); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int OP>
+cudaError_t b_vec(pp_batch_state* B, const double* bin, double* xout, int first, cudaStream_t s) {
+  b_vec_kernel<OP><<<grid_b(B->d.nslices), kBlock, 0, s>>>(B->d, B->c, bin, xout, B->x, B->r, B->z, B->p, B->q,
+                                                          B->r32, B->z32, B->part0, B->part1, first);
+  return cudaGetLastError();
+}
+
+// z = p_k(A_hat) r for every active column, then (r,z), (q,z) -> rz_new, zq.
+cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
+  const BatchDev& d = B->d;
+  const int k = d.k;
+  const int g = grid_b(d.nslices);
+  cudaError_t e = cudaSuccess;
+  if (k == 0) {
+    e = b_vec<kBDeg0>(B, nullptr, nullptr, 0, s);
+    return e == cudaSuccess ? b_reduce(B, kRedRZ, nullptr, 0, s) : e;
+  }
+  if (B->apply_prec == PP_PREC_F32) {
+    e = b_vec<kBTo32>(B, nullptr, nullptr, 0, s);
+    float* buf[3] = {B->u32, B->v32, B->z32};
+    const int off = ((2 - k) % 3 + 3) % 3;
+    auto Y = [&](int j) { return buf[(j + off) % 3]; };
+    for (int j = 1; j <= k && e == cudaSuccess; ++j) {
+      if (j == 1)
+        b_cheb_kernel<float, float, kCheb1><<<g, kBlock, 0, s>>>(d, d.val32, B->r32, nullptr, B->r32, Y(1), B->c.done, 1);
+      else if (j == 2)
+        b_cheb_kernel<float, float, kCheb2><<<g, kBlock, 0, s>>>(d, d.val32, Y(1), nullptr, B->r32, Y(2), B->c.done, 2);
+      else
+        b_cheb_kernel<float, float, kChebK><<<g, kBlock, 0, s>>>(d, d.val32, Y(j - 1), Y(j - 2), B->r32, Y(j), B->c.done,
+                                                               j);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = b_vec<kBFrom32>(B, nullptr, nullptr, 0, s);
+  } else {
+    double* buf[3] = {B->t1, B->t2, B->z};
+    const int off = ((2 - k) % 3 + 3) % 3;
+    auto Y = [&](int j) { return buf[(j + off) % 3]; };
+    for (int j = 1; j <= k && e == cudaSuccess; ++j) {
+      if (j == 1)
+        b_cheb_kernel<double, double, kCheb1><<<g, kBlock, 0, s>>>(d, d.val64, B->r, nullptr, B->r, Y(1), B->c.done, 1);
+      else if (j == 2)
+        b_cheb_kernel<double, double, kCheb2><<<g, kBlock, 0, s>>>(d, d.val64, Y(1), nullptr, B->r, Y(2), B->c.done, 2);
+      else
+        b_cheb_kernel<double, double, kChebK><<<g, kBlock, 0, s>>>(d, d.val64, Y(j - 1), Y(j - 2), B->r, Y(j),
+                                                                 B->c.done, j);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = b_vec<kBZtoP>(B, nullptr, nullptr, 0, s);
+  }
+  return e == cudaSuccess ? b_reduce(B, kRedRZ, nullptr, 0, s) : e;
+}
+
+cudaError_t b_iteration(pp_batch_state* B, cudaStream_t s) {
+  const BatchDev& d = B->d;
+  b_spmv64_kernel<kSpmv><<<grid_b(d.nslices), kBlock, 0, s>>>(d, B->p, nullptr, B->q, B->c.done, nullptr, 0, B->part0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = b_reduce(B, kRedPQ, nullptr, 0, s);
+  if (e == cudaSuccess) e = b_vec<kBUpdXR>(B, nullptr, nullptr, 0, s);
+  if (e == cudaSuccess) e = b_reduce(B, kRedRR, nullptr, 0, s);
+  if (e == cudaSuccess) e = b_precond(B, s);
+  if (e == cudaSuccess) e = b_vec<kBUpdP>(B, nullptr, nullptr, 0, s);
+  return e;
+}
+
+void set_coeffs(pp_batch_state* B, int k) {
+  const int nc = B->d.ncols;
+  std::vector<double> tb(nc), dl(nc), sb(nc), rho((size_t)nc * (k + 1));
+  for (int g = 0; g < nc; ++g)
+    polyprec_coeffs(B->abx[3 * g], B->abx[3 * g + 1], B->abx[3 * g + 2], k, &tb[g], &dl[g], &sb[g],
+                    &rho[(size_t)g * (k + 1)]);
+  cudaMemcpy(B->theta_bar, tb.data(), sizeof(double) * nc, cudaMemcpyHostToDevice);
+  cudaMemcpy(B->delta, dl.data(), sizeof(double) * nc, cudaMemcpyHostToDevice);
+  cudaMemcpy(B->sigma_bar, sb.data(), sizeof(double) * nc, cudaMemcpyHostToDevice);
+  cudaMemcpy(B->rho, rho.data(), sizeof(double) * rho.size(), cudaMemcpyHostToDevice);
+}
+
+int b_lanczos(pp_ctx* c, pp_batch_state* B, cudaStream_t s) {
+  const BatchDev& d = B->d;
+  const int m = c->opt.lanczos_steps;
+  const int g = grid_b(d.nslices);
+  double* buf[3] = {B->t1, B->t2, B->z};
+  b_lan_start_kernel<<<g, kBlock, 0, s>>>(d, c->opt.seed, buf[0], B->part0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = b_reduce(B, kRedNrm, B->nrm, 0, s);
+  if (e == cudaSuccess) {
+    b_lan_vec_kernel<0><<<g, kBlock, 0, s>>>(d, buf[0], nullptr, B->nrm, 0, nullptr);
+    e = cudaGetLastError();
+  }
+  int iv = 0, ivp = -1, iw = 1;
+  for (int j = 0; j < m && e == cudaSuccess; ++j) {
+    b_spmv64_kernel<kLanczos><<<g, kBlock, 0, s>>>(d, buf[iv], ivp >= 0 ? buf[ivp] : nullptr, buf[iw], B->c.done,
+                                                   B->lan_b2, j, B->part0);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = b_reduce(B, kRedLanA, B->lan_a, j, s);
+    if (e == cudaSuccess) {
+      b_lan_vec_kernel<1><<<g, kBlock, 0, s>>>(d, buf[iw], buf[iv], B->lan_a, j, B->part0);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = b_reduce(B, kRedLanB, B->lan_b2, j, s);
+    if (e == cudaSuccess && j < m - 1) {
+      b_lan_vec_kernel<0><<<g, kBlock, 0, s>>>(d, buf[iw], nullptr, B->lan_b2, j, nullptr);
+      e = cudaGetLastError();
+      const int spare = ivp >= 0 ? ivp : 2;
+      ivp = iv;
+      iv = iw;
+      iw = spare;
+    }
+  }
+  std::vector<double> ha((size_t)d.nb * kMaxLanczos), hb((size_t)d.nb * kMaxLanczos);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ha.data(), B->lan_a, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), B->lan_b2, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pp_batch: Lanczos");
+  B->ritz.assign((size_t)d.nb * 5, 0.0);
+  std::vector<double> alpha(d.nb), beta(d.nb);
+  for (int i = 0; i < d.nb; ++i) {
+    std::vector<double> ta, tb;
+    for (int j = 0; j < m; ++j) {
+      ta.push_back(ha[(size_t)i * kMaxLanczos + j]);
+      if (j == m - 1) break;
+      const double bj = std::sqrt(hb[(size_t)i * kMaxLanczos + j]);
+      if (!(bj > 1e-300)) break;
+      tb.push_back(bj);
+    }
+    double lo, hi;
+    tridiag_extremes_jacobi(ta, tb, &lo, &hi);
+    if (!(lo > 0.0)) return fail(c, PP_EBREAKDOWN, "pp_batch: instance " + std::to_string(i) + " is not SPD");
+    alpha[i] = lo;
+    beta[i] = hi > lo ? hi : lo * (1.0 + 1e-12);
+    B->ritz[(size_t)i * 5 + 0] = lo;
+    B->ritz[(size_t)i * 5 + 1] = hi;
+  }
+  B->abx.assign((size_t)d.ncols * 3, 0.0);
+  for (int i = 0; i < d.nb; ++i)
+    for (int r = 0; r < B->R_h[i]; ++r) {
+      const int gg = B->cbase_h[i] + r;
+      B->abx[3 * gg] = alpha[i];
+      B->abx[3 * gg + 1] = beta[i];
+      B->abx[3 * gg + 2] = c->opt.xi >= 0.0 ? c->opt.xi : auto_xi(alpha[i], beta[i]);
+    }
+  B->lanczos_steps = m;
+  return PP_OK;
+}
+
+}  // namespace
+
+void batch_free(pp_batch_state* B) {
+  if (!B) return;
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  delete B;
+}
+
+}  // namespace pp
+
+using namespace pp;
+
+namespace {
+
+int check_items(const pp_batch_item* items, int count) {
+  if (!items || count <= 0) return fail(nullptr, PP_EINVAL, "pp_batch: no items");
+  for (int i = 0; i < count; ++i) {
+    const pp_batch_item& it = items[i];
+    if (it.n <= 0 || it.nnz < 0 || it.nnz > 2147483647LL || !it.rowptr || !it.col || !it.val)
+      return fail(nullptr, PP_EINVAL, "pp_batch: invalid matrix " + std::to_string(i));
+    if (it.nrhs < 1 || it.nrhs > kBR)
+      return fail(nullptr, PP_EINVAL, "pp_batch: nrhs must be in [1, 8] (item " + std::to_string(i) + ")");
+  }
+  return PP_OK;
+}
+
+int check_batch_opts(const pp_options* o) {
+  int rc = validate_options(nullptr, o);
+  if (rc) return rc;
+  if (o->apply_prec == PP_PREC_BF16) return fail(nullptr, PP_EUNSUPPORTED, "pp_batch: apply_prec must be F64 or F32");
+  if (o->seed_scaling != PP_SEED_JACOBI) return fail(nullptr, PP_EUNSUPPORTED, "pp_batch: Jacobi seed only");
+  return PP_OK;
+}
+
+}  // namespace
+
+extern "C" int pp_batch_workspace_size(const pp_batch_item* items, int count, const pp_options* opt, size_t* bytes) {
+  int rc = check_items(items, count);
+  if (rc) return rc;
+  if ((rc = check_batch_opts(opt))) return rc;
+  if (!bytes) return fail(nullptr, PP_EINVAL, "bytes is NULL");
+  BPlan P;
+  if ((rc = plan_batch(items, count, P, nullptr))) return rc;
+  pp_ctx tmp;
+  tmp.opt = *opt;
+  pp_batch_state B;
+  B.apply_prec = opt->apply_prec;
+  *bytes = layout_batch(&tmp, &B, P, nullptr);
+  return PP_OK;
+}
+
+extern "C" int pp_batch_setup(pp_ctx** out, const pp_batch_item* items, int count, const pp_options* opt, void* ws,
+                              size_t ws_bytes, void* stream) {
+  if (!out) return fail(nullptr, PP_EINVAL, "ctx pointer is NULL");
+  *out = nullptr;
+  int rc = check_items(items, count);
+  if (rc) return rc;
+  if ((rc = check_batch_opts(opt))) return rc;
+  if (!ws || ((uintptr_t)ws & 255)) return fail(nullptr, PP_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  pp_ctx* c = new pp_ctx();
+  c->kind = 2;
+  c->opt = *opt;
+  if (c->opt.check_every <= 0) c->opt.check_every = 4;
+  pp_batch_state* B = new pp_batch_state();
+  c->batch = B;
+  B->apply_prec = opt->apply_prec;
+  auto bail = [&](int code) {
+    std::string m = c->err;
+    destroy_ctx_resources(c);
+    delete c;
+    if (!m.empty()) fail(nullptr, code, m);
+    return code;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  BPlan P;
+  if ((rc = plan_batch(items, count, P, s))) return bail(rc);
+  const size_t need = layout_batch(c, B, P, nullptr);
+  if (ws_bytes < need) return bail(fail(c, PP_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes"));
+  layout_batch(c, B, P, ws);
+  c->ws = ws;
+  c->ws_bytes = ws_bytes;
+  c->n = P.ncols;
+  c->nnz = 0;
+  for (int i = 0; i < count; ++i) c->nnz += items[i].nnz;
+  c->nnz_pad = P.nnz_pad;
+  B->n_h = P.n;
+  B->R_h = P.R;
+  B->cbase_h = P.cbase;
+  B->voff_h = P.voff;
+  B->woff_h = P.woff;
+  B->vec_elems = P.vec_elems;
+  B->rows_pad = P.rows_pad;
+  BatchDev& d = B->d;
+  B->c.maxit = opt->maxit;
+  B->c.flexible = opt->flexible;
+  B->c.rtol = opt->rtol;
+  // upload the plan (and the instance pointer tables, kept in t1 for the fill)
+  std::vector<const int*> rps(count), cis(count);
+  std::vector<const double*> vas(count);
+  for (int i = 0; i < count; ++i) {
+    rps[i] = items[i].rowptr;
+    cis[i] = items[i].col;
+    vas[i] = items[i].val;
+  }
+  const int** d_rp = reinterpret_cast<const int**>(B->t1);
+  const int** d_ci = d_rp + count;
+  const double** d_va = reinterpret_cast<const double**>(d_ci + count);
+  struct Up {
+    const void* dst;
+    const void* src;
+    size_t n;
+  } ups[] = {{d.s_inst, P.s_inst.data(), sizeof(int) * P.s_inst.size()},
+             {d.s_row0, P.s_row0.data(), sizeof(long long) * P.s_row0.size()},
+             {d.sptr, P.sptr.data(), sizeof(long long) * P.sptr.size()},
+             {d.n, P.n.data(), sizeof(int) * P.n.size()},
+             {d.R, P.R.data(), sizeof(int) * P.R.size()},
+             {d.voff, P.voff.data(), sizeof(long long) * P.voff.size()},
+             {d.uoff, P.uoff.data(), sizeof(long long) * P.uoff.size()},
+             {d.cbase, P.cbase.data(), sizeof(int) * P.cbase.size()},
+             {d.sbase, P.sbase.data(), sizeof(long long) * P.sbase.size()},
+             {d.ccol_inst, P.ccol_inst.data(), sizeof(int) * P.ccol_inst.size()},
+             {d.woff, P.woff.data(), sizeof(long long) * P.woff.size()},
+             {d_rp, rps.data(), sizeof(void*) * count},
+             {d_ci, cis.data(), sizeof(void*) * count},
+             {d_va, vas.data(), sizeof(void*) * count}};
+  cudaError_t e = cudaSuccess;
+  for (const Up& u : ups)
+    if (e == cudaSuccess && u.n) e = cudaMemcpyAsync(const_cast<void*>(u.dst), u.src, u.n, cudaMemcpyHostToDevice, s);
+  int* d_bad = B->c.n_active;
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+  double* diag_log = c->partials;
+  if (e == cudaSuccess) {
+    b_fill_kernel<<<grid_b(d.nslices), kBlock, 0, s>>>(d, d_rp, d_ci, d_va, const_cast<double*>(d.w), diag_log,
+                                                        const_cast<int*>(d.col), const_cast<double*>(d.val64), d_bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    b_scale_kernel<<<grid_b(d.nslices), kBlock, 0, s>>>(d, const_cast<double*>(d.val64), const_cast<float*>(d.val32));
+    e = cudaGetLastError();
+  }
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+  // clear vectors and column state
+  const size_t vb = sizeof(double) * (size_t)P.vec_elems;
+  for (double* v : {B->x, B->r, B->z, B->p, B->q, B->t1, B->t2})
+    if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, vb, s);
+  if (B->apply_prec == PP_PREC_F32)
+    for (float* v : {B->r32, B->u32, B->v32, B->z32})
+      if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(float) * (size_t)P.vec_elems, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->c.done, 0, sizeof(int) * P.ncols, s);
+  // features: sums of log diag(A) and Gershgorin bounds of A_hat
+  if (e == cudaSuccess) {
+    b_feature_kernel<<<grid_b(d.nslices), kBlock, 0, s>>>(d, diag_log, B->part0);
+    b_feature_reduce_kernel<<<std::min(d.nb, 1024), 32, 0, s>>>(d, B->part0, B->feat);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "pp_batch setup"));
+  if (bad) return bail(fail(c, PP_EINVAL, "pp_batch: non-positive diagonal"));
+  if (opt->interval == PP_INTERVAL_GIVEN) {
+    B->abx.assign((size_t)P.ncols * 3, 0.0);
+    for (int g = 0; g < P.ncols; ++g) {
+      B->abx[3 * g] = opt->alpha;
+      B->abx[3 * g + 1] = opt->beta;
+      B->abx[3 * g + 2] = opt->xi >= 0.0 ? opt->xi : auto_xi(opt->alpha, opt->beta);
+    }
+    B->ritz.assign((size_t)P.nb * 5, 0.0);
+  } else if ((rc = b_lanczos(c, B, s))) {
+    return bail(rc);
+  }
+  set_coeffs(B, opt->k);
+  cudaEventRecord(e1, s);
+  e = cudaEventSynchronize(e1);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "pp_batch setup"));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->t_setup_ms = ms;
+  *out = c;
+  return PP_OK;
+}
+
+extern "C" int pp_batch_intervals(pp_ctx* c, double* abx_out, const double* abx_in) {
+  if (!c || c->kind != 2) return fail(c, PP_EINVAL, "not a batch context");
+  pp_batch_state* B = c->batch;
+  if (abx_out) std::memcpy(abx_out, B->abx.data(), sizeof(double) * B->abx.size());
+  if (abx_in) {
+    for (int g = 0; g < B->d.ncols; ++g)
+      if (!(abx_in[3 * g] > 0.0 && abx_in[3 * g + 1] > abx_in[3 * g] && abx_in[3 * g + 2] >= 0.0))
+        return fail(c, PP_EINVAL, "pp_batch_intervals: need 0 < alpha < beta and xi >= 0 for column " +
+                                      std::to_string(g));
+    std::memcpy(B->abx.data(), abx_in, sizeof(double) * B->abx.size());
+    set_coeffs(B, c->opt.k);
+  }
+  return PP_OK;
+}
+
+extern "C" int pp_batch_features(const pp_ctx* c, double* feat) {
+  if (!c || c->kind != 2 || !feat) return fail(nullptr, PP_EINVAL, "pp_batch_features: bad argument");
+  pp_batch_state* B = c->batch;
+  const int nb = B->d.nb;
+  std::vector<double> f4((size_t)nb * 4);
+  if (cudaMemcpy(f4.data(), B->feat, sizeof(double) * f4.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(nullptr, PP_ECUDA, "pp_batch_features: copy");
+  for (int i = 0; i < nb; ++i) {
+    const double n = B->n_h[i];
+    const double mean = f4[i * 4] / n;
+    const double var = std::max(0.0, f4[i * 4 + 1] / n - mean * mean);
+    double* o = feat + (size_t)i * PP_BATCH_NFEAT;
+    const double lo = B->ritz[(size_t)i * 5], hi = B->ritz[(size_t)i * 5 + 1];
+    o[0] = std::log10(n);
+    o[1] = mean;
+    o[2] = std::sqrt(var);
+    o[3] = f4[i * 4 + 2];
+    o[4] = f4[i * 4 + 3];
+    o[5] = lo > 0 ? std::log10(lo) : 0.0;
+    o[6] = hi > 0 ? std::log10(hi) : 0.0;
+    o[7] = (lo > 0 && hi > 0) ? std::log10(hi / lo) : 0.0;
+  }
+  return PP_OK;
+}
+
+extern "C" int pp_batch_solve(pp_ctx* c, const double* b, double* x, int* iters, int* status, pp_stats* st,
+                              void* stream) {
+  if (!c || c->kind != 2) return fail(c, PP_EINVAL, "not a batch context");
+  if (!b || !x) return fail(c, PP_EINVAL, "vector argument is NULL");
+  pp_batch_state* B = c->batch;
+  BatchDev& d = B->d;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int Bk = std::max(1, std::min(c->opt.check_every, kMaxCheck));
+  const bool graphs = c->opt.use_graphs != 0;
+  if (c->events.size() < 2) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t ev;
+      cudaEventCreate(&ev);
+      c->events.push_back(ev);
+    }
+  }
+  if (graphs && (!B->graph || B->graph_block != Bk)) {
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!B->cap) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pp_batch: capture");
+    cudaError_t e2 = cudaSuccess;
+    for (int i = 0; i < Bk && e2 == cudaSuccess; ++i) e2 = b_iteration(B, B->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(B->cap, &g);
+    if (e2 != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(c, e2 != cudaSuccess ? e2 : e, "pp_batch: capture");
+    }
+    e = cudaGraphInstantiate(&B->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pp_batch: graph instantiate");
+    B->graph_block = Bk;
+  }
+  const int nc = d.ncols;
+  cudaError_t e = cudaEventRecord(c->events[0], s);
+  int act = nc;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->c.n_active, &act, sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->c.done, 0, sizeof(int) * nc, s);
+  if (e == cudaSuccess) e = b_vec<kBScaleIn>(B, b, nullptr, 0, s);
+  if (e == cudaSuccess) e = b_reduce(B, kRedBB, nullptr, 0, s);
+  if (e == cudaSuccess) e = b_precond(B, s);
+  if (e == cudaSuccess) e = b_vec<kBUpdP>(B, nullptr, nullptr, 1, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pp_batch_solve start");
+  long long launches = 0;
+  const long long k = c->opt.k;
+  const long long pre = k == 0 ? 2 : (B->apply_prec == PP_PREC_F32 ? k + 3 : k + 2);
+  const long long per_it = 5 + pre;
+  launches += 3 + pre + 1;
+  for (int guard = 0;; ++guard) {
+    if (graphs) {
+      e = cudaGraphLaunch(B->graph, s);
+    } else {
+      for (int i = 0; i < Bk && e == cudaSuccess; ++i) e = b_iteration(B, s);
+    }
+    launches += per_it * Bk;
+    int host_act = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host_act, B->c.n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pp_batch_solve iteration");
+    if (host_act <= 0) break;
+    if ((long long)guard * Bk > (long long)c->opt.maxit + 2LL * Bk) break;  // every column hits maxit before this
+  }
+  if (e == cudaSuccess) e = b_vec<kBScaleOut>(B, nullptr, x, 0, s);
+  launches += 1;
+  if (e == cudaSuccess) e = cudaEventRecord(c->events[1], s);
+  std::vector<int> hi(nc), hs(nc);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hi.data(), B->c.iter, sizeof(int) * nc, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), B->c.status, sizeof(int) * nc, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pp_batch_solve finish");
+  if (iters) std::memcpy(iters, hi.data(), sizeof(int) * nc);
+  if (status) std::memcpy(status, hs.data(), sizeof(int) * nc);
+  int worst = PP_OK, maxit = 0;
+  for (int g = 0; g < nc; ++g) {
+    maxit = std::max(maxit, hi[g]);
+    if (hs[g] < 0) worst = std::min(worst, hs[g]);
+    else if (hs[g] == PP_MAXIT && worst == PP_OK) worst = PP_MAXIT;
+  }
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->iterations = maxit;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->events[0], c->events[1]);
+    st->t_solve_ms = ms;
+    st->kernel_launches = launches;
+    st->status = worst;
+  }
+  return worst;
+}

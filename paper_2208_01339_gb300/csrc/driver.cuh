@@ -9,6 +9,8 @@
 #include "../../include/polyprec.h"
 #include "kernels.cuh"
 
+struct pp_batch_state;  // batched.cu
+
 namespace pp {
 
 constexpr int kMaxGrid = 152 * 16;   // upper bound on blocks of any reducing kernel
@@ -37,6 +39,9 @@ int setup_interval_and_coeffs(pp_ctx* c, cudaStream_t s);
 cudaError_t op_step(pp_ctx* c, bool apply_matrix, const StepParams& p, const Scalars* skip, unsigned int* counter,
                     cudaStream_t s);
 void destroy_ctx_resources(pp_ctx* c);
+
+// batched.cu
+void batch_free(pp_batch_state* b);
 
 // schur.cu
 cudaError_t schur_scaled_step(pp_ctx* c, const StepParams& p, const Scalars* skip, unsigned int* counter,
@@ -77,5 +82,6 @@ struct pp_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   int graph_block = 0;
   pp::SchurImpl* schur = nullptr;
+  pp_batch_state* batch = nullptr;
   int op_launches = 1;  // kernel launches per operator step (1 for a matrix)
 };

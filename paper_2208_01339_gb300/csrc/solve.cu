@@ -240,6 +240,8 @@ void destroy_ctx_resources(pp_ctx* c) {
   c->cap_stream = nullptr;
   if (c->schur) schur_free(c->schur);
   c->schur = nullptr;
+  if (c->batch) batch_free(c->batch);
+  c->batch = nullptr;
 }
 
 }  // namespace pp

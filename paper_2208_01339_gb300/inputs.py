@@ -462,3 +462,40 @@ def tiny_fracture_network(seed: int = 7) -> FractureNetwork:
     """3 fractures of about 5 x 6 nodes and 3 traces, for dense checks."""
     return fracture_network(n_f=3, side_min=1.4, side_max=1.8, h=0.25, trace_min=0.75, trace_max=1.25,
                             trace_fraction=10.0, seed=seed, max_traces=3)
+
+
+# ---------------------------------------------------------------------------
+# Batched workload: many uneven diffusion instances with several RHS each
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class BatchSpec:
+    N: int
+    sigma_ln: float
+    nrhs: int
+    seed: int
+
+
+def batch_specs(count: int = 64, seed: int = 4, nmin: int = 48, nmax: int = 160, smin: float = 0.5,
+                smax: float = 3.0, rmin: int = 1, rmax: int = 8) -> list:
+    """Instance i: grid N ~ U{nmin..nmax}, lognormal sigma ~ U[smin, smax],
+    nrhs ~ U{rmin..rmax}, matrix seed 1000*seed + i (stream STREAM_BATCH)."""
+    u = uniform(seed, STREAM_BATCH + 10, 3 * count)
+    out = []
+    for i in range(count):
+        N = nmin + min(int(u[3 * i] * (nmax - nmin + 1)), nmax - nmin)
+        s = smin + (smax - smin) * u[3 * i + 1]
+        r = rmin + min(int(u[3 * i + 2] * (rmax - rmin + 1)), rmax - rmin)
+        out.append(BatchSpec(N, float(s), r, 1000 * seed + i))
+    return out
+
+
+def batch_instance(spec: BatchSpec) -> CSR:
+    return diffusion3d(spec.N, spec.sigma_ln, seed=spec.seed)
+
+
+def batch_rhs(spec: BatchSpec) -> np.ndarray:
+    """N(0,1) right-hand sides, shape (n, nrhs), row-major [row][rhs]."""
+    n = spec.N ** 3
+    return normal(spec.seed, STREAM_RHS_NORMAL, n * spec.nrhs).reshape(n, spec.nrhs)

@@ -73,6 +73,13 @@ class Info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nnz", ctypes.c_longlong), ("rowptr", _vp), ("col", _vp), ("val", _vp),
+                ("nrhs", ctypes.c_int)]
+
+
+BATCH_NFEAT = 8
+
 _DFN_MATS = ("C", "B", "CT", "BT", "Gh", "Gu")
 
 
@@ -108,6 +115,13 @@ SIGNATURES = [
     ("schur_rhs", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("schur_recover", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("schur_ainv", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("pp_batch_workspace_size", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(Options),
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    ("pp_batch_setup", ctypes.c_int, [ctypes.POINTER(_vp), _vp, ctypes.c_int, ctypes.POINTER(Options), _vp,
+                                      ctypes.c_size_t, _vp]),
+    ("pp_batch_intervals", ctypes.c_int, [_vp, _vp, _vp]),
+    ("pp_batch_features", ctypes.c_int, [_vp, _vp]),
+    ("pp_batch_solve", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(Stats), _vp]),
     ("polyprec_apply_csr_static", ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp]),
 ]
@@ -351,3 +365,81 @@ class SchurSolver(Solver):
         y = torch.empty_like(v)
         _check(lib().schur_ainv(self.ctx, _ptr(v), _ptr(y), _stream(stream)), self.ctx)
         return y
+
+
+class BatchSolver:
+    """Many SPD instances (each with 1..8 right-hand sides) solved together
+    by one set of persistent launches (pp_batch_setup / pp_batch_solve)."""
+
+    def __init__(self, mats, nrhs, device="cuda", stream=None, **options):
+        torch = _torch()
+        self.opts = make_options(**options)
+        self.nrhs = [int(r) for r in nrhs]
+        self.sizes = [int(A.n) for A in mats]
+        items = (BatchItem * len(mats))()
+        keep = []
+        for i, A in enumerate(mats):
+            rp, ci, va = to_device_csr(A, device)
+            keep.append((rp, ci, va))
+            items[i] = BatchItem(A.n, int(A.nnz), _ptr(rp), _ptr(ci), _ptr(va), self.nrhs[i])
+        self._items = items
+        nbytes = ctypes.c_size_t()
+        _check(lib().pp_batch_workspace_size(ctypes.cast(items, _vp), len(mats), ctypes.byref(self.opts),
+                                             ctypes.byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=device)
+        ctx = _vp()
+        _check(lib().pp_batch_setup(ctypes.byref(ctx), ctypes.cast(items, _vp), len(mats), ctypes.byref(self.opts),
+                                    _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
+        self.ctx = ctx
+        del keep  # the matrices are copied into the workspace at setup
+        self.device = torch.device(device)
+        self.ncols = sum(self.nrhs)
+        self.offsets = np.concatenate([[0], np.cumsum([n * r for n, r in zip(self.sizes, self.nrhs)])]).astype(np.int64)
+
+    def intervals(self, abx=None) -> np.ndarray:
+        out = np.zeros((self.ncols, 3))
+        inp = None if abx is None else np.ascontiguousarray(abx, dtype=np.float64).reshape(self.ncols, 3)
+        _check(lib().pp_batch_intervals(self.ctx, _vp(out.ctypes.data), None if inp is None else _vp(inp.ctypes.data)),
+               self.ctx)
+        return out
+
+    def features(self) -> np.ndarray:
+        f = np.zeros((len(self.sizes), BATCH_NFEAT))
+        _check(lib().pp_batch_features(self.ctx, _vp(f.ctypes.data)), self.ctx)
+        return f
+
+    def pack(self, blocks) -> "object":
+        """Concatenate per-instance (n_i, nrhs_i) arrays into one device vector."""
+        torch = _torch()
+        flat = np.concatenate([np.ascontiguousarray(b, dtype=np.float64).reshape(-1) for b in blocks])
+        return torch.as_tensor(flat, device=self.device)
+
+    def unpack(self, x):
+        h = x.detach().cpu().numpy()
+        return [h[self.offsets[i]:self.offsets[i + 1]].reshape(self.sizes[i], self.nrhs[i])
+                for i in range(len(self.sizes))]
+
+    def solve(self, b, x=None, stream=None, allow=(PP_OK, PP_MAXIT)):
+        torch = _torch()
+        if x is None:
+            x = torch.zeros_like(b)
+        it = np.zeros(self.ncols, dtype=np.int32)
+        stv = np.zeros(self.ncols, dtype=np.int32)
+        st = Stats()
+        rc = lib().pp_batch_solve(self.ctx, _ptr(b), _ptr(x), _vp(it.ctypes.data), _vp(stv.ctypes.data),
+                                  ctypes.byref(st), _stream(stream))
+        _check(rc, self.ctx, allow)
+        d = st.as_dict()
+        d["status"] = rc
+        return x, it, stv, d
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().pp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

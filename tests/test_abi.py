@@ -48,6 +48,7 @@ def test_struct_layouts_match_c(tmp_path):
         "pp_stats": [f for f, _ in P.Stats._fields_],
         "pp_info": [f for f, _ in P.Info._fields_],
         "pp_dfn": [f for f, _ in P.Dfn._fields_],
+        "pp_batch_item": [f for f, _ in P.BatchItem._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for st, fs in fields.items():
@@ -61,7 +62,7 @@ def test_struct_layouts_match_c(tmp_path):
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
     c = {k: int(v) for k, v in (ln.split() for ln in out if ln.strip())}
     for st, cls in (("pp_csr", P.Csr), ("pp_options", P.Options), ("pp_stats", P.Stats), ("pp_info", P.Info),
-                    ("pp_dfn", P.Dfn)):
+                    ("pp_dfn", P.Dfn), ("pp_batch_item", P.BatchItem)):
         assert c[st] == ctypes.sizeof(cls), st
         for f, _ in cls._fields_:
             assert c[f"{st}.{f}"] == getattr(cls, f).offset, f"{st}.{f}"

@@ -1,0 +1,136 @@
+"""GPU parity of the batched solver (many instances, many right-hand sides,
+one global slice list) against the FP64 oracle, column by column.
+
+FP64 apply: every column's iteration count and solution equal those of the
+oracle's single solve with the same interval (Lanczos from the same start
+vector, or the interval set for that column) -- solution within 1e-10.
+FP32 apply: converges to rtol, within 1e-7 of the oracle solution.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import rel
+from paper_2208_01339_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2208_01339_gb300.polyprec")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+SPECS = [I.BatchSpec(6, 0.5, 1, 11), I.BatchSpec(9, 2.0, 3, 12), I.BatchSpec(5, 1.0, 2, 13),
+         I.BatchSpec(11, 3.0, 4, 14), I.BatchSpec(8, 1.5, 8, 15)]
+
+
+@pytest.fixture(scope="module")
+def problem():
+    mats = [I.batch_instance(s) for s in SPECS]
+    rhs = [I.batch_rhs(s) for s in SPECS]
+    return mats, rhs
+
+
+def oracle_cols(mats, rhs, k, seed, steps, abx=None, rtol=1e-10, flexible=False):
+    out = []
+    g = 0
+    for i, (A, B) in enumerate(zip(mats, rhs)):
+        for r in range(B.shape[1]):
+            if abx is None:
+                x, st = O.pcg_csr(A, B[:, r], v0=I.lanczos_start(A.n, seed + i), k=k, lanczos_steps=steps, rtol=rtol,
+                                  flexible=flexible)
+            else:
+                a, b, xi = abx[g]
+                x, st = O.pcg_csr(A, B[:, r], k=k, interval="given", alpha=a, beta=b, xi=xi, rtol=rtol,
+                                  flexible=flexible)
+            out.append((x, st))
+            g += 1
+    return out
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+@pytest.mark.parametrize("k", [0, 1, 6])
+def test_batch_f64_matches_oracle_per_column(problem, graphs, k):
+    mats, rhs = problem
+    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=k, lanczos_steps=10, seed=3, rtol=1e-10, use_graphs=graphs,
+                      check_every=3)
+    x, it, stv, st = S.solve(S.pack(rhs))
+    xs = S.unpack(x)
+    ref = oracle_cols(mats, rhs, k, 3, 10)
+    g = 0
+    for i, Xi in enumerate(xs):
+        for r in range(Xi.shape[1]):
+            xo, so = ref[g]
+            assert stv[g] == 0 and so["status"] == 0
+            assert it[g] == so["iterations"], (i, r)
+            assert rel(Xi[:, r], xo) <= 1e-10
+            g += 1
+    abx = S.intervals()
+    for i, A in enumerate(mats):
+        vh, _ = O.jacobi_scale(A)
+        a, b = O.lanczos(A, I.lanczos_start(A.n, 3 + i), 10, val=vh)
+        lo, hi = O.tridiag_extremes(a, b)
+        c0 = sum(s.nrhs for s in SPECS[:i])
+        assert abx[c0, 0] == pytest.approx(lo, rel=1e-9) and abx[c0, 1] == pytest.approx(hi, rel=1e-9)
+
+
+def test_batch_per_column_intervals(problem):
+    mats, rhs = problem
+    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=5, rtol=1e-10)
+    abx = S.intervals()
+    u = I.uniform(7, 9, 3 * S.ncols)
+    abx[:, 0] *= 0.3 + u[0::3]        # different interval and xi in every column
+    abx[:, 1] *= 1.0 + 0.2 * u[1::3]
+    abx[:, 2] = 10.0 ** (-5 + 3 * u[2::3])
+    S.intervals(abx)
+    x, it, stv, st = S.solve(S.pack(rhs))
+    ref = oracle_cols(mats, rhs, 5, 0, 10, abx=abx)
+    xs = S.unpack(x)
+    g = 0
+    for Xi in xs:
+        for r in range(Xi.shape[1]):
+            xo, so = ref[g]
+            assert it[g] == so["iterations"]
+            assert rel(Xi[:, r], xo) <= 1e-10
+            g += 1
+
+
+def test_batch_f32_apply_converges(problem):
+    mats, rhs = problem
+    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=6, rtol=1e-9, apply_prec="f32", flexible=1, use_graphs=1)
+    x, it, stv, st = S.solve(S.pack(rhs))
+    assert (stv == 0).all()
+    xs = S.unpack(x)
+    ref = oracle_cols(mats, rhs, 6, 0, 10, rtol=1e-12)
+    g = 0
+    for i, Xi in enumerate(xs):
+        for r in range(Xi.shape[1]):
+            assert rel(Xi[:, r], ref[g][0]) <= 1e-7
+            assert it[g] <= 2 * ref[g][1]["iterations"] + 5
+            g += 1
+
+
+def test_batch_zero_rhs_column_and_features(problem):
+    mats, rhs = problem
+    rhs = [b.copy() for b in rhs]
+    rhs[1][:, 1] = 0.0
+    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=3, rtol=1e-9)
+    x, it, stv, st = S.solve(S.pack(rhs))
+    assert it[SPECS[0].nrhs + 1] == 0 and stv[SPECS[0].nrhs + 1] == 0
+    assert not S.unpack(x)[1][:, 1].any()
+    F = S.features()
+    for i, A in enumerate(mats):
+        d = np.diag(A.to_dense())
+        assert F[i, 0] == pytest.approx(np.log10(A.n))
+        assert F[i, 1] == pytest.approx(np.log(d).mean(), rel=1e-12, abs=1e-12)
+        assert F[i, 2] == pytest.approx(np.log(d).std(), rel=1e-9, abs=1e-12)
+        vh, _ = O.jacobi_scale(A)
+        Ah = I.CSR(A.n, A.rowptr, A.col, vh).to_dense()
+        off = np.abs(Ah).sum(axis=1) - np.diag(Ah)
+        assert F[i, 3] == pytest.approx((np.diag(Ah) + off).max(), rel=1e-12)
+        assert F[i, 4] == pytest.approx((np.diag(Ah) - off).min(), rel=1e-12, abs=1e-12)
