@@ -284,6 +284,38 @@ int pp_batch_features(const pp_ctx* ctx, double* feat);
 int pp_batch_solve(pp_ctx* ctx, const double* b, double* x, int* iters, int* status,
                    pp_stats* stats, void* stream);
 
+/* ---- learned interval predictor --------------------------------------- */
+
+/* A 3-layer MLP (PP_MLP_NIN -> 128 -> 128 -> PP_MLP_NOUT, ReLU) that maps
+ * the cheap instance statistics of pp_batch_features to the multipliers of
+ * the Lanczos interval and to xi.  The paper chooses xi by hand sweeps
+ * (Section 6); this predictor has no counterpart there.  BF16 weights and
+ * activations with FP32 accumulation on the tensor cores, FP32 master
+ * parameters, Adam.  Parameter layout (FP32, PP_MLP_NPARAM): W1 [128 x 16]
+ * (columns >= 8 zero), b1 [128], W2 [128 x 128], b2 [128], W3 [8 x 128]
+ * (rows >= 3 zero), b3 [8] (entries >= 3 zero).  x, y, t: device FP32,
+ * row-major [batch x 8], [batch x 3], [batch x 3]. */
+#define PP_MLP_NIN 8
+#define PP_MLP_NHID 128
+#define PP_MLP_NOUT 3
+#define PP_MLP_NPARAM 19720
+typedef struct pp_mlp pp_mlp;
+int pp_mlp_workspace_size(int max_batch, size_t* bytes);
+/* He-uniform weights from SplitMix64 (seed, stream 7), zero biases. */
+int pp_mlp_create(pp_mlp** mlp, int max_batch, unsigned long long seed, void* workspace,
+                  size_t ws_bytes);
+/* Copy the FP32 master parameters out (get_host) and/or in (set_host). */
+int pp_mlp_params(pp_mlp* mlp, float* get_host, const float* set_host);
+int pp_mlp_forward(pp_mlp* mlp, const float* x, float* y, int batch, void* stream);
+/* Loss (1/(2 batch)) sum ||y - t||^2 and its gradient (host, PP_MLP_NPARAM),
+ * parameters unchanged.  Synchronous. */
+int pp_mlp_grad(pp_mlp* mlp, const float* x, const float* t, int batch, float* loss_host,
+                float* grad_host, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the same loss. */
+int pp_mlp_train_step(pp_mlp* mlp, const float* x, const float* t, int batch, float lr,
+                      float* loss_host, void* stream);
+int pp_mlp_destroy(pp_mlp* mlp);
+
 /* ---- workspace-free apply (no counterpart in the paper) ---------------- */
 
 /* z = p_k(A) r for a CSR matrix on the device, without a workspace and

@@ -1,0 +1,212 @@
+"""Learned spectral interval and scaling parameter.
+
+The paper picks xi by hand sweeps per problem (Section 6) and the interval
+from an eigenvalue estimate.  Here a small MLP predicts, from cheap
+statistics of an instance (pp_batch_features: size, diagonal statistics,
+Gershgorin bounds, extreme Ritz values of a short Lanczos run), three
+numbers: multipliers s_alpha, s_beta of the Lanczos interval and xi.  Its
+training labels are found by the method itself: every training instance is
+solved for a grid of (s_alpha, s_beta, xi) settings in one batched solve
+(one column per setting), and the setting with the fewest CG iterations is
+the label.  Training runs on the GPU through the library's MLP kernels.
+
+At inference the prediction is used unless it is non-finite or its beta
+falls outside the Gershgorin bound (or alpha >= beta); then the Lanczos
+interval with xi = clip(10 alpha/beta, 1e-6, 1e-2) is used instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import inputs as I
+from . import polyprec as P
+
+S_ALPHA = (1.0, 0.3, 0.1, 0.03)
+S_BETA = (1.0, 1.1)
+XIS = (1e-4, 1e-3, 1e-2, 5e-2)
+SETTINGS = [(a, b, x) for a in S_ALPHA for b in S_BETA for x in XIS]  # 32 settings, 4 items x 8 columns
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mlp_weights.npz")
+
+
+def auto_xi(alpha, beta):
+    return float(min(max(10.0 * alpha / beta, 1e-6), 1e-2))
+
+
+def training_specs(count: int, seed: int = 5, nmin: int = 12, nmax: int = 40):
+    specs = I.batch_specs(count, seed=seed, nmin=nmin, nmax=nmax, rmin=8, rmax=8)
+    return specs
+
+
+def sweep(specs, k: int = 20, chunk: int = 200, device="cuda", maxit: int = 600, lanczos_steps: int = 10):
+    """Iteration counts of every setting for every instance.
+
+    Returns (features [n x 8], iterations [n x 32] with failures as inf,
+    base intervals [n x 2])."""
+    import torch
+
+    feats, iters, base = [], [], []
+    reps = len(SETTINGS) // 8
+    for c0 in range(0, len(specs), chunk):
+        part = specs[c0:c0 + chunk]
+        mats = [I.batch_instance(s) for s in part]
+        items = [A for A in mats for _ in range(reps)]
+        S = P.BatchSolver(items, [8] * len(items), device=device, k=k, lanczos_steps=lanczos_steps, rtol=1e-8,
+                          maxit=maxit, use_graphs=1, check_every=10)
+        abx = S.intervals()
+        F = S.features()
+        new = abx.copy()
+        for i in range(len(part)):
+            a0, b0 = abx[i * reps * 8, 0], abx[i * reps * 8, 1]
+            base.append((a0, b0))
+            feats.append(F[i * reps])
+            for j, (sa, sb, xi) in enumerate(SETTINGS):
+                g = i * reps * 8 + j
+                new[g] = (a0 * sa, b0 * sb, xi)
+        S.intervals(new)
+        rhs = []
+        for s in part:
+            b = I.rhs_normal(s.N ** 3, s.seed)
+            blk = np.repeat(b[:, None], 8, axis=1)
+            rhs.extend([blk] * reps)
+        _, it, st, _ = S.solve(S.pack(rhs), allow=(0, 1, -2, -3))
+        it = it.astype(np.float64)
+        it[st != 0] = np.inf
+        iters.extend(it.reshape(len(part), len(SETTINGS)))
+        S.close()
+        del S
+        torch.cuda.synchronize()
+    return np.array(feats), np.array(iters), np.array(base)
+
+
+def labels(iters):
+    """Best setting per instance (first of equal counts) as log10 targets."""
+    best = np.argmin(iters, axis=1)
+    y = np.array([[np.log10(SETTINGS[j][0]), np.log10(SETTINGS[j][1]), np.log10(SETTINGS[j][2])] for j in best])
+    return y, best
+
+
+class Model:
+    """MLP weights plus the feature/target normalisation."""
+
+    def __init__(self, params, mu_x, sd_x, mu_y, sd_y):
+        self.params = np.asarray(params, dtype=np.float32)
+        self.mu_x, self.sd_x = np.asarray(mu_x), np.asarray(sd_x)
+        self.mu_y, self.sd_y = np.asarray(mu_y), np.asarray(sd_y)
+
+    def save(self, path=WEIGHTS):
+        np.savez(path, params=self.params, mu_x=self.mu_x, sd_x=self.sd_x, mu_y=self.mu_y, sd_y=self.sd_y)
+
+    @classmethod
+    def load(cls, path=WEIGHTS):
+        z = np.load(path)
+        return cls(z["params"], z["mu_x"], z["sd_x"], z["mu_y"], z["sd_y"])
+
+    def predict(self, feats, device="cuda"):
+        net = P.Mlp(max_batch=max(16, len(feats)), device=device)
+        net.params(self.params)
+        y = net.forward((feats - self.mu_x) / self.sd_x)
+        net.close()
+        return y * self.sd_y + self.mu_y
+
+
+def train(feats, targets, steps: int = 1500, lr: float = 3e-3, seed: int = 0, device="cuda"):
+    mu_x = feats.mean(axis=0)
+    sd_x = feats.std(axis=0) + 1e-6
+    mu_y = targets.mean(axis=0)
+    sd_y = targets.std(axis=0) + 1e-6
+    X = (feats - mu_x) / sd_x
+    Y = (targets - mu_y) / sd_y
+    net = P.Mlp(max_batch=max(16, len(X)), seed=seed, device=device)
+    losses = [net.train_step(X, Y, lr) for _ in range(steps)]
+    m = Model(net.params(), mu_x, sd_x, mu_y, sd_y)
+    net.close()
+    return m, losses
+
+
+def predicted_intervals(model: Model, feats, base, device="cuda"):
+    """(alpha, beta, xi) per instance from the model, with the Lanczos fallback."""
+    y = model.predict(feats, device)
+    out, used = [], []
+    for i in range(len(feats)):
+        a0, b0 = base[i]
+        sa, sb, xi = 10.0 ** y[i]
+        a, b = a0 * sa, b0 * sb
+        gersh = feats[i, 3]
+        ok = np.isfinite([a, b, xi]).all() and 0 < a < b and b <= 1.05 * gersh and 1e-7 <= xi <= 0.1
+        if ok:
+            out.append((a, b, xi))
+        else:
+            out.append((a0, b0, auto_xi(a0, b0)))
+        used.append(bool(ok))
+    return np.array(out), np.array(used)
+
+
+def evaluate(specs, model: Model | None, k: int = 20, device="cuda", apply_prec="f64", maxit: int = 2000):
+    """Iterations and solve time of the batched solver on `specs` with the
+    fallback interval and, if a model is given, with the predicted one."""
+    import torch
+
+    mats = [I.batch_instance(s) for s in specs]
+    rhs = [I.batch_rhs(s) for s in specs]
+    S = P.BatchSolver(mats, [s.nrhs for s in specs], device=device, k=k, lanczos_steps=10, rtol=1e-8, maxit=maxit,
+                      apply_prec=apply_prec, flexible=1 if apply_prec == "f32" else 0, use_graphs=1, check_every=10)
+    bt = S.pack(rhs)
+    res = {}
+    abx0 = S.intervals()
+    for name in ("fallback",) + (("mlp",) if model is not None else ()):
+        if name == "mlp":
+            feats = S.features()
+            cols = np.cumsum([0] + [s.nrhs for s in specs])
+            base = np.array([abx0[cols[i], :2] for i in range(len(specs))])
+            ab, used = predicted_intervals(model, feats, base, device)
+            new = np.concatenate([np.repeat(ab[i:i + 1], specs[i].nrhs, axis=0) for i in range(len(specs))])
+            S.intervals(new)
+            res["mlp_used"] = int(used.sum())
+        else:
+            S.intervals(abx0)
+        S.solve(bt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, it, st, stats = S.solve(bt)
+        torch.cuda.synchronize()
+        res[name] = {"time_s": time.perf_counter() - t0, "iterations_mean": float(it.mean()),
+                     "iterations_max": int(it.max()), "converged": int((st == 0).sum()), "columns": int(len(it))}
+    S.close()
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser(description="sweep, train and evaluate the interval/xi predictor")
+    ap.add_argument("--count", type=int, default=2000)
+    ap.add_argument("--eval-count", type=int, default=64)
+    ap.add_argument("--k", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--report", default=None)
+    args = ap.parse_args()
+    t0 = time.perf_counter()
+    specs = training_specs(args.count)
+    feats, iters, base = sweep(specs, k=args.k)
+    y, best = labels(iters)
+    t_sweep = time.perf_counter() - t0
+    model, losses = train(feats, y, steps=args.steps)
+    model.save(args.out)
+    ev_specs = I.batch_specs(args.eval_count, seed=4)
+    ev = evaluate(ev_specs, model, k=args.k, apply_prec="f32")
+    rep = {"instances": len(specs), "sweep_s": t_sweep, "loss_first": losses[0], "loss_last": losses[-1],
+           "label_histogram": np.bincount(best, minlength=len(SETTINGS)).tolist(),
+           "fallback_iters_mean_train": float(iters[:, SETTINGS.index((1.0, 1.0, 1e-3))].mean()),
+           "best_iters_mean_train": float(iters.min(axis=1).mean()), "eval": ev}
+    print(json.dumps(rep))
+    if args.report:
+        with open(args.report, "w") as fh:
+            json.dump(rep, fh, indent=1)
+
+
+if __name__ == "__main__":
+    main()

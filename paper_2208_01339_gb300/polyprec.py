@@ -122,6 +122,13 @@ SIGNATURES = [
     ("pp_batch_intervals", ctypes.c_int, [_vp, _vp, _vp]),
     ("pp_batch_features", ctypes.c_int, [_vp, _vp]),
     ("pp_batch_solve", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(Stats), _vp]),
+    ("pp_mlp_workspace_size", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    ("pp_mlp_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_ulonglong, _vp, ctypes.c_size_t]),
+    ("pp_mlp_params", ctypes.c_int, [_vp, _vp, _vp]),
+    ("pp_mlp_forward", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    ("pp_mlp_grad", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp]),
+    ("pp_mlp_train_step", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _vp, _vp]),
+    ("pp_mlp_destroy", ctypes.c_int, [_vp]),
     ("polyprec_apply_csr_static", ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp]),
 ]
@@ -437,6 +444,69 @@ class BatchSolver:
         if getattr(self, "ctx", None):
             lib().pp_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MLP_NIN, MLP_NHID, MLP_NOUT, MLP_NPARAM = 8, 128, 3, 19720
+
+
+class Mlp:
+    """The interval/xi predictor: forward, gradient and Adam steps run in the
+    library's tensor-core kernels (pp_mlp_*)."""
+
+    def __init__(self, max_batch: int = 4096, seed: int = 0, device="cuda"):
+        torch = _torch()
+        nbytes = ctypes.c_size_t()
+        _check(lib().pp_mlp_workspace_size(int(max_batch), ctypes.byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=device)
+        h = _vp()
+        _check(lib().pp_mlp_create(ctypes.byref(h), int(max_batch), int(seed), _ptr(self.workspace),
+                                   self.workspace.numel()))
+        self.h = h
+        self.device = torch.device(device)
+        self.max_batch = int(max_batch)
+
+    def params(self, new=None) -> np.ndarray:
+        out = np.zeros(MLP_NPARAM, dtype=np.float32)
+        inp = None if new is None else np.ascontiguousarray(new, dtype=np.float32)
+        _check(lib().pp_mlp_params(self.h, _vp(out.ctypes.data), None if inp is None else _vp(inp.ctypes.data)))
+        return out if new is None else inp
+
+    def _f32(self, a):
+        torch = _torch()
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=self.device)
+
+    def forward(self, x) -> np.ndarray:
+        xt = self._f32(x)
+        B = xt.shape[0]
+        y = _torch().empty((B, MLP_NOUT), dtype=_torch().float32, device=self.device)
+        _check(lib().pp_mlp_forward(self.h, _ptr(xt), _ptr(y), B, _stream(None)))
+        return y.cpu().numpy()
+
+    def grad(self, x, t):
+        xt, tt = self._f32(x), self._f32(t)
+        loss = ctypes.c_float()
+        g = np.zeros(MLP_NPARAM, dtype=np.float32)
+        _check(lib().pp_mlp_grad(self.h, _ptr(xt), _ptr(tt), xt.shape[0], _vp(ctypes.addressof(loss)),
+                                 _vp(g.ctypes.data), _stream(None)))
+        return float(loss.value), g
+
+    def train_step(self, x, t, lr: float) -> float:
+        xt, tt = self._f32(x), self._f32(t)
+        loss = ctypes.c_float()
+        _check(lib().pp_mlp_train_step(self.h, _ptr(xt), _ptr(tt), xt.shape[0], float(lr),
+                                       _vp(ctypes.addressof(loss)), _stream(None)))
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pp_mlp_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:
