@@ -78,6 +78,22 @@ def bytes_per_step_launch(nnz: int, n: int, k: int, prec: str) -> float:
     return (k * nnz * (sa + 4) + n * sv * vec_passes) / k
 
 
+def flops_per_step_launch(nnz: int, n: int, k: int) -> float:
+    """Arithmetic of one fused degree step, averaged over the k steps: one
+    fused multiply-add per stored nonzero, then per row 3 flops in the first
+    step (y = ca r + cb A r) and 6 in the others (y = ca x + cb x_old +
+    cc (r - A x))."""
+    if k <= 0:
+        return 0.0
+    return 2.0 * nnz + n * (3.0 + 6.0 * (k - 1)) / k
+
+
+def fp64_peak_tflops() -> float:
+    """152 SMs x 2 FP64 FMA per clock per SM (4 flop) x 2.07 GHz: the nominal
+    1.25 TFLOP/s FP64 rate of GB300 expressed in unit counts and clocks."""
+    return 152 * 4 * 2.07e9 / 1e12
+
+
 def source_sha() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2208_01339_gb300", "csrc")
@@ -222,6 +238,31 @@ def run_reference(args, w, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_k_sweep(args, w, A, b, opts, dev):
+    """Degree sweep: one line per k with the time to rtol and iterations."""
+    import torch
+
+    from paper_2208_01339_gb300 import polyprec as P
+
+    bt = torch.as_tensor(b, device=dev)
+    for k in [int(v) for v in args.k_sweep.split(",")]:
+        o = dict(opts)
+        o["k"] = k
+        S = P.Solver.from_host(A, device=dev, **o)
+        for _ in range(2):
+            S.solve(bt)
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(max(1, args.steps)):
+            x, st = S.solve(bt)
+            ts.append(st["t_solve_ms"])
+        apply_us = st["t_apply_ms"] / max(1, st["apply_launches"]) * 1e3
+        print(json.dumps({"workload": args.workload, "prec": w["prec"], "k": k, "iterations": st["iterations"],
+                          "time_s": statistics.median(ts) / 1e3, "mvp": st["mvp"], "dots": st["dots"],
+                          "step_us": round(apply_us, 2), "status": st["status"]}), flush=True)
+        S.close()
+
+
 def run_batch(args, w, specs, k, dev, world, rank):
     """Config-5 shape: many uneven instances with several RHS each, solved by
     the batched solver (FP32 p_k, FP64 flexible CG, CUDA graphs) and, for
@@ -236,6 +277,17 @@ def run_batch(args, w, specs, k, dev, world, rank):
     S = P.BatchSolver(mats, [s.nrhs for s in specs], device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8,
                       apply_prec=w["prec"], flexible=1, use_graphs=1, check_every=10, maxit=5000)
     bt = S.pack(rhs)
+    mlp_used = 0
+    from paper_2208_01339_gb300 import learn as Lrn
+
+    if os.path.exists(Lrn.WEIGHTS):
+        model = Lrn.Model.load()
+        abx0 = S.intervals()
+        cols = np.cumsum([0] + [s.nrhs for s in specs])
+        base = np.array([abx0[cols[i], :2] for i in range(len(specs))])
+        ab, used = Lrn.predicted_intervals(model, S.features(), base, device=dev)
+        S.intervals(np.concatenate([np.repeat(ab[i:i + 1], specs[i].nrhs, axis=0) for i in range(len(specs))]))
+        mlp_used = int(used.sum())
     for _ in range(max(3, args.warmup)):
         S.solve(bt)
     torch.cuda.synchronize(dev)
@@ -278,7 +330,8 @@ def run_batch(args, w, specs, k, dev, world, rank):
                "vs_baseline": None, "dtype": w["prec"], "data": "synthetic",
                "config": {"workload": args.workload, "instances": len(specs), "rows": rows,
                           "columns": int(sum(s.nrhs for s in specs)), "k": k, "apply": w["prec"],
-                          "outer": "f64 flexible CG", "graphs": 1},
+                          "outer": "f64 flexible CG", "graphs": 1, "interval": f"mlp ({mlp_used} instances)"
+                          if mlp_used else "lanczos"},
                "iterations_max": int(max(stats[-1]["iterations"], 0)),
                "sequential_f64_s": t_seq, "speedup_vs_sequential_f64": t_seq / (ms / 1e3),
                "max_rel_diff_vs_f64": err, "iterations_f64_max": int(max(its64)),
@@ -336,6 +389,7 @@ def main():
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--k-sweep", default="", help="comma-separated degrees: time one solve per degree instead")
     ap.add_argument("--batch-count", type=int, default=0, help="override the batched workload's instance count")
     ap.add_argument("--batch-nmax", type=int, default=0, help="override the batched workload's largest grid")
     args = ap.parse_args()
@@ -379,6 +433,8 @@ def main():
     opts = dict(k=k, lanczos_steps=w["lanczos"], format=w["fmt"], apply_prec=w["prec"], rtol=1e-8,
                 check_every=args.check_every, use_graphs=args.graphs, flexible=w.get("flexible", 0),
                 sell_variant=args.sell_variant, sell_C=args.sell_C, sell_sigma=args.sell_sigma)
+    if args.k_sweep:
+        return run_k_sweep(args, w, A, b, opts, dev)
     S = P.Solver.from_host(A, device=dev, **opts)
     info = S.info()
     bt = torch.as_tensor(b, device=dev)
@@ -449,11 +505,25 @@ def main():
         avg_s = t_apply / 1e3 / n_launch
         peak, peak_src = measured_peak()
         ach = bpl / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                "traffic": traffic_from_profile(args.workload, k, w["prec"]), "peak_source": peak_src,
-                "kernel": f"sell_step_kernel ({w['prec']}, C={info['sell_C']})" if info["format"] == 2 else
-                f"csr_step_kernel ({w['prec']})",
-                "algorithmic_bytes_per_launch": int(bpl), "avg_launch_us": round(avg_s * 1e6, 2)}
+        kname = (f"sell_step_{'tma_' if args.sell_variant != 1 else ''}kernel ({w['prec']}, C={info['sell_C']})"
+                 if info["format"] == 2 else f"csr_step_kernel ({w['prec']})")
+        hbm = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+               "traffic": traffic_from_profile(args.workload, k, w["prec"]), "peak_source": peak_src,
+               "kernel": kname, "algorithmic_bytes_per_launch": int(bpl), "avg_launch_us": round(avg_s * 1e6, 2)}
+        if w["prec"] == "f64":
+            # FP64 arithmetic is scarce on GB300: the step kernel is bound by the
+            # FP64 pipe before HBM (ncu: FP64 pipe ~77% busy, DRAM ~50%).
+            fl = flops_per_step_launch(A.nnz, A.n, k)
+            tf = fl / avg_s / 1e12
+            pk = fp64_peak_tflops()
+            roof = {"bound": "alu", "achieved": round(tf, 4), "peak": round(pk, 4), "unit": "TFLOP/s",
+                    "frac": round(tf / pk, 4), "traffic": hbm["traffic"],
+                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                    "kernel": kname, "algorithmic_flops_per_launch": int(fl), "avg_launch_us": hbm["avg_launch_us"],
+                    "hbm": {k2: hbm[k2] for k2 in ("achieved", "peak", "unit", "frac", "peak_source",
+                                                  "algorithmic_bytes_per_launch")}}
+        else:
+            roof = hbm
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         import oracle as O

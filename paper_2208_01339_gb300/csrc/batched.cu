@@ -85,6 +85,7 @@ struct pp_batch_state {
   double* lan_b2 = nullptr;  // [inst][m]
   double* nrm = nullptr;     // [inst]
   double *theta_bar = nullptr, *delta = nullptr, *sigma_bar = nullptr, *rho = nullptr;
+  double* coefT = nullptr;   // [j][column][3] folded step coefficients (cheb_step_coeffs)
   double* feat = nullptr;    // [inst][4] device feature sums
   std::vector<double> abx;   // host (alpha, beta, xi) per column
   std::vector<double> ritz;  // host: per instance, lanczos Ritz extremes and more
@@ -106,112 +107,169 @@ __device__ __forceinline__ T ldv(const T* p) {
 }
 
 // ------------------------------------------------------------- products ---
-// FP64 product over all slices: y = A x (kSpmv, partial (x, y)) or the
-// Lanczos step y = A x - sqrt(b2_prev) x_old on column 0 (partial (y, x)).
+// R consecutive vector entries of one row (the instance's right-hand sides).
+template <typename T, int R>
+struct RowVec {
+  T v[R];
+  __device__ __forceinline__ void load(const T* p) {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+#pragma unroll
+      for (int q = 0; q < (int)(sizeof(T) * R / 16); ++q) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(p) + q);
+        const T* t = reinterpret_cast<const T*>(&u);
+#pragma unroll
+        for (int e = 0; e < (int)(16 / sizeof(T)); ++e) v[q * (16 / sizeof(T)) + e] = t[e];
+      }
+    } else if constexpr (sizeof(T) * R == 8) {
+      const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+      const T* t = reinterpret_cast<const T*>(&u);
+#pragma unroll
+      for (int e = 0; e < R; ++e) v[e] = t[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < R; ++e) v[e] = __ldg(p + e);
+    }
+  }
+};
+
+__device__ __forceinline__ unsigned active_mask(const int* done, int g0, int R) {
+  unsigned m = 0;
+  for (int r = 0; r < R; ++r)
+    if (!done[g0 + r]) m |= 1u << r;
+  return m;
+}
+
+// FP64 product of one slice for R right-hand sides: y = A x with partials
+// (x, y) (kSpmv), or the Lanczos step on column 0 (R = 1 view).
+template <int R, int MODE>
+__device__ __forceinline__ void b_spmv_slice(const BatchDev& d, long long s, int i, int RS, const double* x,
+                                             const double* xold, double* y, double coef, unsigned act,
+                                             double* part) {
+  const int lane = threadIdx.x & 31;
+  const long long row = d.s_row0[s] + lane;
+  const bool in = row < d.n[i];
+  const long long base = d.sptr[s];
+  const int w = (int)((d.sptr[s + 1] - base) / 32);
+  const double* xi = x + d.voff[i];
+  double acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.0;
+  for (int j = 0; j < w; ++j) {
+    const double v = __ldcs(d.val64 + base + (long long)j * 32 + lane);
+    const long long c = __ldcs(d.col + base + (long long)j * 32 + lane);
+    RowVec<double, R> xv;
+    if (MODE == kLanczos) xv.v[0] = __ldg(xi + c * RS); else xv.load(xi + c * R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = fma(v, xv.v[r], acc[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    double pr = 0.0;
+    const long long e = d.voff[i] + row * RS + r;
+    if ((act >> r) & 1u) {
+      double yv = acc[r];
+      if (MODE == kLanczos && xold) yv -= coef * xold[e];
+      y[e] = yv;
+      if (in) pr = x[e] * yv;
+    }
+    pr = warp_sum(pr);
+    if (lane == 0) part[s * kBR + r] = pr;
+  }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) b_spmv64_kernel(BatchDev d, const double* __restrict__ x,
                                                           const double* __restrict__ xold, double* __restrict__ y,
                                                           const int* __restrict__ done, const double* b2prev, int lan_j,
                                                           double* __restrict__ part) {
-  const int lane = threadIdx.x & 31;
   for (long long s = bgw(); s < d.nslices; s += bnw()) {
     const int i = d.s_inst[s];
-    const int R = MODE == kLanczos ? 1 : d.R[i];
     const int RS = d.R[i];
-    const int g0 = d.cbase[i];
-    bool act[kBR];
-    bool any = false;
-#pragma unroll
-    for (int r = 0; r < kBR; ++r) {
-      act[r] = r < R && (MODE == kLanczos || !done[g0 + r]);
-      any |= act[r];
+    if (MODE == kLanczos) {
+      const double coef = lan_j > 0 ? sqrt(b2prev[(long long)i * kMaxLanczos + lan_j - 1]) : 0.0;
+      b_spmv_slice<1, kLanczos>(d, s, i, RS, x, lan_j > 0 ? xold : nullptr, y, coef, 1u, part);
+      continue;
     }
-    if (!any) continue;
-    const long long row = d.s_row0[s] + lane;
-    const bool in = row < d.n[i];
-    const long long base = d.sptr[s];
-    const int w = (int)((d.sptr[s + 1] - base) / 32);
-    const double* xi = x + d.voff[i];
-    double acc[kBR];
-#pragma unroll
-    for (int r = 0; r < kBR; ++r) acc[r] = 0.0;
-    for (int j = 0; j < w; ++j) {
-      const double v = __ldcs(d.val64 + base + (long long)j * 32 + lane);
-      const long long c = __ldcs(d.col + base + (long long)j * 32 + lane);
-#pragma unroll
-      for (int r = 0; r < kBR; ++r)
-        if (act[r]) acc[r] = fma(v, __ldg(xi + c * RS + r), acc[r]);
-    }
-    double coef = 0.0;
-    if (MODE == kLanczos && lan_j > 0) coef = sqrt(b2prev[(long long)i * kMaxLanczos + lan_j - 1]);
-#pragma unroll
-    for (int r = 0; r < kBR; ++r) {
-      double pr = 0.0;
-      if (act[r]) {
-        const long long e = d.voff[i] + row * RS + r;
-        double yv = acc[r];
-        if (MODE == kLanczos && lan_j > 0) yv -= coef * xold[e];
-        y[e] = yv;
-        if (in) pr = x[e] * yv;
-      }
-      pr = warp_sum(pr);
-      if (lane == 0 && r < R) part[s * kBR + r] = pr;
+    const unsigned act = active_mask(done, d.cbase[i], RS);
+    if (!act) continue;
+    switch (RS) {
+      case 1: b_spmv_slice<1, kSpmv>(d, s, i, RS, x, nullptr, y, 0.0, act, part); break;
+      case 2: b_spmv_slice<2, kSpmv>(d, s, i, RS, x, nullptr, y, 0.0, act, part); break;
+      case 3: b_spmv_slice<3, kSpmv>(d, s, i, RS, x, nullptr, y, 0.0, act, part); break;
+      case 4: b_spmv_slice<4, kSpmv>(d, s, i, RS, x, nullptr, y, 0.0, act, part); break;
+      case 5: b_spmv_slice<5, kSpmv>(d, s, i, RS, x, nullptr, y, 0.0, act, part); break;
+      case 6: b_spmv_slice<6, kSpmv>(d, s, i, RS, x, nullptr, y, 0.0, act, part); break;
+      case 7: b_spmv_slice<7, kSpmv>(d, s, i, RS, x, nullptr, y, 0.0, act, part); break;
+      default: b_spmv_slice<8, kSpmv>(d, s, i, RS, x, nullptr, y, 0.0, act, part); break;
     }
   }
 }
 
-// FP64 / FP32 Chebyshev degree step j (modes as in the single-instance kernels)
-// with per-column coefficients.
+// Chebyshev degree step of one slice for R right-hand sides, with the folded
+// per-column coefficients (ca, cb, cc) of this step (see cheb_step_coeffs):
+//   kCheb1 y = ca r + cb (A r); kCheb2 y = ca x + cb r + cc (r - A x);
+//   kChebK y = ca x + cb x_old + cc (r - A x).
+template <typename TV, typename TX, int R, int MODE>
+__device__ __forceinline__ void b_cheb_slice(const BatchDev& d, long long s, int i, const TV* val, const TX* x,
+                                             const TX* xold, const TX* rin, TX* y, const double* coef, unsigned act) {
+  const int lane = threadIdx.x & 31;
+  const long long row = d.s_row0[s] + lane;
+  const long long base = d.sptr[s];
+  const int w = (int)((d.sptr[s + 1] - base) / 32);
+  const TX* xi = x + d.voff[i];
+  TX acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = (TX)0;
+  for (int jj = 0; jj < w; ++jj) {
+    const TX v = (TX)__ldcs(val + base + (long long)jj * 32 + lane);
+    const long long c = __ldcs(d.col + base + (long long)jj * 32 + lane);
+    RowVec<TX, R> xv;
+    xv.load(xi + c * R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = fma(v, xv.v[r], acc[r]);
+  }
+  const long long e0 = d.voff[i] + row * R;
+  RowVec<TX, R> rs, xs, xo;
+  rs.load(rin + e0);
+  if (MODE != kCheb1) xs.load(x + e0);
+  if (MODE == kChebK) xo.load(xold + e0);
+  const int g0 = d.cbase[i];
+  TX out[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const double* cf = coef + (long long)(g0 + r) * 3;
+    const TX ca = (TX)cf[0], cb = (TX)cf[1], cc = (TX)cf[2];
+    if (MODE == kCheb1)
+      out[r] = fma(cb, acc[r], ca * rs.v[r]);
+    else if (MODE == kCheb2)
+      out[r] = fma(cc, rs.v[r] - acc[r], fma(cb, rs.v[r], ca * xs.v[r]));
+    else
+      out[r] = fma(cc, rs.v[r] - acc[r], fma(cb, xo.v[r], ca * xs.v[r]));
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if ((act >> r) & 1u) y[e0 + r] = out[r];
+}
+
 template <typename TV, typename TX, int MODE>
 __global__ void __launch_bounds__(kBlock) b_cheb_kernel(BatchDev d, const TV* __restrict__ val, const TX* __restrict__ x,
                                                         const TX* __restrict__ xold, const TX* __restrict__ rin,
-                                                        TX* __restrict__ y, const int* __restrict__ done, int j) {
-  const int lane = threadIdx.x & 31;
+                                                        TX* __restrict__ y, const int* __restrict__ done,
+                                                        const double* __restrict__ coef) {
   for (long long s = bgw(); s < d.nslices; s += bnw()) {
     const int i = d.s_inst[s];
     const int R = d.R[i];
-    const int g0 = d.cbase[i];
-    bool act[kBR];
-    bool any = false;
-#pragma unroll
-    for (int r = 0; r < kBR; ++r) {
-      act[r] = r < R && !done[g0 + r];
-      any |= act[r];
-    }
-    if (!any) continue;
-    const long long row = d.s_row0[s] + lane;
-    const long long base = d.sptr[s];
-    const int w = (int)((d.sptr[s + 1] - base) / 32);
-    const TX* xi = x + d.voff[i];
-    TX acc[kBR];
-#pragma unroll
-    for (int r = 0; r < kBR; ++r) acc[r] = (TX)0;
-    for (int jj = 0; jj < w; ++jj) {
-      const TX v = (TX)__ldcs(val + base + (long long)jj * 32 + lane);
-      const long long c = __ldcs(d.col + base + (long long)jj * 32 + lane);
-#pragma unroll
-      for (int r = 0; r < kBR; ++r)
-        if (act[r]) acc[r] = fma(v, __ldg(xi + c * R + r), acc[r]);
-    }
-    const int kp1 = d.k + 1;
-#pragma unroll
-    for (int r = 0; r < kBR; ++r) {
-      if (!act[r]) continue;
-      const int g = g0 + r;
-      const double rho_j = d.rho[(long long)g * kp1 + j];
-      const double rho_m = d.rho[(long long)g * kp1 + j - 1];
-      const double dl = d.delta[g], tb = d.theta_bar[g], sb = d.sigma_bar[g];
-      const long long e = d.voff[i] + row * R + r;
-      const TX rs = rin[e];
-      TX yv;
-      if (MODE == kCheb1) {
-        yv = (TX)(2.0 * rho_j / dl) * ((TX)2 * rs - acc[r] * (TX)(1.0 / tb));
-      } else if (MODE == kCheb2) {
-        yv = (TX)rho_j * ((TX)(2.0 * sb) * x[e] - (TX)rho_m * (rs * (TX)(1.0 / tb)) + (TX)(2.0 / dl) * (rs - acc[r]));
-      } else {
-        yv = (TX)rho_j * ((TX)(2.0 * sb) * x[e] - (TX)rho_m * xold[e] + (TX)(2.0 / dl) * (rs - acc[r]));
-      }
-      y[e] = yv;
+    const unsigned act = active_mask(done, d.cbase[i], R);
+    if (!act) continue;
+    switch (R) {
+      case 1: b_cheb_slice<TV, TX, 1, MODE>(d, s, i, val, x, xold, rin, y, coef, act); break;
+      case 2: b_cheb_slice<TV, TX, 2, MODE>(d, s, i, val, x, xold, rin, y, coef, act); break;
+      case 3: b_cheb_slice<TV, TX, 3, MODE>(d, s, i, val, x, xold, rin, y, coef, act); break;
+      case 4: b_cheb_slice<TV, TX, 4, MODE>(d, s, i, val, x, xold, rin, y, coef, act); break;
+      case 5: b_cheb_slice<TV, TX, 5, MODE>(d, s, i, val, x, xold, rin, y, coef, act); break;
+      case 6: b_cheb_slice<TV, TX, 6, MODE>(d, s, i, val, x, xold, rin, y, coef, act); break;
+      case 7: b_cheb_slice<TV, TX, 7, MODE>(d, s, i, val, x, xold, rin, y, coef, act); break;
+      default: b_cheb_slice<TV, TX, 8, MODE>(d, s, i, val, x, xold, rin, y, coef, act); break;
     }
   }
 }
@@ -222,68 +280,96 @@ __global__ void __launch_bounds__(kBlock) b_cheb_kernel(BatchDev d, const TV* __
 enum BVec { kBScaleIn = 0, kBUpdXR = 1, kBTo32 = 2, kBFrom32 = 3, kBUpdP = 4, kBScaleOut = 5, kBZtoP = 6,
             kBDeg0 = 7 };
 
+template <int OP, int R>
+__device__ __forceinline__ void b_vec_slice(const BatchDev& d, const BatchCols& cc, long long s, int i, unsigned act,
+                                            const double* bin, double* xout, double* x, double* r, double* z,
+                                            double* p, const double* q, float* r32, const float* z32, double* part0,
+                                            double* part1, int first) {
+  const int lane = threadIdx.x & 31;
+  const int g0 = d.cbase[i];
+  const long long row = d.s_row0[s] + lane;
+  const bool in = row < d.n[i];
+  const double wr = in ? d.w[d.woff[i] + row] : 1.0;
+  const long long e0 = d.voff[i] + row * R;
+  double p0[R], p1[R];
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    p0[rr] = 0.0;
+    p1[rr] = 0.0;
+    const int g = g0 + rr;
+    const long long e = e0 + rr;
+    const bool a = (OP == kBScaleIn || OP == kBScaleOut) || ((act >> rr) & 1u);
+    if (!a) continue;
+    if (OP == kBScaleIn) {
+      const double v = in ? wr * bin[d.uoff[i] + row * R + rr] : 0.0;
+      r[e] = v;
+      x[e] = 0.0;
+      p0[rr] = v * v;
+    } else if (OP == kBScaleOut) {
+      if (in) xout[d.uoff[i] + row * R + rr] = wr * x[e];
+    } else if (OP == kBUpdXR) {
+      const double pq = cc.pq[g];
+      if (pq > 0.0 && isfinite(pq)) {
+        const double al = cc.rz[g] / pq;
+        x[e] += al * p[e];
+        const double rv = r[e] - al * q[e];
+        r[e] = rv;
+        p0[rr] = rv * rv;
+      }
+    } else if (OP == kBTo32) {
+      r32[e] = (float)r[e];
+    } else if (OP == kBFrom32 || OP == kBDeg0) {
+      const double zv = OP == kBFrom32 ? (double)z32[e] : r[e] / d.theta_bar[g];
+      z[e] = zv;
+      p0[rr] = r[e] * zv;
+      p1[rr] = q[e] * zv;
+    } else if (OP == kBUpdP) {
+      double beta = 0.0;
+      if (!first) beta = cc.flexible ? -cc.zq[g] / cc.pq[g] : cc.rz_new[g] / cc.rz[g];
+      p[e] = z[e] + beta * p[e];
+    } else if (OP == kBZtoP) {
+      p0[rr] = r[e] * z[e];
+      p1[rr] = q[e] * z[e];
+    }
+  }
+  if (OP == kBScaleIn || OP == kBUpdXR || OP == kBFrom32 || OP == kBZtoP || OP == kBDeg0) {
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const double a0 = warp_sum(in ? p0[rr] : 0.0);
+      const double a1 = (OP == kBFrom32 || OP == kBZtoP || OP == kBDeg0) ? warp_sum(in ? p1[rr] : 0.0) : 0.0;
+      if (lane == 0) {
+        part0[s * kBR + rr] = a0;
+        if (part1) part1[s * kBR + rr] = a1;
+      }
+    }
+  }
+}
+
 template <int OP>
 __global__ void __launch_bounds__(kBlock) b_vec_kernel(BatchDev d, BatchCols cc, const double* __restrict__ bin,
                                                        double* __restrict__ xout, double* x, double* r, double* z,
                                                        double* p, const double* q, float* r32, const float* z32,
                                                        double* __restrict__ part0, double* __restrict__ part1,
                                                        int first) {
-  const int lane = threadIdx.x & 31;
   for (long long s = bgw(); s < d.nslices; s += bnw()) {
     const int i = d.s_inst[s];
     const int R = d.R[i];
-    const int g0 = d.cbase[i];
-    const long long row = d.s_row0[s] + lane;
-    const bool in = row < d.n[i];
-    const double wr = in ? d.w[d.woff[i] + row] : 1.0;
-#pragma unroll 1
-    for (int rr = 0; rr < R; ++rr) {
-      const int g = g0 + rr;
-      const long long e = d.voff[i] + row * R + rr;
-      double p0 = 0.0, p1 = 0.0;
-      const bool act = OP == kBScaleIn || OP == kBScaleOut || !cc.done[g];
-      if (act) {
-        if (OP == kBScaleIn) {
-          const double v = in ? wr * bin[d.uoff[i] + row * R + rr] : 0.0;
-          r[e] = v;
-          x[e] = 0.0;
-          p0 = v * v;
-        } else if (OP == kBScaleOut) {
-          if (in) xout[d.uoff[i] + row * R + rr] = wr * x[e];
-        } else if (OP == kBUpdXR) {
-          const double pq = cc.pq[g];
-          if (pq > 0.0 && isfinite(pq)) {
-            const double al = cc.rz[g] / pq;
-            x[e] += al * p[e];
-            const double rv = r[e] - al * q[e];
-            r[e] = rv;
-            p0 = rv * rv;
-          }
-        } else if (OP == kBTo32) {
-          r32[e] = (float)r[e];
-        } else if (OP == kBFrom32 || OP == kBDeg0) {
-          const double zv = OP == kBFrom32 ? (double)z32[e] : r[e] / d.theta_bar[g];
-          z[e] = zv;
-          p0 = r[e] * zv;
-          p1 = q[e] * zv;
-        } else if (OP == kBUpdP) {
-          double beta = 0.0;
-          if (!first) beta = cc.flexible ? -cc.zq[g] / cc.pq[g] : cc.rz_new[g] / cc.rz[g];
-          p[e] = z[e] + beta * p[e];
-        } else if (OP == kBZtoP) {
-          p0 = r[e] * z[e];
-          p1 = q[e] * z[e];
-        }
-      }
-      if (OP == kBScaleIn || OP == kBUpdXR || OP == kBFrom32 || OP == kBZtoP || OP == kBDeg0) {
-        p0 = warp_sum(in ? p0 : 0.0);
-        p1 = warp_sum(in ? p1 : 0.0);
-        if (lane == 0) {
-          part0[s * kBR + rr] = p0;
-          if (part1) part1[s * kBR + rr] = p1;
-        }
-      }
+    const unsigned act = (OP == kBScaleIn || OP == kBScaleOut) ? 0xffu : active_mask(cc.done, d.cbase[i], R);
+    if (!act) continue;
+#define PP_BV(RR)                                                                                             \
+  b_vec_slice<OP, RR>(d, cc, s, i, act, bin, xout, x, r, z, p, q, r32, z32, part0, part1, first); \
+  break;
+    switch (R) {
+      case 1: PP_BV(1)
+      case 2: PP_BV(2)
+      case 3: PP_BV(3)
+      case 4: PP_BV(4)
+      case 5: PP_BV(5)
+      case 6: PP_BV(6)
+      case 7: PP_BV(7)
+      default: PP_BV(8)
     }
+#undef PP_BV
   }
 }
 
@@ -629,6 +715,7 @@ size_t layout_batch(pp_ctx* c, pp_batch_state* B, const BPlan& P, void* base) {
   B->delta = M.take<double>(P.ncols);
   B->sigma_bar = M.take<double>(P.ncols);
   B->rho = M.take<double>((long long)P.ncols * (k + 1));
+  B->coefT = M.take<double>((long long)(k + 1) * P.ncols * 3);
   d.theta_bar = B->theta_bar;
   d.delta = B->delta;
   d.sigma_bar = B->sigma_bar;
@@ -712,13 +799,14 @@ cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
     const int off = ((2 - k) % 3 + 3) % 3;
     auto Y = [&](int j) { return buf[(j + off) % 3]; };
     for (int j = 1; j <= k && e == cudaSuccess; ++j) {
+      const double* cj = B->coefT + (size_t)j * d.ncols * 3;
       if (j == 1)
-        b_cheb_kernel<float, float, kCheb1><<<g, kBlock, 0, s>>>(d, d.val32, B->r32, nullptr, B->r32, Y(1), B->c.done, 1);
+        b_cheb_kernel<float, float, kCheb1><<<g, kBlock, 0, s>>>(d, d.val32, B->r32, nullptr, B->r32, Y(1), B->c.done, cj);
       else if (j == 2)
-        b_cheb_kernel<float, float, kCheb2><<<g, kBlock, 0, s>>>(d, d.val32, Y(1), nullptr, B->r32, Y(2), B->c.done, 2);
+        b_cheb_kernel<float, float, kCheb2><<<g, kBlock, 0, s>>>(d, d.val32, Y(1), nullptr, B->r32, Y(2), B->c.done, cj);
       else
         b_cheb_kernel<float, float, kChebK><<<g, kBlock, 0, s>>>(d, d.val32, Y(j - 1), Y(j - 2), B->r32, Y(j), B->c.done,
-                                                               j);
+                                                               cj);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = b_vec<kBFrom32>(B, nullptr, nullptr, 0, s);
@@ -727,13 +815,14 @@ cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
     const int off = ((2 - k) % 3 + 3) % 3;
     auto Y = [&](int j) { return buf[(j + off) % 3]; };
     for (int j = 1; j <= k && e == cudaSuccess; ++j) {
+      const double* cj = B->coefT + (size_t)j * d.ncols * 3;
       if (j == 1)
-        b_cheb_kernel<double, double, kCheb1><<<g, kBlock, 0, s>>>(d, d.val64, B->r, nullptr, B->r, Y(1), B->c.done, 1);
+        b_cheb_kernel<double, double, kCheb1><<<g, kBlock, 0, s>>>(d, d.val64, B->r, nullptr, B->r, Y(1), B->c.done, cj);
       else if (j == 2)
-        b_cheb_kernel<double, double, kCheb2><<<g, kBlock, 0, s>>>(d, d.val64, Y(1), nullptr, B->r, Y(2), B->c.done, 2);
+        b_cheb_kernel<double, double, kCheb2><<<g, kBlock, 0, s>>>(d, d.val64, Y(1), nullptr, B->r, Y(2), B->c.done, cj);
       else
         b_cheb_kernel<double, double, kChebK><<<g, kBlock, 0, s>>>(d, d.val64, Y(j - 1), Y(j - 2), B->r, Y(j),
-                                                                 B->c.done, j);
+                                                                 B->c.done, cj);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = b_vec<kBZtoP>(B, nullptr, nullptr, 0, s);
@@ -763,6 +852,16 @@ void set_coeffs(pp_batch_state* B, int k) {
   cudaMemcpy(B->delta, dl.data(), sizeof(double) * nc, cudaMemcpyHostToDevice);
   cudaMemcpy(B->sigma_bar, sb.data(), sizeof(double) * nc, cudaMemcpyHostToDevice);
   cudaMemcpy(B->rho, rho.data(), sizeof(double) * rho.size(), cudaMemcpyHostToDevice);
+  std::vector<double> ct((size_t)(k + 1) * nc * 3, 0.0);
+  for (int j = 1; j <= k; ++j)
+    for (int g = 0; g < nc; ++g) {
+      const StepCoeffs cf = cheb_step_coeffs(j, &rho[(size_t)g * (k + 1)], tb[g], dl[g], sb[g]);
+      double* o = &ct[((size_t)j * nc + g) * 3];
+      o[0] = cf.ca;
+      o[1] = cf.cb;
+      o[2] = cf.cc;
+    }
+  cudaMemcpy(B->coefT, ct.data(), sizeof(double) * ct.size(), cudaMemcpyHostToDevice);
 }
 
 int b_lanczos(pp_ctx* c, pp_batch_state* B, cudaStream_t s) {

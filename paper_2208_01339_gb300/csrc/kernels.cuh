@@ -16,10 +16,12 @@ enum Prec { kF64 = 0, kF32 = 1, kBF16 = 2 };
 // One fused pass of a degree step (or a plain product) over the matrix:
 //   kSpmv    y = A x
 //   kResid   y = r - A x
-//   kCheb1   y = ca (2 r - ce (A r))                   (Algorithm 2, step 3; x = r)
-//   kCheb2   y = ca (cb x - cc ce r + cd (r - A x))    (first loop pass, x_old = r/theta)
-//   kChebK   y = ca (cb x - cc x_old + cd (r - A x))   (Algorithm 2 loop body)
+//   kCheb1   y = ca r + cb (A r)                       (Algorithm 2, step 3; x = r)
+//   kCheb2   y = ca x + cb r + cc (r - A x)            (first loop pass, x_old = r/theta)
+//   kChebK   y = ca x + cb x_old + cc (r - A x)        (Algorithm 2 loop body)
 //   kLanczos y = A x - sqrt(*dev_coef) x_old           (Lanczos three-term step)
+// The Chebyshev coefficients arrive folded (cheb_step_coeffs), so an update
+// costs one multiply and three fused multiply-adds per row.
 // Optional fused inner products (ndot = 0, 1 or 2), written by the last block:
 //   kSpmv: (x, y)   kResid: (y, y), (r, r)   kCheb*: (r, y), (aux, y)   kLanczos: (y, x)
 enum StepMode { kSpmv = 0, kResid = 1, kCheb1 = 2, kCheb2 = 3, kChebK = 4, kLanczos = 5 };
@@ -40,6 +42,22 @@ struct MatDesc {
   int prec;
   int tma;               // SELL: stage slices through shared memory with cp.async.bulk
 };
+
+// Folded coefficients of degree step j of Algorithm 2 (j >= 1): with
+// rho_j, 2 sigma_bar, 2/delta and 1/theta_bar, the step
+//   x_j = rho_j (2 sigma x_{j-1} - rho_{j-1} x_{j-2} + (2/delta)(r - A x_{j-1}))
+// (x_0 = r/theta, and x_1 = (2 rho_1/delta)(2 r - A r/theta)) becomes
+//   j = 1: ca = 4 rho_1/delta,        cb = -2 rho_1/(delta theta)
+//   j = 2: ca = 2 sigma rho_2, cb = -rho_2 rho_1/theta, cc = 2 rho_2/delta
+//   j > 2: ca = 2 sigma rho_j, cb = -rho_j rho_{j-1},   cc = 2 rho_j/delta
+struct StepCoeffs {
+  double ca, cb, cc;
+};
+inline StepCoeffs cheb_step_coeffs(int j, const double* rho, double theta_bar, double delta, double sigma_bar) {
+  if (j == 1) return {4.0 * rho[1] / delta, -2.0 * rho[1] / (delta * theta_bar), 0.0};
+  if (j == 2) return {2.0 * sigma_bar * rho[2], -rho[2] * rho[1] / theta_bar, 2.0 * rho[2] / delta};
+  return {2.0 * sigma_bar * rho[j], -rho[j] * rho[j - 1], 2.0 * rho[j] / delta};
+}
 
 struct StepParams {
   int mode = kSpmv;

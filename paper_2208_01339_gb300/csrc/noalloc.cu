@@ -92,27 +92,20 @@ extern "C" int polyprec_apply_csr_static(int n, long long nnz, const int* rowptr
       StepParams p;
       p.r = r;
       p.y = Y(j);
+      const StepCoeffs cf = cheb_step_coeffs(j, rho.data(), theta_bar, delta, sigma_bar);
+      p.ca = cf.ca;
+      p.cb = cf.cb;
+      p.cc = cf.cc;
       if (j == 1) {
         p.mode = kCheb1;
         p.x = r;
-        p.ca = 2.0 * rho[1] / delta;
-        p.ce = 1.0 / theta_bar;
       } else if (j == 2) {
         p.mode = kCheb2;
         p.x = Y(1);
-        p.ca = rho[2];
-        p.cb = 2.0 * sigma_bar;
-        p.cc = rho[1];
-        p.cd = 2.0 / delta;
-        p.ce = 1.0 / theta_bar;
       } else {
         p.mode = kChebK;
         p.x = Y(j - 1);
         p.xold = Y(j - 2);
-        p.ca = rho[j];
-        p.cb = 2.0 * sigma_bar;
-        p.cc = rho[j - 1];
-        p.cd = 2.0 / delta;
       }
       e = launch_step(A, p, nullptr, nullptr, nullptr, grid, s);
     }

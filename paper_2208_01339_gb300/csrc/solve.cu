@@ -51,27 +51,20 @@ cudaError_t cheb_core(pp_ctx* c, const Scalars* skip, const void* rin, void* zou
     StepParams p;
     p.r = rin;
     p.y = Y(j);
+    const StepCoeffs cf = cheb_step_coeffs(j, rho, c->theta_bar, c->delta, c->sigma_bar);
+    p.ca = cf.ca;
+    p.cb = cf.cb;
+    p.cc = cf.cc;
     if (j == 1) {  // x = (2 rho_1/delta)(2 r - A r / theta)
       p.mode = kCheb1;
       p.x = rin;
-      p.ca = 2.0 * rho[1] / c->delta;
-      p.ce = 1.0 / c->theta_bar;
     } else if (j == 2) {  // x_old = r / theta
       p.mode = kCheb2;
       p.x = Y(1);
-      p.ca = rho[2];
-      p.cb = 2.0 * c->sigma_bar;
-      p.cc = rho[1];
-      p.cd = 2.0 / c->delta;
-      p.ce = 1.0 / c->theta_bar;
     } else {
       p.mode = kChebK;
       p.x = Y(j - 1);
       p.xold = Y(j - 2);
-      p.ca = rho[j];
-      p.cb = 2.0 * c->sigma_bar;
-      p.cc = rho[j - 1];
-      p.cd = 2.0 / c->delta;
     }
     if (j == k && ndot > 0) {
       p.ndot = ndot;

@@ -226,11 +226,11 @@ __device__ __forceinline__ TX row_value(const StepArgs<TX>& a, TX acc, TX xs, TX
   } else if constexpr (MODE == kResid) {
     return rs - acc;
   } else if constexpr (MODE == kCheb1) {
-    return a.ca * ((TX)2 * rs - acc * a.ce);
+    return fma(a.cb, acc, a.ca * rs);
   } else if constexpr (MODE == kCheb2) {
-    return a.ca * (a.cb * xs - a.cc * (rs * a.ce) + a.cd * (rs - acc));
+    return fma(a.cc, rs - acc, fma(a.cb, rs, a.ca * xs));
   } else if constexpr (MODE == kChebK) {
-    return a.ca * (a.cb * xs - a.cc * xo + a.cd * (rs - acc));
+    return fma(a.cc, rs - acc, fma(a.cb, xo, a.ca * xs));
   } else {
     return acc - lan_coef * xo;
   }
