@@ -187,7 +187,10 @@ def oracle_iterations(workload: str, k: int):
     if not os.path.exists(p):
         return None
     with open(p) as fh:
-        return json.load(fh).get(f"{workload}/k{k}")
+        table = json.load(fh)
+    # the FP32/BF16 variants solve the same system; the oracle is FP64
+    base = workload.replace("_f32", "").replace("_bf16", "")
+    return table.get(f"{workload}/k{k}", table.get(f"{base}/k{k}"))
 
 
 def cpu_sample(A, b, w, k, alpha, beta, xi):
