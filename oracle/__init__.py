@@ -15,6 +15,12 @@ Parity status of each routine (how it is pinned independently of itself):
   newton_apply              equals cheb_apply at degree 2^nlev - 1, Table 1
   lanczos / extremes        numpy eigvalsh of T, interlacing, exact
                             extremes after n steps, Poisson closed form
+  lanczos_basis             Q^T Q = I and Q^T A Q = T_m, n steps give the
+                            exact spectrum
+  tridiag_eig               numpy eigh of T (up to sign), residuals
+  lowrank_apply             spectrum of P A for exact eigenvectors
+                            (eigenvalue + 1, Section 3.1), invariance
+                            under V -> V R, symmetry
   pcg_csr                   dense solves, Table 1 iteration counts,
                             Table 4 work counts
   schur_*                   dense S_u from its expansion, diag, dense K_0
@@ -67,7 +73,7 @@ class Options(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("xi", ctypes.c_double), ("interval", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("lanczos_steps", ctypes.c_int),
                 ("seed_scaling", ctypes.c_int), ("flexible", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("rtol", ctypes.c_double)]
+                ("rtol", ctypes.c_double), ("lowrank", ctypes.c_int), ("lr_V", ctypes.POINTER(ctypes.c_double))]
 
 
 class Dfn(ctypes.Structure):
@@ -92,6 +98,10 @@ def lib():
         L.oracle_jacobi_scale.argtypes = [ctypes.c_int, _i, _i, _d, _d, _d]
         L.oracle_lanczos.argtypes = [ctypes.c_int, _i, _i, _d, _d, ctypes.c_int, _d, _d]
         L.oracle_tridiag_extremes.argtypes = [ctypes.c_int, _d, _d, _d, _d]
+        L.oracle_lanczos_basis.argtypes = [ctypes.c_int, _i, _i, _d, _d, ctypes.c_int, _d, _d, _d]
+        L.oracle_tridiag_eig.argtypes = [ctypes.c_int, _d, _d, ctypes.c_int, _d, _d]
+        L.oracle_lowrank_apply.argtypes = [ctypes.c_int, _i, _i, _d, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, _d, _d, _d]
         L.oracle_pcg_csr.argtypes = [ctypes.c_int, _i, _i, _d, _d, _d, _d, ctypes.POINTER(Options),
                                      ctypes.POINTER(Stats)]
         L.oracle_schur_create.argtypes = [ctypes.POINTER(Dfn)]
@@ -206,11 +216,64 @@ def tridiag_extremes(a, b):
     return lo.value, hi.value
 
 
+def lanczos_basis(A, v0, m: int, val=None):
+    """(a, b, Q) of m Lanczos steps keeping the basis (full reorthogonalisation).
+
+    b has one entry per step: b[-1] is beta_m, the coupling to the next vector.
+    Q is n x steps with the Lanczos vectors as columns."""
+    a = np.zeros(m)
+    b = np.zeros(m)
+    Q = np.zeros((m, A.n))
+    rp, ci = _i32(A.rowptr), _i32(A.col)
+    va = _f64(A.val if val is None else val)
+    v0 = _f64(v0)
+    steps = lib().oracle_lanczos_basis(A.n, _p(rp, ctypes.c_int), _p(ci, ctypes.c_int), _p(va, ctypes.c_double),
+                                       _p(v0, ctypes.c_double), m, _p(a, ctypes.c_double), _p(b, ctypes.c_double),
+                                       _p(Q, ctypes.c_double))
+    return a[:steps], b[:steps], Q[:steps].T.copy()
+
+
+def tridiag_eig(a, b, i: int):
+    """(lambda_i, y_i): the i-th smallest eigenpair of the tridiagonal (a, b)."""
+    a, b = _f64(a), _f64(np.append(b, 0.0))
+    lam = ctypes.c_double()
+    y = np.zeros(len(a))
+    rc = lib().oracle_tridiag_eig(len(a), _p(a, ctypes.c_double), _p(b, ctypes.c_double), i, ctypes.byref(lam),
+                                  _p(y, ctypes.c_double))
+    if rc:
+        raise RuntimeError("tridiag_eig")
+    return lam.value, y
+
+
+def lowrank_apply(A, alpha: float, beta: float, xi: float, k: int, V, r, val=None) -> np.ndarray:
+    """z = p_k(A) r + V (V^T A V)^{-1} V^T r (Section 3.1); V is n x p."""
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    Vc = np.ascontiguousarray(V.T)
+    r = _f64(r)
+    z = np.zeros(A.n)
+    rp, ci = _i32(A.rowptr), _i32(A.col)
+    va = _f64(A.val if val is None else val)
+    rc = lib().oracle_lowrank_apply(A.n, _p(rp, ctypes.c_int), _p(ci, ctypes.c_int), _p(va, ctypes.c_double), alpha,
+                                    beta, xi, k, V.shape[1], _p(Vc, ctypes.c_double), _p(r, ctypes.c_double),
+                                    _p(z, ctypes.c_double))
+    if rc:
+        raise RuntimeError(f"oracle lowrank_apply status {rc}")
+    return z
+
+
 def make_options(k=20, xi=-1.0, interval="lanczos", alpha=0.0, beta=0.0, lanczos_steps=10, seed_scaling=True,
-                 flexible=False, maxit=10000, rtol=1e-8) -> Options:
-    return Options(k=k, xi=xi, interval=0 if interval == "lanczos" else 1, alpha=alpha, beta=beta,
-                   lanczos_steps=lanczos_steps, seed_scaling=1 if seed_scaling else 0,
-                   flexible=1 if flexible else 0, maxit=maxit, rtol=rtol)
+                 flexible=False, maxit=10000, rtol=1e-8, lowrank=0, lr_V=None) -> Options:
+    """Options; lr_V (n x p, seed-scaled space) must stay alive while they are used."""
+    o = Options(k=k, xi=xi, interval=0 if interval == "lanczos" else 1, alpha=alpha, beta=beta,
+                lanczos_steps=lanczos_steps, seed_scaling=1 if seed_scaling else 0,
+                flexible=1 if flexible else 0, maxit=maxit, rtol=rtol, lowrank=lowrank)
+    if lr_V is not None:
+        o._keep = np.ascontiguousarray(np.asarray(lr_V, dtype=np.float64).T)
+        o.lowrank = lr_V.shape[1]
+        o.lr_V = _p(o._keep, ctypes.c_double)
+    return o
 
 
 def pcg_csr(A, b, x0=None, v0=None, **opts):

@@ -314,6 +314,219 @@ int oracle_tridiag_extremes(int m, const double* a, const double* b, double* lmi
 }
 
 /* ------------------------------------------------------------------ */
+/* Section 3.1: leftmost eigenpairs for the low-rank acceleration      */
+/* ------------------------------------------------------------------ */
+/* Lanczos that keeps its basis: q_0 = v0/||v0||; step j forms
+ * w = A q_j - b_{j-1} q_{j-1}, a_j = (w, q_j), w -= a_j q_j, then
+ * orthogonalises w against every kept q_0..q_j by classical Gram-Schmidt,
+ * done twice, and sets b_j = ||w||, q_{j+1} = w / b_j.  Q is n x m with
+ * q_j at Q + j n.  b[m-1] is the coupling beta_m to the next (not kept)
+ * vector: the Ritz pair (theta, Q y) of T_m has residual beta_m |y_m|. */
+static int lanczos_basis_op(const op_t* A, const double* v0, int m, double* a, double* b,
+                            double* Q) {
+  int n = A->n;
+  double* w = (double*)calloc((size_t)n, sizeof(double));
+  double* h = (double*)calloc((size_t)m, sizeof(double));
+  double nv = sqrt(dot(n, v0, v0));
+  int steps = 0;
+  if (nv > 0.0) {
+    for (int i = 0; i < n; ++i) Q[i] = v0[i] / nv;
+    for (int j = 0; j < m; ++j) {
+      const double* qj = Q + (size_t)j * n;
+      A->apply(A->ctx, qj, w);
+      if (j > 0) {
+        const double* qp = Q + (size_t)(j - 1) * n;
+        for (int i = 0; i < n; ++i) w[i] -= b[j - 1] * qp[i];
+      }
+      a[j] = dot(n, w, qj);
+      for (int i = 0; i < n; ++i) w[i] -= a[j] * qj[i];
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int l = 0; l <= j; ++l) h[l] = dot(n, Q + (size_t)l * n, w);
+        for (int l = 0; l <= j; ++l) {
+          const double* ql = Q + (size_t)l * n;
+          for (int i = 0; i < n; ++i) w[i] -= h[l] * ql[i];
+        }
+      }
+      b[j] = sqrt(dot(n, w, w));
+      steps = j + 1;
+      if (j == m - 1) break;
+      if (!(b[j] > 1e-300)) break; /* invariant subspace found */
+      double* qn = Q + (size_t)(j + 1) * n;
+      for (int i = 0; i < n; ++i) qn[i] = w[i] / b[j];
+    }
+  }
+  free(w);
+  free(h);
+  return steps;
+}
+
+int oracle_lanczos_basis(int n, const int* rowptr, const int* col, const double* val,
+                         const double* v0, int m, double* a, double* b, double* Q) {
+  csr_t c = {n, rowptr, col, val};
+  op_t op = {csr_apply, &c, n};
+  return lanczos_basis_op(&op, v0, m, a, b, Q);
+}
+
+/* Solve the dense m x m system M y = f by Gaussian elimination with
+ * partial pivoting (M and f are overwritten); a zero pivot is replaced by
+ * tiny, which is what inverse iteration wants at an exact eigenvalue. */
+static void dense_solve(int m, double* M, double* f, double* y, double tiny) {
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (fabs(M[(size_t)r * m + c]) > fabs(M[(size_t)piv * m + c])) piv = r;
+    if (piv != c) {
+      for (int k = 0; k < m; ++k) {
+        double t = M[(size_t)c * m + k];
+        M[(size_t)c * m + k] = M[(size_t)piv * m + k];
+        M[(size_t)piv * m + k] = t;
+      }
+      double t = f[c];
+      f[c] = f[piv];
+      f[piv] = t;
+    }
+    if (fabs(M[(size_t)c * m + c]) < tiny) M[(size_t)c * m + c] = tiny;
+    for (int r = c + 1; r < m; ++r) {
+      double l = M[(size_t)r * m + c] / M[(size_t)c * m + c];
+      if (l == 0.0) continue;
+      for (int k = c; k < m; ++k) M[(size_t)r * m + k] -= l * M[(size_t)c * m + k];
+      f[r] -= l * f[c];
+    }
+  }
+  for (int r = m - 1; r >= 0; --r) {
+    double s = f[r];
+    for (int k = r + 1; k < m; ++k) s -= M[(size_t)r * m + k] * y[k];
+    y[r] = s / M[(size_t)r * m + r];
+  }
+}
+
+/* The i-th smallest eigenvalue (i = 0, 1, ...) of the tridiagonal T (diag a,
+ * off-diagonal b) by Sturm-sequence bisection, and its unit eigenvector by
+ * three steps of inverse iteration on the dense T - lambda I.  The sign is
+ * fixed by making the largest-magnitude entry positive. */
+int oracle_tridiag_eig(int m, const double* a, const double* b, int i, double* lambda,
+                       double* y) {
+  if (m <= 0 || i < 0 || i >= m) return -1;
+  double lo = a[0], hi = a[0];
+  for (int r = 0; r < m; ++r) {
+    double rad = 0.0;
+    if (r > 0) rad += fabs(b[r - 1]);
+    if (r < m - 1) rad += fabs(b[r]);
+    if (a[r] - rad < lo) lo = a[r] - rad;
+    if (a[r] + rad > hi) hi = a[r] + rad;
+  }
+  double span = hi - lo + 1e-300;
+  double l = lo - 1e-12 * span, h = hi + 1e-12 * span;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (l + h);
+    if (sturm_count(m, a, b, mid) >= i + 1) h = mid; else l = mid;
+  }
+  double lam = 0.5 * (l + h);
+  *lambda = lam;
+  double* M = (double*)malloc(sizeof(double) * (size_t)m * m);
+  double* f = (double*)malloc(sizeof(double) * (size_t)m);
+  for (int r = 0; r < m; ++r) y[r] = 1.0 / sqrt((double)m) * (1.0 + 0.01 * r);
+  for (int step = 0; step < 3; ++step) {
+    for (size_t t = 0; t < (size_t)m * m; ++t) M[t] = 0.0;
+    for (int r = 0; r < m; ++r) {
+      M[(size_t)r * m + r] = a[r] - lam;
+      if (r + 1 < m) M[(size_t)r * m + r + 1] = M[(size_t)(r + 1) * m + r] = b[r];
+      f[r] = y[r];
+    }
+    dense_solve(m, M, f, y, 1e-300 + 1e-15 * span);
+    double nrm = sqrt(dot(m, y, y));
+    for (int r = 0; r < m; ++r) y[r] /= nrm;
+  }
+  int big = 0;
+  for (int r = 1; r < m; ++r)
+    if (fabs(y[r]) > fabs(y[big])) big = r;
+  if (y[big] < 0.0)
+    for (int r = 0; r < m; ++r) y[r] = -y[r];
+  free(M);
+  free(f);
+  return 0;
+}
+
+/* Ritz vectors of the p smallest Ritz values: V_i = Q y_i (n x p). */
+static int ritz_vectors(int n, int m, const double* a, const double* b, const double* Q, int p,
+                        double* V, double* theta) {
+  if (p > m) return -1;
+  double* y = (double*)malloc(sizeof(double) * (size_t)m);
+  for (int i = 0; i < p; ++i) {
+    double th;
+    oracle_tridiag_eig(m, a, b, i, &th, y);
+    if (theta) theta[i] = th;
+    double* vi = V + (size_t)i * n;
+    for (int r = 0; r < n; ++r) vi[r] = 0.0;
+    for (int j = 0; j < m; ++j)
+      for (int r = 0; r < n; ++r) vi[r] += y[j] * Q[(size_t)j * n + r];
+  }
+  free(y);
+  return 0;
+}
+
+/* The spectral correction of Section 3.1: P = P_0 + V (V^T A V)^{-1} V^T.
+ * G = V^T A V is formed once (p products by A, not counted as PCG work)
+ * and factorised by Cholesky, G = L L^T; each application then costs p
+ * inner products (V^T r) and one combination of the columns of V. */
+typedef struct {
+  int p;
+  const double* V; /* n x p, column i at V + i n */
+  double* L;       /* p x p lower Cholesky factor of G */
+} lowrank_t;
+
+static int lowrank_setup(const op_t* A, int p, const double* V, lowrank_t* lr) {
+  int n = A->n;
+  lr->p = p;
+  lr->V = V;
+  lr->L = (double*)calloc((size_t)(p > 0 ? p * p : 1), sizeof(double));
+  if (p == 0) return 0;
+  double* G = (double*)malloc(sizeof(double) * (size_t)p * p);
+  double* t = (double*)malloc(sizeof(double) * (size_t)n);
+  for (int j = 0; j < p; ++j) {
+    A->apply(A->ctx, V + (size_t)j * n, t);
+    for (int i = 0; i < p; ++i) G[(size_t)i * p + j] = dot(n, V + (size_t)i * n, t);
+  }
+  int rc = 0;
+  for (int j = 0; j < p && rc == 0; ++j) {
+    double d = G[(size_t)j * p + j];
+    for (int k = 0; k < j; ++k) d -= lr->L[(size_t)j * p + k] * lr->L[(size_t)j * p + k];
+    if (!(d > 0.0)) { rc = -2; break; }
+    lr->L[(size_t)j * p + j] = sqrt(d);
+    for (int i = j + 1; i < p; ++i) {
+      double s = G[(size_t)i * p + j];
+      for (int k = 0; k < j; ++k) s -= lr->L[(size_t)i * p + k] * lr->L[(size_t)j * p + k];
+      lr->L[(size_t)i * p + j] = s / lr->L[(size_t)j * p + j];
+    }
+  }
+  free(G);
+  free(t);
+  return rc;
+}
+
+/* z += V G^{-1} V^T r */
+static void lowrank_add(int n, const lowrank_t* lr, const double* r, double* z) {
+  int p = lr->p;
+  double* c = (double*)malloc(sizeof(double) * (size_t)p);
+  for (int i = 0; i < p; ++i) c[i] = dot(n, lr->V + (size_t)i * n, r);
+  for (int i = 0; i < p; ++i) { /* L u = w */
+    double s = c[i];
+    for (int k = 0; k < i; ++k) s -= lr->L[(size_t)i * p + k] * c[k];
+    c[i] = s / lr->L[(size_t)i * p + i];
+  }
+  for (int i = p - 1; i >= 0; --i) { /* L^T c = u */
+    double s = c[i];
+    for (int k = i + 1; k < p; ++k) s -= lr->L[(size_t)k * p + i] * c[k];
+    c[i] = s / lr->L[(size_t)i * p + i];
+  }
+  for (int i = 0; i < p; ++i) {
+    const double* vi = lr->V + (size_t)i * n;
+    for (int r2 = 0; r2 < n; ++r2) z[r2] += c[i] * vi[r2];
+  }
+  free(c);
+}
+
+/* ------------------------------------------------------------------ */
 /* PCG with P = p_k(A) (Section 1, Algorithm 2 as the preconditioner)  */
 /* ------------------------------------------------------------------ */
 /* Standard PCG from x0: r = b - A x, z = P r, p = z; each iteration
@@ -329,7 +542,19 @@ typedef struct {
   int m;
   double theta_bar, delta, sigma_bar;
   const double* rho;
+  lowrank_t lr; /* lr.p = 0: no spectral correction */
 } cheb_t;
+
+/* z = P r with P = p_m(A) (+ V G^{-1} V^T, Section 3.1); the p inner
+ * products of the correction are counted in dots. */
+static int prec_apply(const op_t* A, const cheb_t* P, const double* r, double* z,
+                      long long* mvp, long long* dots) {
+  int rc = cheb_apply_op(A, P->m, P->theta_bar, P->delta, P->sigma_bar, P->rho, r, z, mvp);
+  if (rc || P->lr.p == 0) return rc;
+  lowrank_add(A->n, &P->lr, r, z);
+  *dots += P->lr.p;
+  return all_finite(A->n, z) ? 0 : -3;
+}
 
 static int pcg_op(const op_t* A, const cheb_t* P, const double* b, double* x, int flexible,
                   int maxit, double rtol, oracle_stats* st) {
@@ -354,7 +579,7 @@ static int pcg_op(const op_t* A, const cheb_t* P, const double* b, double* x, in
   }
   double rel = (bnorm > 0.0) ? sqrt(dot(n, r, r)) / bnorm : 0.0;
   if (bnorm == 0.0 || rel <= rtol) goto done;
-  rc = cheb_apply_op(A, P->m, P->theta_bar, P->delta, P->sigma_bar, P->rho, r, z, &mvp);
+  rc = prec_apply(A, P, r, z, &mvp, &dots);
   if (rc) goto done;
   memcpy(p, z, sizeof(double) * (size_t)n);
   double rz = dot(n, r, z);
@@ -377,7 +602,7 @@ static int pcg_op(const op_t* A, const cheb_t* P, const double* b, double* x, in
     if (!isfinite(rr)) { rc = -3; break; }
     rel = sqrt(rr) / bnorm;
     if (rel <= rtol) { rc = 0; break; }
-    rc = cheb_apply_op(A, P->m, P->theta_bar, P->delta, P->sigma_bar, P->rho, r, z, &mvp);
+    rc = prec_apply(A, P, r, z, &mvp, &dots);
     if (rc) break;
     rc = 1;
     double rz_new = dot(n, r, z);
@@ -416,18 +641,46 @@ static double auto_xi(double a, double b) {
   return xi;
 }
 
+/* The interval [alpha, beta] (given, or the extreme Ritz values of
+ * lanczos_steps Lanczos steps from v0) and, when opt->lowrank = p > 0, the
+ * vectors of the correction: opt->lr_V if given, else the Ritz vectors of
+ * the p smallest Ritz values of the same Lanczos run, which then keeps its
+ * basis (full reorthogonalisation).  *Vown receives memory to free. */
 static int pick_interval(const op_t* A, const double* v0, const oracle_options* opt,
-                         double* alpha, double* beta) {
-  if (opt->interval == 1) {
+                         double* alpha, double* beta, const double** V, double** Vown) {
+  *V = opt->lr_V;
+  *Vown = NULL;
+  int need_ritz = opt->lowrank > 0 && opt->lr_V == NULL;
+  if (opt->interval == 1 && !need_ritz) {
     *alpha = opt->alpha;
     *beta = opt->beta;
     return 0;
   }
+  int n = A->n;
   int m = opt->lanczos_steps > 0 ? opt->lanczos_steps : 10;
   double* a = (double*)calloc((size_t)m, sizeof(double));
   double* b = (double*)calloc((size_t)m, sizeof(double));
-  int steps = lanczos_op(A, v0, m, a, b);
-  int rc = steps > 0 ? oracle_tridiag_extremes(steps, a, b, alpha, beta) : -1;
+  int rc = 0;
+  if (need_ritz) {
+    double* Q = (double*)calloc((size_t)n * m, sizeof(double));
+    int steps = lanczos_basis_op(A, v0, m, a, b, Q);
+    if (steps < opt->lowrank) {
+      rc = -1;
+    } else {
+      *Vown = (double*)malloc(sizeof(double) * (size_t)n * opt->lowrank);
+      ritz_vectors(n, steps, a, b, Q, opt->lowrank, *Vown, NULL);
+      *V = *Vown;
+      rc = oracle_tridiag_extremes(steps, a, b, alpha, beta);
+    }
+    free(Q);
+  } else {
+    int steps = lanczos_op(A, v0, m, a, b);
+    rc = steps > 0 ? oracle_tridiag_extremes(steps, a, b, alpha, beta) : -1;
+  }
+  if (opt->interval == 1) {
+    *alpha = opt->alpha;
+    *beta = opt->beta;
+  }
   free(a);
   free(b);
   return rc;
@@ -457,13 +710,19 @@ int oracle_pcg_csr(int n, const int* rowptr, const int* col, const double* val,
     for (int i = 0; i < n; ++i) bh[i] = w[i] * b[i];
     for (int i = 0; i < n; ++i) xh[i] = x[i] / w[i];
     double alpha, beta;
-    rc = pick_interval(&A, v0, opt, &alpha, &beta);
+    const double* V = NULL;
+    double* Vown = NULL;
+    rc = pick_interval(&A, v0, opt, &alpha, &beta, &V, &Vown);
     if (rc == 0) {
       double xi = opt->xi >= 0.0 ? opt->xi : auto_xi(alpha, beta);
       cheb_t P;
       P.m = opt->k;
       P.rho = rho;
+      P.lr.p = 0;
+      P.lr.V = NULL;
+      P.lr.L = NULL;
       rc = oracle_cheb_coeffs(alpha, beta, xi, opt->k, &P.theta_bar, &P.delta, &P.sigma_bar, rho);
+      if (rc == 0) rc = lowrank_setup(&A, opt->lowrank > 0 ? opt->lowrank : 0, V, &P.lr);
       if (rc == 0) rc = pcg_op(&A, &P, bh, xh, opt->flexible, opt->maxit, opt->rtol, st);
       if (st) {
         st->alpha_hat = alpha;
@@ -480,7 +739,9 @@ int oracle_pcg_csr(int n, const int* rowptr, const int* col, const double* val,
         st->true_rel_res = bn > 0.0 ? sqrt(num) / bn : 0.0;
         free(t);
       }
+      free(P.lr.L);
     }
+    free(Vown);
   }
   if (st) st->status = rc;
   free(vh);
@@ -763,13 +1024,19 @@ int oracle_pcg_schur(const oracle_schur* s, const double* ds, const double* r, d
     for (int i = 0; i < nu; ++i) rh[i] = w[i] * r[i];
     for (int i = 0; i < nu; ++i) uh[i] = u[i] / w[i];
     double alpha, beta;
-    rc = pick_interval(&A, v0, opt, &alpha, &beta);
+    const double* V = NULL;
+    double* Vown = NULL;
+    rc = pick_interval(&A, v0, opt, &alpha, &beta, &V, &Vown);
     if (rc == 0) {
       double xi = opt->xi >= 0.0 ? opt->xi : auto_xi(alpha, beta);
       cheb_t P;
       P.m = opt->k;
       P.rho = rho;
+      P.lr.p = 0;
+      P.lr.V = NULL;
+      P.lr.L = NULL;
       rc = oracle_cheb_coeffs(alpha, beta, xi, opt->k, &P.theta_bar, &P.delta, &P.sigma_bar, rho);
+      if (rc == 0) rc = lowrank_setup(&A, opt->lowrank > 0 ? opt->lowrank : 0, V, &P.lr);
       if (rc == 0) rc = pcg_op(&A, &P, rh, uh, opt->flexible, opt->maxit, opt->rtol, st);
       if (st) {
         st->alpha_hat = alpha;
@@ -788,7 +1055,9 @@ int oracle_pcg_schur(const oracle_schur* s, const double* ds, const double* r, d
         st->true_rel_res = bn > 0.0 ? sqrt(num / bn) : 0.0;
         free(t);
       }
+      free(P.lr.L);
     }
+    free(Vown);
   }
   if (st) st->status = rc;
   free(w);
@@ -797,5 +1066,31 @@ int oracle_pcg_schur(const oracle_schur* s, const double* ds, const double* r, d
   free(rho);
   free(ss.tmp);
   free(ss.tmp2);
+  return rc;
+}
+
+/* z = p_k(A) r + V (V^T A V)^{-1} V^T r (Section 3.1) for a CSR matrix. */
+int oracle_lowrank_apply(int n, const int* rowptr, const int* col, const double* val,
+                         double alpha, double beta, double xi, int k, int p, const double* V,
+                         const double* r, double* z) {
+  if (p < 0) return -1;
+  double tb, d, sb;
+  double* rho = (double*)malloc(sizeof(double) * (size_t)(k + 1));
+  int rc = oracle_cheb_coeffs(alpha, beta, xi, k, &tb, &d, &sb, rho);
+  if (rc == 0) {
+    csr_t a = {n, rowptr, col, val};
+    op_t op = {csr_apply, &a, n};
+    cheb_t P;
+    P.m = k;
+    P.theta_bar = tb;
+    P.delta = d;
+    P.sigma_bar = sb;
+    P.rho = rho;
+    rc = lowrank_setup(&op, p, V, &P.lr);
+    long long mvp = 0, dots = 0;
+    if (rc == 0) rc = prec_apply(&op, &P, r, z, &mvp, &dots);
+    free(P.lr.L);
+  }
+  free(rho);
   return rc;
 }

@@ -19,6 +19,9 @@
  *   oracle_lanczos         plain Lanczos tridiagonalisation (the interval
  *                          estimator used instead of the paper's DACG)
  *   oracle_tridiag_extremes  Sturm-sequence bisection on T_m
+ *   oracle_lanczos_basis   Lanczos keeping its (fully reorthogonalised) basis
+ *   oracle_tridiag_eig     eigenpair of T_m: bisection + inverse iteration
+ *   oracle_lowrank_apply   Section 3.1: P = P_0 + V (V^T A V)^{-1} V^T
  *   oracle_pcg_csr         PCG (Section 1) with P = W p_k(A_hat) W^T
  *   oracle_schur_*         Section 4.2: Algorithm 3 (y = S_u r), Algorithm 4
  *                          (D_S = diag S_u), the right-hand side
@@ -64,9 +67,25 @@ int oracle_lanczos(int n, const int* rowptr, const int* col, const double* val,
 int oracle_tridiag_extremes(int m, const double* a, const double* b, double* lmin,
                             double* lmax);
 
+/* Section 3.1: Lanczos keeping its basis Q (n x m, full reorthogonalisation;
+ * b[m-1] = beta_m), the i-th smallest eigenpair of T_m, and the corrected
+ * preconditioner z = p_k(A) r + V (V^T A V)^{-1} V^T r (V: n x p, column i
+ * at V + i n). */
+int oracle_lanczos_basis(int n, const int* rowptr, const int* col, const double* val,
+                         const double* v0, int m, double* a, double* b, double* Q);
+int oracle_tridiag_eig(int m, const double* a, const double* b, int i, double* lambda,
+                       double* y);
+int oracle_lowrank_apply(int n, const int* rowptr, const int* col, const double* val,
+                         double alpha, double beta, double xi, int k, int p, const double* V,
+                         const double* r, double* z);
+
 /* Options of the full solve.  interval: 0 = Lanczos on A_hat from v0,
  * 1 = given (alpha, beta).  xi < 0 selects xi = clip(10 alpha/beta, 1e-6, 1e-2).
- * seed_scaling: 0 none, 1 Jacobi.  flexible: 0 plain PCG, 1 flexible CG. */
+ * seed_scaling: 0 none, 1 Jacobi.  flexible: 0 plain PCG, 1 flexible CG.
+ * lowrank = p > 0 adds the Section 3.1 correction V (V^T A_hat V)^{-1} V^T
+ * with V = lr_V (n x p, seed-scaled space) or, when lr_V is NULL, the Ritz
+ * vectors of the p smallest Ritz values of the (basis-keeping) Lanczos run
+ * of lanczos_steps steps from v0, which then also gives the interval. */
 typedef struct {
   int k;
   double xi;
@@ -77,6 +96,8 @@ typedef struct {
   int flexible;
   int maxit;
   double rtol;
+  int lowrank;
+  const double* lr_V;
 } oracle_options;
 
 int oracle_pcg_csr(int n, const int* rowptr, const int* col, const double* val,
