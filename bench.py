@@ -219,6 +219,8 @@ def run_reference(args, w, rank):
 
     A, b = build_problem(w)
     k = args.k if args.k is not None else w["k"]
+    if args.lanczos_steps:
+        w["lanczos"] = args.lanczos_steps
     vh, _ = O.jacobi_scale(A)
     a, bb = O.lanczos(A, I.lanczos_start(A.n, 0), w["lanczos"], val=vh)
     alpha, beta = O.tridiag_extremes(a, bb)
@@ -267,6 +269,32 @@ def run_k_sweep(args, w, A, b, opts, dev):
         print(json.dumps({"workload": args.workload, "prec": w["prec"], "k": k, "iterations": st["iterations"],
                           "time_s": statistics.median(ts) / 1e3, "mvp": st["mvp"], "dots": st["dots"],
                           "step_us": round(apply_us, 2), "status": st["status"]}), flush=True)
+        S.close()
+
+
+def run_dfn_sweep(args, w, net, dopts, dev):
+    """Degree sweep on the fracture network (the shape of Table 4): one line
+    per k with iterations, products, inner products and time to rtol."""
+    import torch
+
+    from paper_2208_01339_gb300 import polyprec as P
+
+    for k in [int(v) for v in args.k_sweep.split(",")]:
+        S = P.SchurSolver(net, device=dev, k=k, **dopts)
+        bt = S.rhs(torch.as_tensor(net.q, device=dev))
+        S.solve(bt)
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(max(1, args.steps)):
+            _, st = S.solve(bt)
+            ts.append(st["t_solve_ms"])
+        info = S.info()
+        print(json.dumps({"workload": args.workload, "k": k, "lowrank": dopts["lowrank"],
+                          "lanczos_steps": dopts["lanczos_steps"], "iterations": st["iterations"],
+                          "time_s": statistics.median(ts) / 1e3, "mvp": st["mvp"], "dots": st["dots"],
+                          "setup_ms": round(info["t_setup_ms"], 2), "alpha_hat": info["alpha_hat"],
+                          "beta_hat": info["beta_hat"], "xi": info["xi"], "ritz_resid": info["ritz_resid"],
+                          "status": st["status"]}), flush=True)
         S.close()
 
 
@@ -373,7 +401,8 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": args.workload, "n_f": net.n_f, "n_h": net.n_h, "n_u": net.n_u, "k": k,
-                          "trace_block_entries": info["nnz"], "alpha_reg": net.alpha},
+                          "trace_block_entries": info["nnz"], "alpha_reg": net.alpha,
+                          "lanczos_steps": w["lanczos"], "lowrank": args.lowrank},
                "iterations": it, "setup_ms": round(info["t_setup_ms"], 2), "alpha_hat": info["alpha_hat"],
                "beta_hat": info["beta_hat"], "xi": info["xi"],
                "apply_ms": sum(s["t_apply_ms"] for s in stats) / max(1, sum(s["apply_launches"] for s in stats)),
@@ -399,6 +428,9 @@ def main():
     ap.add_argument("--k-sweep", default="", help="comma-separated degrees: time one solve per degree instead")
     ap.add_argument("--batch-count", type=int, default=0, help="override the batched workload's instance count")
     ap.add_argument("--batch-nmax", type=int, default=0, help="override the batched workload's largest grid")
+    ap.add_argument("--lowrank", type=int, default=0,
+                    help="Section 3.1 low-rank correction with this many Ritz vectors (0: none)")
+    ap.add_argument("--lanczos-steps", type=int, default=0, help="override the workload's Lanczos steps")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.batch_count:
@@ -433,13 +465,16 @@ def main():
         return run_batch(args, w, A, k, dev, world, rank)
     if w.get("dfn"):
         net = A
-        S = P.SchurSolver(net, device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8, check_every=args.check_every,
-                          use_graphs=args.graphs, maxit=5000)
+        dopts = dict(lanczos_steps=w["lanczos"], rtol=1e-8, check_every=args.check_every, use_graphs=args.graphs,
+                     maxit=5000, lowrank=args.lowrank)
+        if args.k_sweep:
+            return run_dfn_sweep(args, w, net, dopts, dev)
+        S = P.SchurSolver(net, device=dev, k=k, **dopts)
         bt = S.rhs(torch.as_tensor(net.q, device=dev))
         return run_dfn(args, w, net, S, bt, k, dev, world, rank, dist)
     opts = dict(k=k, lanczos_steps=w["lanczos"], format=w["fmt"], apply_prec=w["prec"], rtol=1e-8,
                 check_every=args.check_every, use_graphs=args.graphs, flexible=w.get("flexible", 0),
-                sell_variant=args.sell_variant, sell_C=args.sell_C, sell_sigma=args.sell_sigma)
+                sell_variant=args.sell_variant, sell_C=args.sell_C, sell_sigma=args.sell_sigma, lowrank=args.lowrank)
     if args.k_sweep:
         return run_k_sweep(args, w, A, b, opts, dev)
     S = P.Solver.from_host(A, device=dev, **opts)
@@ -542,6 +577,7 @@ def main():
                    "sell_C": info["sell_C"], "lanczos_steps": w["lanczos"], "rtol": 1e-8,
                    "l2": "inputs larger than L2 (matrix >> 129 MB)" if A.nnz * 12 > 129e6 else "L2-resident inputs",
                    "graphs": args.graphs, "sell_variant": "direct" if args.sell_variant == 1 else "tma",
+                   "lowrank": args.lowrank,
                    "parallelism": f"replicas x{world}"},
         "iterations": int(statistics.median(it)), "setup_ms": round(info["t_setup_ms"], 2),
         "alpha_hat": info["alpha_hat"], "beta_hat": info["beta_hat"], "xi": info["xi"],

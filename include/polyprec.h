@@ -100,6 +100,14 @@ typedef struct {
                          one captured CUDA graph                            */
   int sell_variant;   /* SELL kernel: 0 auto, 1 direct global loads,
                          2 slices staged in shared memory by TMA bulk copies */
+  int lowrank;        /* p in [0, 32]: low-rank acceleration of Section 3.1,
+                         P_hat = p_k(A_hat) + V (V^T A_hat V)^{-1} V^T with V
+                         the Ritz vectors of the p smallest Ritz values of
+                         the setup Lanczos run, which then keeps its basis
+                         (full reorthogonalisation, lanczos_steps >= p
+                         steps, (lanczos_steps + 1 + p) n doubles of
+                         workspace) and also gives the interval when
+                         interval = LANCZOS.  0: no correction            */
 } pp_options;
 
 typedef struct {
@@ -126,11 +134,16 @@ typedef struct {
   int k, apply_prec, lanczos_steps_done;
   double t_setup_ms;
   int grid_blocks;    /* blocks of the persistent step kernels             */
+  int lowrank;        /* vectors of the low-rank correction in use         */
+  double ritz_resid;  /* max over those Ritz pairs of beta_m |y_m| / theta,
+                         the relative residual ||A_hat v - theta v|| / theta
+                         (0 for caller vectors)                            */
+  double ritz_min;    /* smallest Ritz value of the setup Lanczos run      */
 } pp_info;
 
 /* Fill *opt with defaults: k=20, xi=-1 (auto), Lanczos with 10 steps, seed 0,
  * Jacobi seed, automatic format, FP64 apply, plain PCG, maxit 10000,
- * rtol 1e-8, zero_guess 1, check_every 4, use_graphs 0. */
+ * rtol 1e-8, zero_guess 1, check_every 4, use_graphs 0, lowrank 0. */
 void pp_options_default(pp_options* opt);
 
 /* Chebyshev coefficients (host, pure).  Section 2.2 and Eq. thetamod:
@@ -157,7 +170,9 @@ int pcg_setup(pp_ctx** ctx, const pp_csr* A, const pp_options* opt, void* worksp
 
 /* z = P r for nrhs vectors (device, n x nrhs column-major), P = W p_k(A_hat)
  * W^T by Algorithm 2: k products by A_hat, each fused with its recurrence
- * update into one pass over the matrix.  Asynchronous. */
+ * update into one pass over the matrix.  With a low-rank correction in use
+ * (Section 3.1) P = W (p_k(A_hat) + V (V^T A_hat V)^{-1} V^T) W^T.
+ * Asynchronous. */
 int polyprec_apply(pp_ctx* ctx, const double* r, double* z, int nrhs, void* stream);
 
 /* y = A x with the operator of the context (unscaled A, or S_u for a Schur
@@ -166,12 +181,24 @@ int pp_operator_apply(pp_ctx* ctx, const double* x, double* y, int nrhs, void* s
 
 /* Solve A x = b (or S_u u = r for a Schur context) by PCG (Section 1) with
  * P = W p_k(A_hat) W^T: standard Hestenes-Stiefel PCG on the seed-scaled
- * system, 1 + k operator products and 3 inner products per iteration, stop
+ * system, 1 + k operator products and 3 inner products per iteration (3 + p
+ * with a rank-p correction, Section 3.1 and Table 4), stop
  * when ||r_hat||/||b_hat|| <= rtol.  b, x: device, n.  x is read as the
  * initial guess unless zero_guess.  stats: host, may be NULL.  Returns
  * PP_OK, PP_MAXIT, PP_EBREAKDOWN or PP_ENONFINITE (x holds the last
  * iterate).  Synchronous with respect to the host. */
 int pcg_solve(pp_ctx* ctx, const double* b, double* x, pp_stats* stats, void* stream);
+
+/* Replace the low-rank correction (Section 3.1) by p caller vectors U
+ * (device, n x p column-major, leading dimension ldu >= n, caller row order,
+ * in the space of the unscaled operator): the preconditioner becomes
+ * P = W p_k(A_hat) W^T + U (U^T A U)^{-1} U^T, i.e. V = W^{-1} U in the
+ * seed-scaled space.  U^T A U is formed here (p operator products) and
+ * inverted on the host.  p must not exceed opt.lowrank of the setup (the
+ * workspace reserved); p = 0 removes the correction.  PP_EBREAKDOWN if
+ * U^T A U is not positive definite (then no correction is in use);
+ * PP_EUNSUPPORTED for batch contexts.  Synchronous. */
+int pp_set_lowrank(pp_ctx* ctx, const double* U, int p, long long ldu, void* stream);
 
 /* Context facts (host struct). */
 int pp_get_info(const pp_ctx* ctx, pp_info* info);

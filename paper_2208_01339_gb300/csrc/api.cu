@@ -148,6 +148,9 @@ int validate_options(pp_ctx* c, const pp_options* o) {
   if (o->check_every < 0 || o->check_every > kMaxCheck) return fail(c, PP_EINVAL, "check_every must be in [0, 64]");
   if (o->sell_sigma < 0) return fail(c, PP_EINVAL, "sell_sigma must be >= 0");
   if (o->sell_variant < 0 || o->sell_variant > 2) return fail(c, PP_EINVAL, "sell_variant must be 0, 1 or 2");
+  if (o->lowrank < 0 || o->lowrank > kMaxLowRank) return fail(c, PP_EINVAL, "lowrank must be in [0, 32]");
+  if (o->lowrank > 0 && (o->lanczos_steps < o->lowrank || o->lanczos_steps > kMaxLanczos))
+    return fail(c, PP_EINVAL, "lowrank > 0 needs lowrank <= lanczos_steps <= 512");
   return PP_OK;
 }
 
@@ -301,6 +304,10 @@ size_t layout(pp_ctx* c, void* base, const SellPlan& P) {
     c->z32 = B.take<float>(n_pad);
   }
   c->vec_end = reinterpret_cast<void*>(B.base + B.off);
+  c->lr_cap = c->opt.lowrank;
+  c->lr_m = c->lr_cap > 0 ? c->opt.lanczos_steps : 0;
+  c->lr_base = B.take<char>((long long)lowrank_bytes(c->lr_cap, c->lr_m, n_pad, kMaxGrid));
+  lowrank_carve(c, c->lr_base);
   return B.off + 256;
 }
 
@@ -451,6 +458,9 @@ extern "C" int pp_get_info(const pp_ctx* c, pp_info* info) {
   info->lanczos_steps_done = c->lanczos_steps_done;
   info->t_setup_ms = c->t_setup_ms;
   info->grid_blocks = c->grid_step;
+  info->lowrank = c->lr_p;
+  info->ritz_resid = c->lr_ritz_resid;
+  info->ritz_min = c->lr_ritz_min;
   return PP_OK;
 }
 

@@ -11,6 +11,7 @@ namespace pp {
 constexpr int kMaxDots = 3;        // values reduced by one fused kernel
 constexpr int kMaxLanczos = 512;   // Lanczos steps kept on the device
 constexpr int kBlock = 256;        // threads per block of the streaming kernels
+constexpr int kMaxLowRank = 32;    // vectors of the low-rank correction (Section 3.1)
 
 // PCG / Lanczos state kept on the device so that a block of iterations can
 // run (or be replayed as a CUDA graph) without host round trips.  Kernels
@@ -39,7 +40,16 @@ struct Scalars {
 
 // Counter slots (one per kernel family so that consecutive kernels never
 // share a counter).
-enum CounterSlot { kCntStep = 0, kCntUpdXR = 1, kCntUpdP = 2, kCntVec = 3, kCntLan = 4, kCntSchur = 5 };
+enum CounterSlot { kCntStep = 0, kCntUpdXR = 1, kCntUpdP = 2, kCntVec = 3, kCntLan = 4, kCntSchur = 5, kCntLr = 6 };
+
+// Device state of the low-rank correction: G^{-1} = (V^T A V)^{-1} (row
+// stride kMaxLowRank), the coefficients c = G^{-1} V^T r of the latest
+// application, and the Gram-Schmidt coefficients of the Lanczos run.
+struct LowRankState {
+  double Ginv[kMaxLowRank * kMaxLowRank];
+  double c[kMaxLowRank];
+  double h[kMaxLanczos + 8];
+};
 
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll

@@ -43,6 +43,15 @@ void destroy_ctx_resources(pp_ctx* c);
 // batched.cu
 void batch_free(pp_batch_state* b);
 
+// lowrank.cu (Section 3.1)
+size_t lowrank_bytes(int cap, int m, long long n_pad, int grid_max);
+void lowrank_carve(pp_ctx* c, void* base);
+int lowrank_lanczos(pp_ctx* c, cudaStream_t s, std::vector<double>& ta, std::vector<double>& tb);
+int lowrank_build_G(pp_ctx* c, int p, cudaStream_t s);
+cudaError_t lowrank_coefs(pp_ctx* c, const Scalars* skip, const double* r, cudaStream_t s);
+cudaError_t lowrank_update(pp_ctx* c, const Scalars* skip, double* z, const double* r, const double* q,
+                           double* rz_out, double* zq_out, cudaStream_t s);
+
 // schur.cu
 cudaError_t schur_scaled_step(pp_ctx* c, const StepParams& p, const Scalars* skip, unsigned int* counter,
                               cudaStream_t s);
@@ -84,4 +93,11 @@ struct pp_ctx {
   pp::SchurImpl* schur = nullptr;
   pp_batch_state* batch = nullptr;
   int op_launches = 1;  // kernel launches per operator step (1 for a matrix)
+  // low-rank correction (Section 3.1): capacity (opt.lowrank), Lanczos steps
+  // kept for it, vectors in use; V and the Lanczos basis Q hold n_pad rows
+  int lr_cap = 0, lr_m = 0, lr_p = 0;
+  pp::LowRankState* lr = nullptr;
+  double *V = nullptr, *Q = nullptr, *lr_Y = nullptr, *lr_part = nullptr;
+  void* lr_base = nullptr;
+  double lr_ritz_resid = 0, lr_ritz_min = 0;
 };

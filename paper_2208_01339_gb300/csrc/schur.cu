@@ -625,6 +625,10 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
   c->t2 = B.take<double>(n_pad);
   c->bh = B.take<double>(n_pad);
   c->vec_end = reinterpret_cast<void*>(B.base + B.off);
+  c->lr_cap = c->opt.lowrank;
+  c->lr_m = c->lr_cap > 0 ? c->opt.lanczos_steps : 0;
+  c->lr_base = B.take<char>((long long)lowrank_bytes(c->lr_cap, c->lr_m, n_pad, kMaxGrid));
+  lowrank_carve(c, c->lr_base);
   S->n_T = P.n_T;
   return B.off + 256;
 }
@@ -747,6 +751,7 @@ extern "C" int pp_schur_workspace_size(const pp_dfn* d, const pp_options* opt, s
   TracePlan P;
   if ((rc = plan_traces(d, P, nullptr))) return rc;
   pp_ctx tmp;
+  tmp.opt = *opt;
   SchurImpl S;
   return prepare(&tmp, &S, d, P, nullptr, false, nullptr, bytes);
 }

@@ -79,21 +79,40 @@ cudaError_t cheb_core(pp_ctx* c, const Scalars* skip, const void* rin, void* zou
 }
 
 // z = p_k(A_hat) r on the internal FP64 vectors r, z, with (r, z) -> rz_new
-// and, for flexible CG, (q, z) -> zq.
+// and, for flexible CG, (q, z) -> zq.  With a low-rank correction in use
+// (Section 3.1) c = G^{-1} V^T r is formed first and z += V c, fused with
+// the inner products, follows the polynomial.
 cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s) {
   Scalars* sc = c->sc;
   VecLaunch L{c->grid_vec, c->partials, s};
   const double* q = c->opt.flexible ? c->q : nullptr;
-  const int nd = q ? 2 : 1;
-  if (c->opt.k == 0)
-    return vec_scale_dot(L, c->n, skip, c->r, c->z, kF64, 1.0 / c->theta_bar, c->r, q, &sc->rz_new, &sc->zq,
-                         &sc->counters[kCntVec]);
-  if (!c->mixed) return cheb_core(c, skip, c->r, c->z, nd, &sc->rz_new, q, &sc->zq, s);
-  cudaError_t e = vec_convert(L, c->n, c->r, kF64, c->r32, kF32, skip);
-  if (e == cudaSuccess) e = cheb_core(c, skip, c->r32, c->z32, 0, nullptr, nullptr, nullptr, s);
-  if (e == cudaSuccess)
-    e = vec_from32_dot(L, c->n, skip, c->z32, c->z, c->r, q, &sc->rz_new, &sc->zq, &sc->counters[kCntVec]);
+  const bool lr = c->lr_p > 0;
+  const int nd = lr ? 0 : (q ? 2 : 1);
+  double* rz = lr ? nullptr : &sc->rz_new;
+  const double* qd = lr ? nullptr : q;
+  cudaError_t e = lr ? lowrank_coefs(c, skip, c->r, s) : cudaSuccess;
+  if (e != cudaSuccess) return e;
+  if (c->opt.k == 0) {
+    e = vec_scale_dot(L, c->n, skip, c->r, c->z, kF64, 1.0 / c->theta_bar, c->r, qd, rz, &sc->zq,
+                      &sc->counters[kCntVec]);
+  } else if (!c->mixed) {
+    e = cheb_core(c, skip, c->r, c->z, nd, rz, qd, &sc->zq, s);
+  } else {
+    e = vec_convert(L, c->n, c->r, kF64, c->r32, kF32, skip);
+    if (e == cudaSuccess) e = cheb_core(c, skip, c->r32, c->z32, 0, nullptr, nullptr, nullptr, s);
+    if (e == cudaSuccess)
+      e = vec_from32_dot(L, c->n, skip, c->z32, c->z, c->r, qd, rz, &sc->zq, &sc->counters[kCntVec]);
+  }
+  if (e == cudaSuccess && lr) e = lowrank_update(c, skip, c->z, c->r, q, &sc->rz_new, &sc->zq, s);
   return e;
+}
+
+// Kernel launches of one precond() call.
+long long precond_launches(const pp_ctx* c) {
+  const long long k = c->opt.k;
+  long long n = k == 0 ? 1 : (c->mixed ? k * c->op_launches + 2 : k * c->op_launches);
+  if (c->lr_p > 0) n += 3;
+  return n;
 }
 
 // One PCG iteration (q = A p; x, r update; z = P r; p update).
@@ -162,7 +181,22 @@ int check_vec_args(pp_ctx* c, const void* a, const void* b) {
 
 int setup_interval_and_coeffs(pp_ctx* c, cudaStream_t s) {
   double a = 0.0, b = 0.0;
-  if (c->opt.interval == PP_INTERVAL_GIVEN) {
+  c->lr_p = 0;
+  if (c->lr_cap > 0) {
+    // Section 3.1: the Lanczos run keeps its basis; its p smallest Ritz
+    // pairs give the correction and its extreme Ritz values the interval.
+    std::vector<double> ta, tb;
+    const int rc = lowrank_lanczos(c, s, ta, tb);
+    if (rc) return rc;
+    if (c->opt.interval == PP_INTERVAL_GIVEN) {
+      a = c->opt.alpha;
+      b = c->opt.beta;
+    } else {
+      tridiag_extremes_jacobi(ta, tb, &a, &b);
+      if (!(a > 0.0)) return fail(c, PP_EBREAKDOWN, "Lanczos estimate of the smallest eigenvalue is not positive");
+      if (!(b > a)) b = a * (1.0 + 1e-12) + 1e-300;
+    }
+  } else if (c->opt.interval == PP_INTERVAL_GIVEN) {
     a = c->opt.alpha;
     b = c->opt.beta;
     c->lanczos_steps_done = 0;
@@ -254,6 +288,24 @@ extern "C" int polyprec_apply(pp_ctx* c, const double* r, double* z, int nrhs, v
   for (int j = 0; j < nrhs; ++j) {
     const double* rj = r + (size_t)j * c->n;
     double* zj = z + (size_t)j * c->n;
+    if (c->lr_p > 0) {  // FP64 r for V^T r, the polynomial in the apply precision, z += V c in FP64
+      cudaError_t e = vec_scale_in(L, c->n, c->n_pad, c->w, c->perm, rj, c->r, kF64, nullptr, nullptr);
+      if (e == cudaSuccess && c->mixed) e = vec_convert(L, c->n, c->r, kF64, c->r32, kF32, nullptr);
+      if (e == cudaSuccess) e = lowrank_coefs(c, nullptr, c->r, s);
+      if (e == cudaSuccess) {
+        if (c->opt.k == 0)
+          e = vec_scale_dot(L, c->n, nullptr, rin, zin, prec, 1.0 / c->theta_bar, nullptr, nullptr, nullptr, nullptr,
+                            nullptr);
+        else
+          e = cheb_core(c, nullptr, rin, zin, 0, nullptr, nullptr, nullptr, s);
+      }
+      if (e == cudaSuccess && c->mixed)
+        e = vec_from32_dot(L, c->n, nullptr, c->z32, c->z, nullptr, nullptr, nullptr, nullptr, nullptr);
+      if (e == cudaSuccess) e = lowrank_update(c, nullptr, c->z, c->r, nullptr, nullptr, nullptr, s);
+      if (e == cudaSuccess) e = vec_scale_out(L, c->n, c->w, c->perm, c->z, kF64, zj, 0);
+      if (e != cudaSuccess) return cuda_fail(c, e, "polyprec_apply");
+      continue;
+    }
     cudaError_t e = vec_scale_in(L, c->n, c->n_pad, c->w, c->perm, rj, rin, prec, nullptr, nullptr);
     if (e == cudaSuccess) {
       if (c->opt.k == 0)
@@ -332,8 +384,7 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
   if (e == cudaSuccess) e = vec_update_p(L, c->n, sc, c->z, c->p, 1);
   if (e != cudaSuccess) return cuda_fail(c, e, "pcg_solve start");
 
-  const long long k = c->opt.k;
-  const long long pre = k == 0 ? 1 : (c->mixed ? k * c->op_launches + 2 : k * c->op_launches);
+  const long long pre = precond_launches(c);
   long long launches = 1 + (c->opt.zero_guess ? 0 : 1 + c->op_launches) + 1 + pre + 1;
   int host[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // done, status, iter, maxit, flexible, lan_steps, dev_error, pad
   double t_apply = 0.0;
@@ -382,7 +433,7 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
     std::memset(st, 0, sizeof(*st));
     st->iterations = iters;
     st->mvp = (long long)iters * (c->opt.k + 1) + (c->opt.zero_guess ? 0 : 1);
-    st->dots = 3LL * iters;
+    st->dots = (3LL + c->lr_p) * iters;
     st->rel_res = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
     st->alpha_hat = c->alpha_hat;
     st->beta_hat = c->beta_hat;

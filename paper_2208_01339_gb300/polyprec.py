@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("sell_C", ctypes.c_int), ("sell_sigma", ctypes.c_int), ("apply_prec", ctypes.c_int),
                 ("flexible", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("zero_guess", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("sell_variant", ctypes.c_int)]
+                ("sell_variant", ctypes.c_int), ("lowrank", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -67,7 +67,8 @@ class Info(ctypes.Structure):
                 ("beta_hat", ctypes.c_double), ("xi", ctypes.c_double), ("theta_bar", ctypes.c_double),
                 ("delta", ctypes.c_double), ("sigma_bar", ctypes.c_double), ("k", ctypes.c_int),
                 ("apply_prec", ctypes.c_int), ("lanczos_steps_done", ctypes.c_int), ("t_setup_ms", ctypes.c_double),
-                ("grid_blocks", ctypes.c_int)]
+                ("grid_blocks", ctypes.c_int), ("lowrank", ctypes.c_int), ("ritz_resid", ctypes.c_double),
+                ("ritz_min", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -104,6 +105,7 @@ SIGNATURES = [
     ("pp_operator_apply", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     ("pcg_solve", ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(Stats), _vp]),
     ("pp_get_info", ctypes.c_int, [_vp, ctypes.POINTER(Info)]),
+    ("pp_set_lowrank", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_longlong, _vp]),
     ("pp_destroy", ctypes.c_int, [_vp]),
     ("pp_last_error", ctypes.c_char_p, [_vp]),
     ("pp_schur_workspace_size", ctypes.c_int, [ctypes.POINTER(Dfn), ctypes.POINTER(Options),
@@ -265,6 +267,13 @@ class Solver:
             z = torch.empty_like(r)
         _check(lib().polyprec_apply(self.ctx, _ptr(r), _ptr(z), nrhs, _stream(stream)), self.ctx)
         return z
+
+    def set_lowrank(self, U, stream=None):
+        """Use the caller vectors U ((p, n) FP64 on the device, unscaled space)
+        for the Section 3.1 correction U (U^T A U)^{-1} U^T; p = 0 removes it."""
+        U = U.contiguous()
+        p = 0 if U.numel() == 0 else (1 if U.dim() == 1 else U.shape[0])
+        _check(lib().pp_set_lowrank(self.ctx, _ptr(U) if p else None, p, self.n, _stream(stream)), self.ctx)
 
     def operator(self, x, y=None, stream=None):
         torch = _torch()
