@@ -219,8 +219,6 @@ def run_reference(args, w, rank):
 
     A, b = build_problem(w)
     k = args.k if args.k is not None else w["k"]
-    if args.lanczos_steps:
-        w["lanczos"] = args.lanczos_steps
     vh, _ = O.jacobi_scale(A)
     a, bb = O.lanczos(A, I.lanczos_start(A.n, 0), w["lanczos"], val=vh)
     alpha, beta = O.tridiag_extremes(a, bb)
@@ -266,9 +264,12 @@ def run_k_sweep(args, w, A, b, opts, dev):
             x, st = S.solve(bt)
             ts.append(st["t_solve_ms"])
         apply_us = st["t_apply_ms"] / max(1, st["apply_launches"]) * 1e3
+        info = S.info()
         print(json.dumps({"workload": args.workload, "prec": w["prec"], "k": k, "iterations": st["iterations"],
                           "time_s": statistics.median(ts) / 1e3, "mvp": st["mvp"], "dots": st["dots"],
-                          "step_us": round(apply_us, 2), "status": st["status"]}), flush=True)
+                          "step_us": round(apply_us, 2), "status": st["status"], "lowrank": info["lowrank"],
+                          "alpha_hat": info["alpha_hat"], "setup_ms": round(info["t_setup_ms"], 2),
+                          "ritz_resid": info["ritz_resid"]}), flush=True)
         S.close()
 
 
@@ -437,6 +438,8 @@ def main():
         w["count"] = args.batch_count
     if args.batch_nmax:
         w["nmax"] = args.batch_nmax
+    if args.lanczos_steps:
+        w["lanczos"] = args.lanczos_steps
 
     from paper_2208_01339_gb300 import replicas
 

@@ -103,11 +103,14 @@ typedef struct {
   int lowrank;        /* p in [0, 32]: low-rank acceleration of Section 3.1,
                          P_hat = p_k(A_hat) + V (V^T A_hat V)^{-1} V^T with V
                          the Ritz vectors of the p smallest Ritz values of
-                         the setup Lanczos run, which then keeps its basis
-                         (full reorthogonalisation, lanczos_steps >= p
-                         steps, (lanczos_steps + 1 + p) n doubles of
-                         workspace) and also gives the interval when
-                         interval = LANCZOS.  0: no correction            */
+                         lowrank_steps Lanczos steps (full
+                         reorthogonalisation, start vector as for the
+                         interval) on p_k(A_hat) A_hat, a polynomial in
+                         A_hat with its eigenvectors and a far smaller
+                         condition number.  The interval is not changed.
+                         Workspace: (lowrank_steps + 1 + p) n doubles
+                         more.  0: no correction                           */
+  int lowrank_steps;  /* Lanczos steps for those vectors, >= lowrank; 0: 30 */
 } pp_options;
 
 typedef struct {
@@ -135,10 +138,10 @@ typedef struct {
   double t_setup_ms;
   int grid_blocks;    /* blocks of the persistent step kernels             */
   int lowrank;        /* vectors of the low-rank correction in use         */
-  double ritz_resid;  /* max over those Ritz pairs of beta_m |y_m| / theta,
-                         the relative residual ||A_hat v - theta v|| / theta
-                         (0 for caller vectors)                            */
-  double ritz_min;    /* smallest Ritz value of the setup Lanczos run      */
+  int lowrank_steps_done; /* Lanczos steps run for them at setup           */
+  double ritz_resid;  /* max over them of ||A_hat v - theta v|| / theta,
+                         theta = v^T A_hat v (0 for caller vectors)        */
+  double theta_min;   /* smallest Rayleigh quotient theta of the vectors   */
 } pp_info;
 
 /* Fill *opt with defaults: k=20, xi=-1 (auto), Lanczos with 10 steps, seed 0,

@@ -18,6 +18,8 @@ Parity status of each routine (how it is pinned independently of itself):
   lanczos_basis             Q^T Q = I and Q^T A Q = T_m, n steps give the
                             exact spectrum
   tridiag_eig               numpy eigh of T (up to sign), residuals
+  lowrank_vectors           eigenvectors of A (residuals) on a spectrum
+                            with an isolated leftmost eigenvalue
   lowrank_apply             spectrum of P A for exact eigenvectors
                             (eigenvalue + 1, Section 3.1), invariance
                             under V -> V R, symmetry
@@ -73,7 +75,8 @@ class Options(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("xi", ctypes.c_double), ("interval", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("lanczos_steps", ctypes.c_int),
                 ("seed_scaling", ctypes.c_int), ("flexible", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("rtol", ctypes.c_double), ("lowrank", ctypes.c_int), ("lr_V", ctypes.POINTER(ctypes.c_double))]
+                ("rtol", ctypes.c_double), ("lowrank", ctypes.c_int), ("lowrank_steps", ctypes.c_int),
+                ("lr_V", ctypes.POINTER(ctypes.c_double))]
 
 
 class Dfn(ctypes.Structure):
@@ -100,6 +103,8 @@ def lib():
         L.oracle_tridiag_extremes.argtypes = [ctypes.c_int, _d, _d, _d, _d]
         L.oracle_lanczos_basis.argtypes = [ctypes.c_int, _i, _i, _d, _d, ctypes.c_int, _d, _d, _d]
         L.oracle_tridiag_eig.argtypes = [ctypes.c_int, _d, _d, ctypes.c_int, _d, _d]
+        L.oracle_lowrank_vectors.argtypes = [ctypes.c_int, _i, _i, _d, _d, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, _d]
         L.oracle_lowrank_apply.argtypes = [ctypes.c_int, _i, _i, _d, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_int, ctypes.c_int, _d, _d, _d]
         L.oracle_pcg_csr.argtypes = [ctypes.c_int, _i, _i, _d, _d, _d, _d, ctypes.POINTER(Options),
@@ -245,6 +250,22 @@ def tridiag_eig(a, b, i: int):
     return lam.value, y
 
 
+def lowrank_vectors(A, v0, alpha: float, beta: float, xi: float, k: int, p: int, m: int, val=None):
+    """(V, theta): Ritz vectors of the p smallest Ritz values of m Lanczos steps
+    (full reorthogonalisation) on p_k(A) A from v0, and v^T A v for each."""
+    V = np.zeros((p, A.n))
+    theta = np.zeros(p)
+    rp, ci = _i32(A.rowptr), _i32(A.col)
+    va = _f64(A.val if val is None else val)
+    v0 = _f64(v0)
+    rc = lib().oracle_lowrank_vectors(A.n, _p(rp, ctypes.c_int), _p(ci, ctypes.c_int), _p(va, ctypes.c_double),
+                                      _p(v0, ctypes.c_double), alpha, beta, xi, k, p, m, _p(V, ctypes.c_double),
+                                      _p(theta, ctypes.c_double))
+    if rc:
+        raise RuntimeError(f"oracle lowrank_vectors status {rc}")
+    return V.T.copy(), theta
+
+
 def lowrank_apply(A, alpha: float, beta: float, xi: float, k: int, V, r, val=None) -> np.ndarray:
     """z = p_k(A) r + V (V^T A V)^{-1} V^T r (Section 3.1); V is n x p."""
     V = np.asarray(V, dtype=np.float64)
@@ -264,11 +285,11 @@ def lowrank_apply(A, alpha: float, beta: float, xi: float, k: int, V, r, val=Non
 
 
 def make_options(k=20, xi=-1.0, interval="lanczos", alpha=0.0, beta=0.0, lanczos_steps=10, seed_scaling=True,
-                 flexible=False, maxit=10000, rtol=1e-8, lowrank=0, lr_V=None) -> Options:
+                 flexible=False, maxit=10000, rtol=1e-8, lowrank=0, lowrank_steps=0, lr_V=None) -> Options:
     """Options; lr_V (n x p, seed-scaled space) must stay alive while they are used."""
     o = Options(k=k, xi=xi, interval=0 if interval == "lanczos" else 1, alpha=alpha, beta=beta,
                 lanczos_steps=lanczos_steps, seed_scaling=1 if seed_scaling else 0,
-                flexible=1 if flexible else 0, maxit=maxit, rtol=rtol, lowrank=lowrank)
+                flexible=1 if flexible else 0, maxit=maxit, rtol=rtol, lowrank=lowrank, lowrank_steps=lowrank_steps)
     if lr_V is not None:
         o._keep = np.ascontiguousarray(np.asarray(lr_V, dtype=np.float64).T)
         o.lowrank = lr_V.shape[1]

@@ -641,49 +641,120 @@ static double auto_xi(double a, double b) {
   return xi;
 }
 
-/* The interval [alpha, beta] (given, or the extreme Ritz values of
- * lanczos_steps Lanczos steps from v0) and, when opt->lowrank = p > 0, the
- * vectors of the correction: opt->lr_V if given, else the Ritz vectors of
- * the p smallest Ritz values of the same Lanczos run, which then keeps its
- * basis (full reorthogonalisation).  *Vown receives memory to free. */
+/* The interval [alpha, beta]: given, or the extreme Ritz values of
+ * lanczos_steps plain Lanczos steps from v0. */
 static int pick_interval(const op_t* A, const double* v0, const oracle_options* opt,
-                         double* alpha, double* beta, const double** V, double** Vown) {
-  *V = opt->lr_V;
-  *Vown = NULL;
-  int need_ritz = opt->lowrank > 0 && opt->lr_V == NULL;
-  if (opt->interval == 1 && !need_ritz) {
+                         double* alpha, double* beta) {
+  if (opt->interval == 1) {
     *alpha = opt->alpha;
     *beta = opt->beta;
     return 0;
   }
-  int n = A->n;
   int m = opt->lanczos_steps > 0 ? opt->lanczos_steps : 10;
   double* a = (double*)calloc((size_t)m, sizeof(double));
   double* b = (double*)calloc((size_t)m, sizeof(double));
-  int rc = 0;
-  if (need_ritz) {
-    double* Q = (double*)calloc((size_t)n * m, sizeof(double));
-    int steps = lanczos_basis_op(A, v0, m, a, b, Q);
-    if (steps < opt->lowrank) {
-      rc = -1;
-    } else {
-      *Vown = (double*)malloc(sizeof(double) * (size_t)n * opt->lowrank);
-      ritz_vectors(n, steps, a, b, Q, opt->lowrank, *Vown, NULL);
-      *V = *Vown;
-      rc = oracle_tridiag_extremes(steps, a, b, alpha, beta);
-    }
-    free(Q);
-  } else {
-    int steps = lanczos_op(A, v0, m, a, b);
-    rc = steps > 0 ? oracle_tridiag_extremes(steps, a, b, alpha, beta) : -1;
-  }
-  if (opt->interval == 1) {
-    *alpha = opt->alpha;
-    *beta = opt->beta;
-  }
+  int steps = lanczos_op(A, v0, m, a, b);
+  int rc = steps > 0 ? oracle_tridiag_extremes(steps, a, b, alpha, beta) : -1;
   free(a);
   free(b);
   return rc;
+}
+
+/* The preconditioned operator B = p_k(A) A used to find the leftmost
+ * eigenvectors: a polynomial in A, so it has the eigenvectors of A, and
+ * with the xi-shifted polynomial the smallest eigenvalues of A go to the
+ * smallest of B (Theorem 2.3) while kappa(B) is far below kappa(A). */
+typedef struct {
+  const op_t* A;
+  const cheb_t* P;
+  double* t;
+} precop_t;
+
+static void precop_apply(const void* c, const double* x, double* y) {
+  const precop_t* pc = (const precop_t*)c;
+  pc->A->apply(pc->A->ctx, x, pc->t);
+  cheb_apply_op(pc->A, pc->P->m, pc->P->theta_bar, pc->P->delta, pc->P->sigma_bar, pc->P->rho, pc->t, y,
+                NULL);
+}
+
+/* Section 3.1 vectors: the Ritz vectors of the p smallest Ritz values of m
+ * Lanczos steps (full reorthogonalisation, from v0) on B = p_k(A) A, and
+ * their Rayleigh quotients theta_i = v_i^T A v_i (unit vectors). */
+static int lowrank_vectors_op(const op_t* A, const cheb_t* P, const double* v0, int p, int m,
+                              double* V, double* theta) {
+  int n = A->n;
+  precop_t pc = {A, P, (double*)malloc(sizeof(double) * (size_t)n)};
+  op_t B = {precop_apply, &pc, n};
+  double* a = (double*)calloc((size_t)m, sizeof(double));
+  double* b = (double*)calloc((size_t)m, sizeof(double));
+  double* Q = (double*)calloc((size_t)n * m, sizeof(double));
+  int steps = lanczos_basis_op(&B, v0, m, a, b, Q);
+  int rc = steps >= p ? ritz_vectors(n, steps, a, b, Q, p, V, NULL) : -1;
+  if (rc == 0 && theta) {
+    for (int i = 0; i < p; ++i) {
+      A->apply(A->ctx, V + (size_t)i * n, pc.t);
+      theta[i] = dot(n, V + (size_t)i * n, pc.t);
+    }
+  }
+  free(pc.t);
+  free(a);
+  free(b);
+  free(Q);
+  return rc;
+}
+
+int oracle_lowrank_vectors(int n, const int* rowptr, const int* col, const double* val,
+                           const double* v0, double alpha, double beta, double xi, int k, int p,
+                           int m, double* V, double* theta) {
+  if (p <= 0 || m < p) return -1;
+  double* rho = (double*)malloc(sizeof(double) * (size_t)(k + 1));
+  cheb_t P;
+  P.m = k;
+  P.rho = rho;
+  P.lr.p = 0;
+  int rc = oracle_cheb_coeffs(alpha, beta, xi, k, &P.theta_bar, &P.delta, &P.sigma_bar, rho);
+  if (rc == 0) {
+    csr_t c = {n, rowptr, col, val};
+    op_t op = {csr_apply, &c, n};
+    rc = lowrank_vectors_op(&op, &P, v0, p, m, V, theta);
+  }
+  free(rho);
+  return rc;
+}
+
+/* Everything the solve needs before its first iteration: the interval, xi,
+ * the coefficients and, for opt->lowrank = p > 0, the Section 3.1
+ * correction with V = opt->lr_V or the vectors of lowrank_vectors_op
+ * (lowrank_steps steps).  The interval is not changed by the correction:
+ * as in Section 3.1 the polynomial keeps its lower end and the correction
+ * lifts the images of the leftmost eigenvalues.  *Vown receives memory to
+ * free. */
+static int setup_prec(const op_t* A, const double* v0, const oracle_options* opt, cheb_t* P,
+                      double* rho, double* alpha, double* beta, double* xi, double** Vown) {
+  *Vown = NULL;
+  P->m = opt->k;
+  P->rho = rho;
+  P->lr.p = 0;
+  P->lr.V = NULL;
+  P->lr.L = NULL;
+  int rc = pick_interval(A, v0, opt, alpha, beta);
+  if (rc) return rc;
+  *xi = opt->xi >= 0.0 ? opt->xi : auto_xi(*alpha, *beta);
+  rc = oracle_cheb_coeffs(*alpha, *beta, *xi, opt->k, &P->theta_bar, &P->delta, &P->sigma_bar, rho);
+  if (rc || opt->lowrank <= 0) return rc;
+  int p = opt->lowrank;
+  const double* V = opt->lr_V;
+  if (V == NULL) {
+    int n = A->n;
+    int m = opt->lowrank_steps > 0 ? opt->lowrank_steps : 30;
+    double* theta = (double*)malloc(sizeof(double) * (size_t)p);
+    *Vown = (double*)malloc(sizeof(double) * (size_t)n * p);
+    rc = lowrank_vectors_op(A, P, v0, p, m, *Vown, theta);
+    V = *Vown;
+    free(theta);
+    if (rc) return rc;
+  }
+  return lowrank_setup(A, p, V, &P->lr);
 }
 
 int oracle_pcg_csr(int n, const int* rowptr, const int* col, const double* val,
@@ -709,21 +780,12 @@ int oracle_pcg_csr(int n, const int* rowptr, const int* col, const double* val,
     /* A_hat x_hat = b_hat with b_hat = W b, x = W x_hat */
     for (int i = 0; i < n; ++i) bh[i] = w[i] * b[i];
     for (int i = 0; i < n; ++i) xh[i] = x[i] / w[i];
-    double alpha, beta;
-    const double* V = NULL;
+    double alpha = 0.0, beta = 0.0, xi = 0.0;
     double* Vown = NULL;
-    rc = pick_interval(&A, v0, opt, &alpha, &beta, &V, &Vown);
+    cheb_t P;
+    rc = setup_prec(&A, v0, opt, &P, rho, &alpha, &beta, &xi, &Vown);
     if (rc == 0) {
-      double xi = opt->xi >= 0.0 ? opt->xi : auto_xi(alpha, beta);
-      cheb_t P;
-      P.m = opt->k;
-      P.rho = rho;
-      P.lr.p = 0;
-      P.lr.V = NULL;
-      P.lr.L = NULL;
-      rc = oracle_cheb_coeffs(alpha, beta, xi, opt->k, &P.theta_bar, &P.delta, &P.sigma_bar, rho);
-      if (rc == 0) rc = lowrank_setup(&A, opt->lowrank > 0 ? opt->lowrank : 0, V, &P.lr);
-      if (rc == 0) rc = pcg_op(&A, &P, bh, xh, opt->flexible, opt->maxit, opt->rtol, st);
+      rc = pcg_op(&A, &P, bh, xh, opt->flexible, opt->maxit, opt->rtol, st);
       if (st) {
         st->alpha_hat = alpha;
         st->beta_hat = beta;
@@ -739,8 +801,8 @@ int oracle_pcg_csr(int n, const int* rowptr, const int* col, const double* val,
         st->true_rel_res = bn > 0.0 ? sqrt(num) / bn : 0.0;
         free(t);
       }
-      free(P.lr.L);
     }
+    free(P.lr.L);
     free(Vown);
   }
   if (st) st->status = rc;
@@ -1023,21 +1085,12 @@ int oracle_pcg_schur(const oracle_schur* s, const double* ds, const double* r, d
     op_t A = {schur_scaled_apply, &ss, nu};
     for (int i = 0; i < nu; ++i) rh[i] = w[i] * r[i];
     for (int i = 0; i < nu; ++i) uh[i] = u[i] / w[i];
-    double alpha, beta;
-    const double* V = NULL;
+    double alpha = 0.0, beta = 0.0, xi = 0.0;
     double* Vown = NULL;
-    rc = pick_interval(&A, v0, opt, &alpha, &beta, &V, &Vown);
+    cheb_t P;
+    rc = setup_prec(&A, v0, opt, &P, rho, &alpha, &beta, &xi, &Vown);
     if (rc == 0) {
-      double xi = opt->xi >= 0.0 ? opt->xi : auto_xi(alpha, beta);
-      cheb_t P;
-      P.m = opt->k;
-      P.rho = rho;
-      P.lr.p = 0;
-      P.lr.V = NULL;
-      P.lr.L = NULL;
-      rc = oracle_cheb_coeffs(alpha, beta, xi, opt->k, &P.theta_bar, &P.delta, &P.sigma_bar, rho);
-      if (rc == 0) rc = lowrank_setup(&A, opt->lowrank > 0 ? opt->lowrank : 0, V, &P.lr);
-      if (rc == 0) rc = pcg_op(&A, &P, rh, uh, opt->flexible, opt->maxit, opt->rtol, st);
+      rc = pcg_op(&A, &P, rh, uh, opt->flexible, opt->maxit, opt->rtol, st);
       if (st) {
         st->alpha_hat = alpha;
         st->beta_hat = beta;
@@ -1055,8 +1108,8 @@ int oracle_pcg_schur(const oracle_schur* s, const double* ds, const double* r, d
         st->true_rel_res = bn > 0.0 ? sqrt(num / bn) : 0.0;
         free(t);
       }
-      free(P.lr.L);
     }
+    free(P.lr.L);
     free(Vown);
   }
   if (st) st->status = rc;

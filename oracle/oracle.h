@@ -21,6 +21,7 @@
  *   oracle_tridiag_extremes  Sturm-sequence bisection on T_m
  *   oracle_lanczos_basis   Lanczos keeping its (fully reorthogonalised) basis
  *   oracle_tridiag_eig     eigenpair of T_m: bisection + inverse iteration
+ *   oracle_lowrank_vectors leftmost eigenvectors by Lanczos on p_k(A) A
  *   oracle_lowrank_apply   Section 3.1: P = P_0 + V (V^T A V)^{-1} V^T
  *   oracle_pcg_csr         PCG (Section 1) with P = W p_k(A_hat) W^T
  *   oracle_schur_*         Section 4.2: Algorithm 3 (y = S_u r), Algorithm 4
@@ -75,6 +76,9 @@ int oracle_lanczos_basis(int n, const int* rowptr, const int* col, const double*
                          const double* v0, int m, double* a, double* b, double* Q);
 int oracle_tridiag_eig(int m, const double* a, const double* b, int i, double* lambda,
                        double* y);
+int oracle_lowrank_vectors(int n, const int* rowptr, const int* col, const double* val,
+                           const double* v0, double alpha, double beta, double xi, int k, int p,
+                           int m, double* V, double* theta);
 int oracle_lowrank_apply(int n, const int* rowptr, const int* col, const double* val,
                          double alpha, double beta, double xi, int k, int p, const double* V,
                          const double* r, double* z);
@@ -84,8 +88,9 @@ int oracle_lowrank_apply(int n, const int* rowptr, const int* col, const double*
  * seed_scaling: 0 none, 1 Jacobi.  flexible: 0 plain PCG, 1 flexible CG.
  * lowrank = p > 0 adds the Section 3.1 correction V (V^T A_hat V)^{-1} V^T
  * with V = lr_V (n x p, seed-scaled space) or, when lr_V is NULL, the Ritz
- * vectors of the p smallest Ritz values of the (basis-keeping) Lanczos run
- * of lanczos_steps steps from v0, which then also gives the interval. */
+ * vectors of the p smallest Ritz values of lowrank_steps (0: 30) Lanczos
+ * steps with full reorthogonalisation from v0 on p_k(A_hat) A_hat; the
+ * interval is not changed by the correction. */
 typedef struct {
   int k;
   double xi;
@@ -97,6 +102,7 @@ typedef struct {
   int maxit;
   double rtol;
   int lowrank;
+  int lowrank_steps;
   const double* lr_V;
 } oracle_options;
 

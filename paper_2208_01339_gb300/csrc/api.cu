@@ -149,8 +149,10 @@ int validate_options(pp_ctx* c, const pp_options* o) {
   if (o->sell_sigma < 0) return fail(c, PP_EINVAL, "sell_sigma must be >= 0");
   if (o->sell_variant < 0 || o->sell_variant > 2) return fail(c, PP_EINVAL, "sell_variant must be 0, 1 or 2");
   if (o->lowrank < 0 || o->lowrank > kMaxLowRank) return fail(c, PP_EINVAL, "lowrank must be in [0, 32]");
-  if (o->lowrank > 0 && (o->lanczos_steps < o->lowrank || o->lanczos_steps > kMaxLanczos))
-    return fail(c, PP_EINVAL, "lowrank > 0 needs lowrank <= lanczos_steps <= 512");
+  if (o->lowrank > 0 && o->lowrank_steps != 0 && (o->lowrank_steps < o->lowrank || o->lowrank_steps > kMaxLanczos))
+    return fail(c, PP_EINVAL, "lowrank > 0 needs lowrank <= lowrank_steps <= 512 (0: 30)");
+  if (o->lowrank > 30 && o->lowrank_steps == 0)
+    return fail(c, PP_EINVAL, "lowrank > 30 needs lowrank_steps >= lowrank");
   return PP_OK;
 }
 
@@ -305,7 +307,7 @@ size_t layout(pp_ctx* c, void* base, const SellPlan& P) {
   }
   c->vec_end = reinterpret_cast<void*>(B.base + B.off);
   c->lr_cap = c->opt.lowrank;
-  c->lr_m = c->lr_cap > 0 ? c->opt.lanczos_steps : 0;
+  c->lr_m = c->lr_cap > 0 ? (c->opt.lowrank_steps > 0 ? c->opt.lowrank_steps : 30) : 0;
   c->lr_base = B.take<char>((long long)lowrank_bytes(c->lr_cap, c->lr_m, n_pad, kMaxGrid));
   lowrank_carve(c, c->lr_base);
   return B.off + 256;
@@ -460,7 +462,8 @@ extern "C" int pp_get_info(const pp_ctx* c, pp_info* info) {
   info->grid_blocks = c->grid_step;
   info->lowrank = c->lr_p;
   info->ritz_resid = c->lr_ritz_resid;
-  info->ritz_min = c->lr_ritz_min;
+  info->lowrank_steps_done = c->lr_steps_done;
+  info->theta_min = c->lr_theta.empty() ? 0.0 : *std::min_element(c->lr_theta.begin(), c->lr_theta.end());
   return PP_OK;
 }
 

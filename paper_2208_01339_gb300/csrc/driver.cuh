@@ -36,6 +36,8 @@ int num_sms();
 
 // solve.cu
 int setup_interval_and_coeffs(pp_ctx* c, cudaStream_t s);
+// y = p_k(A_hat) A_hat x on FP64 vectors (the polynomial in the apply precision)
+cudaError_t prec_op_apply(pp_ctx* c, const double* x, double* y, cudaStream_t s);
 cudaError_t op_step(pp_ctx* c, bool apply_matrix, const StepParams& p, const Scalars* skip, unsigned int* counter,
                     cudaStream_t s);
 void destroy_ctx_resources(pp_ctx* c);
@@ -46,8 +48,8 @@ void batch_free(pp_batch_state* b);
 // lowrank.cu (Section 3.1)
 size_t lowrank_bytes(int cap, int m, long long n_pad, int grid_max);
 void lowrank_carve(pp_ctx* c, void* base);
-int lowrank_lanczos(pp_ctx* c, cudaStream_t s, std::vector<double>& ta, std::vector<double>& tb);
-int lowrank_build_G(pp_ctx* c, int p, cudaStream_t s);
+int lowrank_lanczos(pp_ctx* c, cudaStream_t s);
+int lowrank_build_G(pp_ctx* c, int p, bool unit_cols, cudaStream_t s);
 cudaError_t lowrank_coefs(pp_ctx* c, const Scalars* skip, const double* r, cudaStream_t s);
 cudaError_t lowrank_update(pp_ctx* c, const Scalars* skip, double* z, const double* r, const double* q,
                            double* rz_out, double* zq_out, cudaStream_t s);
@@ -99,5 +101,7 @@ struct pp_ctx {
   pp::LowRankState* lr = nullptr;
   double *V = nullptr, *Q = nullptr, *lr_Y = nullptr, *lr_part = nullptr;
   void* lr_base = nullptr;
-  double lr_ritz_resid = 0, lr_ritz_min = 0;
+  int lr_steps_done = 0;
+  double lr_ritz_resid = 0;
+  std::vector<double> lr_theta;  // Rayleigh quotients v^T A_hat v of the vectors
 };

@@ -230,10 +230,13 @@ void lowrank_carve(pp_ctx* c, void* base) {
 }
 
 // G = V^T A_hat V for the first p columns of V, inverted on the host
-// (Cholesky, then the explicit inverse) and stored in lr->Ginv.
-int lowrank_build_G(pp_ctx* c, int p, cudaStream_t s) {
+// (Cholesky, then the explicit inverse) and stored in lr->Ginv.  With
+// unit_cols (Ritz vectors), theta_c = G_cc are Rayleigh quotients and the
+// relative residuals ||A_hat v_c - theta_c v_c|| / theta_c are recorded.
+int lowrank_build_G(pp_ctx* c, int p, bool unit_cols, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  std::vector<double> G((size_t)p * p);
+  VecLaunch L{c->grid_vec, c->partials, s};
+  std::vector<double> G((size_t)p * p), av2(p);
   for (int j = 0; j < p && e == cudaSuccess; ++j) {
     StepParams sp;
     sp.mode = kSpmv;
@@ -241,24 +244,34 @@ int lowrank_build_G(pp_ctx* c, int p, cudaStream_t s) {
     sp.y = c->t1;
     e = op_step(c, false, sp, nullptr, &c->sc->counters[kCntStep], s);
     if (e == cudaSuccess) e = mdot(c, p, c->V, c->t1, c->lr->h, s);
+    if (e == cudaSuccess) e = vec_dot(L, c->n, c->t1, c->t1, &c->sc->vv, &c->sc->counters[kCntLan]);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&G[(size_t)j * p], c->lr->h, sizeof(double) * p,
                                               cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&av2[j], &c->sc->vv, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "low-rank V^T A V");
+  c->lr_theta.assign(p, 0.0);
+  c->lr_ritz_resid = 0.0;
+  for (int j = 0; j < p; ++j) {
+    const double th = G[(size_t)j * p + j];
+    c->lr_theta[j] = th;
+    if (unit_cols && th > 0.0)
+      c->lr_ritz_resid = std::max(c->lr_ritz_resid, std::sqrt(std::max(av2[j] - th * th, 0.0)) / th);
+  }
   // G[j * p + i] = V_i . A V_j; use the lower triangle i >= j
-  std::vector<double> L((size_t)p * p, 0.0);
+  std::vector<double> Lc((size_t)p * p, 0.0);
   for (int j = 0; j < p; ++j) {
     double d = G[(size_t)j * p + j];
-    for (int k = 0; k < j; ++k) d -= L[(size_t)j * p + k] * L[(size_t)j * p + k];
+    for (int k = 0; k < j; ++k) d -= Lc[(size_t)j * p + k] * Lc[(size_t)j * p + k];
     // relative threshold: dependent columns leave d at rounding level
     if (!(d > 1e-13 * std::fabs(G[(size_t)j * p + j])) || !std::isfinite(d))
       return fail(c, PP_EBREAKDOWN, "V^T A V is not positive definite (dependent or zero correction vectors)");
-    L[(size_t)j * p + j] = std::sqrt(d);
+    Lc[(size_t)j * p + j] = std::sqrt(d);
     for (int i = j + 1; i < p; ++i) {
       double t = G[(size_t)j * p + i];
-      for (int k = 0; k < j; ++k) t -= L[(size_t)i * p + k] * L[(size_t)j * p + k];
-      L[(size_t)i * p + j] = t / L[(size_t)j * p + j];
+      for (int k = 0; k < j; ++k) t -= Lc[(size_t)i * p + k] * Lc[(size_t)j * p + k];
+      Lc[(size_t)i * p + j] = t / Lc[(size_t)j * p + j];
     }
   }
   // Ginv = L^{-T} L^{-1}, column by column
@@ -267,13 +280,13 @@ int lowrank_build_G(pp_ctx* c, int p, cudaStream_t s) {
     for (int i = 0; i < p; ++i) col[i] = (i == j) ? 1.0 : 0.0;
     for (int i = 0; i < p; ++i) {
       double t = col[i];
-      for (int k = 0; k < i; ++k) t -= L[(size_t)i * p + k] * col[k];
-      col[i] = t / L[(size_t)i * p + i];
+      for (int k = 0; k < i; ++k) t -= Lc[(size_t)i * p + k] * col[k];
+      col[i] = t / Lc[(size_t)i * p + i];
     }
     for (int i = p - 1; i >= 0; --i) {
       double t = col[i];
-      for (int k = i + 1; k < p; ++k) t -= L[(size_t)k * p + i] * col[k];
-      col[i] = t / L[(size_t)i * p + i];
+      for (int k = i + 1; k < p; ++k) t -= Lc[(size_t)k * p + i] * col[k];
+      col[i] = t / Lc[(size_t)i * p + i];
     }
     for (int i = 0; i < p; ++i) Ginv[(size_t)i * kMaxLowRank + j] = col[i];
   }
@@ -284,13 +297,16 @@ int lowrank_build_G(pp_ctx* c, int p, cudaStream_t s) {
   return PP_OK;
 }
 
-// Lanczos on A_hat keeping its basis Q (columns of n_pad doubles): step j
-// forms w = A q_j - b_{j-1} q_{j-1} and a_j = (q_j, w) in one fused pass,
-// w -= a_j q_j, then w is orthogonalised against q_0..q_j by classical
-// Gram-Schmidt, twice, b_j = ||w||, q_{j+1} = w / b_j.  The p smallest
-// Ritz pairs give V = Q Y; returns the tridiagonal (ta, tb) for the
-// interval.  b_m (the coupling to q_{m+1}) gives the Ritz residuals.
-int lowrank_lanczos(pp_ctx* c, cudaStream_t s, std::vector<double>& ta, std::vector<double>& tb) {
+// The vectors of the correction: Lanczos with a kept basis Q (columns of
+// n_pad doubles) on the preconditioned operator B = p_k(A_hat) A_hat, which
+// has the eigenvectors of A_hat, maps its smallest eigenvalues to the
+// smallest of B (Theorem 2.3) and is far better conditioned, so its
+// leftmost Ritz pairs converge in few steps.  Step j: w = B q_j -
+// b_{j-1} q_{j-1}, a_j = (q_j, w), w -= a_j q_j, then classical Gram-Schmidt
+// against q_0..q_j, twice, b_j = ||w||, q_{j+1} = w / b_j.  The Ritz
+// vectors of the p smallest Ritz values give V = Q Y; G = V^T A_hat V
+// follows.  Needs the coefficients of p_k.
+int lowrank_lanczos(pp_ctx* c, cudaStream_t s) {
   const int m = c->lr_m;
   const long long ld = c->n_pad;
   Scalars* sc = c->sc;
@@ -301,19 +317,14 @@ int lowrank_lanczos(pp_ctx* c, cudaStream_t s, std::vector<double>& ta, std::vec
     e = lanczos_start(L, c->n, c->n_pad, splitmix_key(c->opt.seed, 3), c->perm, Q, &sc->vv, &sc->counters[kCntVec]);
   if (e == cudaSuccess) e = vec_scale_by_rsqrt(L, c->n, Q, &sc->vv);
   int steps = 0;
-  std::vector<double> hb2(1);
+  std::vector<double> ha, hb;
+  double h2[2] = {0.0, 0.0};
   for (int j = 0; j < m && e == cudaSuccess; ++j) {
     double* qj = Q + (long long)j * ld;
     double* w = Q + (long long)(j + 1) * ld;
-    StepParams p;
-    p.mode = kLanczos;
-    p.ndot = 1;
-    p.x = qj;
-    p.xold = j > 0 ? Q + (long long)(j - 1) * ld : nullptr;
-    p.y = w;
-    p.dev_coef = j > 0 ? &sc->lan_b2[j - 1] : nullptr;
-    p.dot_out0 = &sc->lan_a[j];
-    e = op_step(c, false, p, nullptr, &sc->counters[kCntStep], s);
+    e = prec_op_apply(c, qj, w, s);
+    if (e == cudaSuccess && j > 0) e = vec_axpby(L, c->n, -hb[j - 1], Q + (long long)(j - 1) * ld, 1.0, w);
+    if (e == cudaSuccess) e = vec_dot(L, c->n, qj, w, &sc->lan_a[j], &sc->counters[kCntLan]);
     if (e == cudaSuccess)
       e = lanczos_orth(L, c->n, w, qj, &sc->lan_a[j], &sc->lan_b2[j], &sc->counters[kCntLan]);
     for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
@@ -324,39 +335,26 @@ int lowrank_lanczos(pp_ctx* c, cudaStream_t s, std::vector<double>& ta, std::vec
       }
     }
     if (e == cudaSuccess) e = vec_dot(L, c->n, w, w, &sc->lan_b2[j], &sc->counters[kCntLan]);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb2.data(), &sc->lan_b2[j], sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h2[0], &sc->lan_a[j], sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h2[1], &sc->lan_b2[j], sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) break;
+    if (!std::isfinite(h2[0]) || !std::isfinite(h2[1])) return fail(c, PP_ENONFINITE, "non-finite Lanczos coefficient");
+    ha.push_back(h2[0]);
+    hb.push_back(std::sqrt(h2[1]));
     steps = j + 1;
-    if (!(hb2[0] > 1e-300)) break;  // invariant subspace
+    if (!(h2[1] > 1e-300)) break;  // invariant subspace
     if (j < m - 1) e = vec_scale_by_rsqrt(L, c->n, w, &sc->lan_b2[j]);
   }
-  std::vector<double> ha(std::max(steps, 1)), hb(std::max(steps, 1));
-  if (e == cudaSuccess && steps > 0)
-    e = cudaMemcpyAsync(ha.data(), sc->lan_a, sizeof(double) * steps, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && steps > 0)
-    e = cudaMemcpyAsync(hb.data(), sc->lan_b2, sizeof(double) * steps, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "Lanczos with full reorthogonalisation");
-  for (int j = 0; j < steps; ++j)
-    if (!std::isfinite(ha[j]) || !std::isfinite(hb[j])) return fail(c, PP_ENONFINITE, "non-finite Lanczos coefficient");
+  if (e != cudaSuccess) return cuda_fail(c, e, "Lanczos on the preconditioned operator");
   const int p = c->lr_cap;
   if (steps < p) return fail(c, PP_EBREAKDOWN, "Lanczos ended (invariant subspace) before lowrank Ritz pairs formed");
-  ta.assign(ha.begin(), ha.begin() + steps);
-  tb.clear();
-  for (int j = 0; j + 1 < steps; ++j) tb.push_back(std::sqrt(hb[j]));
-  const double beta_m = std::sqrt(hb[steps - 1]);
-  std::vector<double> w, S;
-  tridiag_eig_jacobi(ta, tb, w, S);
+  std::vector<double> ta(ha.begin(), ha.begin() + steps), tb(hb.begin(), hb.begin() + steps - 1);
+  std::vector<double> wv, S;
+  tridiag_eig_jacobi(ta, tb, wv, S);
   std::vector<double> Y((size_t)steps * p);
-  double worst = 0.0;
-  for (int cc = 0; cc < p; ++cc) {
+  for (int cc = 0; cc < p; ++cc)
     for (int j = 0; j < steps; ++j) Y[(size_t)j * p + cc] = S[(size_t)j * steps + cc];
-    const double res = beta_m * std::fabs(S[(size_t)(steps - 1) * steps + cc]);
-    worst = std::max(worst, res / std::max(std::fabs(w[cc]), 1e-300));
-  }
-  c->lr_ritz_resid = worst;
-  c->lr_ritz_min = w[0];
   e = cudaMemcpyAsync(c->lr_Y, Y.data(), sizeof(double) * Y.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     combine_kernel<<<c->grid_vec, kBlock, 0, s>>>(c->n_pad, steps, Q, ld, p, c->lr_Y, c->V);
@@ -364,8 +362,8 @@ int lowrank_lanczos(pp_ctx* c, cudaStream_t s, std::vector<double>& ta, std::vec
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "Ritz vectors");
-  c->lanczos_steps_done = steps;
-  return lowrank_build_G(c, p, s);
+  c->lr_steps_done = steps;
+  return lowrank_build_G(c, p, true, s);
 }
 
 // Per application: c = G^{-1} V^T r (2 launches, before p_k) ...
@@ -418,9 +416,7 @@ extern "C" int pp_set_lowrank(pp_ctx* c, const double* U, int p, long long ldu, 
   for (int j = 0; j < p && e == cudaSuccess; ++j)
     e = vec_unscale_in(L, c->n, c->n_pad, c->w, c->perm, U + (long long)j * ldu, c->V + (long long)j * c->n_pad);
   if (e != cudaSuccess) return cuda_fail(c, e, "pp_set_lowrank");
-  c->lr_ritz_resid = 0.0;
-  c->lr_ritz_min = 0.0;
-  const int rc = lowrank_build_G(c, p, s);
+  const int rc = lowrank_build_G(c, p, false, s);
   if (rc) c->lr_p = 0;
   return rc;
 }

@@ -626,7 +626,7 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
   c->bh = B.take<double>(n_pad);
   c->vec_end = reinterpret_cast<void*>(B.base + B.off);
   c->lr_cap = c->opt.lowrank;
-  c->lr_m = c->lr_cap > 0 ? c->opt.lanczos_steps : 0;
+  c->lr_m = c->lr_cap > 0 ? (c->opt.lowrank_steps > 0 ? c->opt.lowrank_steps : 30) : 0;
   c->lr_base = B.take<char>((long long)lowrank_bytes(c->lr_cap, c->lr_m, n_pad, kMaxGrid));
   lowrank_carve(c, c->lr_base);
   S->n_T = P.n_T;

@@ -107,6 +107,30 @@ cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s) {
   return e;
 }
 
+}  // namespace
+
+// y = p_k(A_hat) A_hat x (x, y FP64; q is scratch; the polynomial runs in the
+// apply precision and writes through t1/t2 or the FP32 buffers).
+cudaError_t prec_op_apply(pp_ctx* c, const double* x, double* y, cudaStream_t s) {
+  VecLaunch L{c->grid_vec, c->partials, s};
+  StepParams sp;
+  sp.mode = kSpmv;
+  sp.x = x;
+  sp.y = c->q;
+  cudaError_t e = op_step(c, false, sp, nullptr, &c->sc->counters[kCntStep], s);
+  if (e != cudaSuccess) return e;
+  if (c->opt.k == 0)
+    return vec_scale_dot(L, c->n, nullptr, c->q, y, kF64, 1.0 / c->theta_bar, nullptr, nullptr, nullptr, nullptr,
+                         nullptr);
+  if (!c->mixed) return cheb_core(c, nullptr, c->q, y, 0, nullptr, nullptr, nullptr, s);
+  e = vec_convert(L, c->n, c->q, kF64, c->r32, kF32, nullptr);
+  if (e == cudaSuccess) e = cheb_core(c, nullptr, c->r32, c->z32, 0, nullptr, nullptr, nullptr, s);
+  if (e == cudaSuccess) e = vec_from32_dot(L, c->n, nullptr, c->z32, y, nullptr, nullptr, nullptr, nullptr, nullptr);
+  return e;
+}
+
+namespace {
+
 // Kernel launches of one precond() call.
 long long precond_launches(const pp_ctx* c) {
   const long long k = c->opt.k;
@@ -182,21 +206,7 @@ int check_vec_args(pp_ctx* c, const void* a, const void* b) {
 int setup_interval_and_coeffs(pp_ctx* c, cudaStream_t s) {
   double a = 0.0, b = 0.0;
   c->lr_p = 0;
-  if (c->lr_cap > 0) {
-    // Section 3.1: the Lanczos run keeps its basis; its p smallest Ritz
-    // pairs give the correction and its extreme Ritz values the interval.
-    std::vector<double> ta, tb;
-    const int rc = lowrank_lanczos(c, s, ta, tb);
-    if (rc) return rc;
-    if (c->opt.interval == PP_INTERVAL_GIVEN) {
-      a = c->opt.alpha;
-      b = c->opt.beta;
-    } else {
-      tridiag_extremes_jacobi(ta, tb, &a, &b);
-      if (!(a > 0.0)) return fail(c, PP_EBREAKDOWN, "Lanczos estimate of the smallest eigenvalue is not positive");
-      if (!(b > a)) b = a * (1.0 + 1e-12) + 1e-300;
-    }
-  } else if (c->opt.interval == PP_INTERVAL_GIVEN) {
+  if (c->opt.interval == PP_INTERVAL_GIVEN) {
     a = c->opt.alpha;
     b = c->opt.beta;
     c->lanczos_steps_done = 0;
@@ -249,13 +259,21 @@ int setup_interval_and_coeffs(pp_ctx* c, cudaStream_t s) {
     if (!(a > 0.0)) return fail(c, PP_EBREAKDOWN, "Lanczos estimate of the smallest eigenvalue is not positive");
     if (!(b > a)) b = a * (1.0 + 1e-12) + 1e-300;
   }
-  c->alpha_hat = a;
-  c->beta_hat = b;
-  c->xi = c->opt.xi >= 0.0 ? c->opt.xi : auto_xi(a, b);
-  c->rho.assign((size_t)c->opt.k + 2, 0.0);
-  if (polyprec_coeffs(a, b, c->xi, c->opt.k, &c->theta_bar, &c->delta, &c->sigma_bar, c->rho.data()) != PP_OK)
-    return fail(c, PP_EINVAL, "invalid spectral interval for the coefficients");
-  return PP_OK;
+  auto set_coeffs = [&](double lo, double hi) {
+    c->alpha_hat = lo;
+    c->beta_hat = hi;
+    c->xi = c->opt.xi >= 0.0 ? c->opt.xi : auto_xi(lo, hi);
+    c->rho.assign((size_t)c->opt.k + 2, 0.0);
+    if (polyprec_coeffs(lo, hi, c->xi, c->opt.k, &c->theta_bar, &c->delta, &c->sigma_bar, c->rho.data()) != PP_OK)
+      return fail(c, PP_EINVAL, "invalid spectral interval for the coefficients");
+    return PP_OK;
+  };
+  int rc = set_coeffs(a, b);
+  if (rc || c->lr_cap <= 0) return rc;
+  // Section 3.1: leftmost eigenvectors for the low-rank correction, found
+  // with the polynomial just built.  The interval stays: the polynomial
+  // keeps its lower end and the correction lifts the leftmost images.
+  return lowrank_lanczos(c, s);
 }
 
 void destroy_ctx_resources(pp_ctx* c) {

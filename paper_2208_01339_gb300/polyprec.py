@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("sell_C", ctypes.c_int), ("sell_sigma", ctypes.c_int), ("apply_prec", ctypes.c_int),
                 ("flexible", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("zero_guess", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("sell_variant", ctypes.c_int), ("lowrank", ctypes.c_int)]
+                ("sell_variant", ctypes.c_int), ("lowrank", ctypes.c_int),
+                ("lowrank_steps", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -67,8 +68,8 @@ class Info(ctypes.Structure):
                 ("beta_hat", ctypes.c_double), ("xi", ctypes.c_double), ("theta_bar", ctypes.c_double),
                 ("delta", ctypes.c_double), ("sigma_bar", ctypes.c_double), ("k", ctypes.c_int),
                 ("apply_prec", ctypes.c_int), ("lanczos_steps_done", ctypes.c_int), ("t_setup_ms", ctypes.c_double),
-                ("grid_blocks", ctypes.c_int), ("lowrank", ctypes.c_int), ("ritz_resid", ctypes.c_double),
-                ("ritz_min", ctypes.c_double)]
+                ("grid_blocks", ctypes.c_int), ("lowrank", ctypes.c_int),
+                ("lowrank_steps_done", ctypes.c_int), ("ritz_resid", ctypes.c_double), ("theta_min", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

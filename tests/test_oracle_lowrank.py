@@ -9,7 +9,8 @@ What fixes each result independently of the oracle's own code:
     one with the p smallest images raised by one (Section 3.1);
   * P depends on span(V) only (V -> V R) and is symmetric positive definite;
   * the work counts of Table 4 (right block): ddot = (3 + p) iter,
-    MVP = (m + 1) iter.
+    MVP = (m + 1) iter;
+  * Lanczos on p_k(A) A returns the leftmost eigenpairs of A (LAPACK).
 """
 import os
 
@@ -157,6 +158,42 @@ def test_rank_one_reduces_iterations_when_leftmost_is_isolated():
     x1, s1 = O.pcg_csr(A, b, v0=v0, lr_V=V, **common)
     assert s1["status"] == 0 and s0["status"] == 0
     assert s1["iterations"] < s0["iterations"]
-    # the same vector found by the basis-keeping Lanczos (100 steps)
-    _, s2 = O.pcg_csr(A, b, v0=v0, lanczos_steps=100, lowrank=1, **common)
+    # the same vector found by Lanczos on p_k(A) A (40 steps)
+    _, s2 = O.pcg_csr(A, b, v0=v0, lowrank_steps=40, lowrank=1, **common)
     assert s2["iterations"] <= s1["iterations"] + 1
+
+
+def test_lowrank_vectors_are_leftmost_eigenvectors():
+    """Lanczos on B = p_k(A) A finds the leftmost eigenpairs of A: B is a
+    polynomial in A (same eigenvectors) that keeps the smallest eigenvalues
+    of A smallest (Theorem 2.3).  Checked against LAPACK eigenpairs; using
+    p_k(A) alone (decreasing in lambda) would return the rightmost ones."""
+    A = I.diffusion3d(10, 2.0, seed=1)
+    vh, _ = O.jacobi_scale(A)
+    Ah = I.CSR(A.n, A.rowptr, A.col, vh)
+    D = Ah.to_dense()
+    ev, E = np.linalg.eigh(D)
+    a, b = O.lanczos(Ah, I.lanczos_start(A.n, 0), 10)
+    lo, hi = O.tridiag_extremes(a, b)
+    V, th = O.lowrank_vectors(Ah, I.lanczos_start(A.n, 0), lo, hi, 1e-3, 8, 2, 30)
+    np.testing.assert_allclose(th, ev[:2], rtol=1e-10)
+    np.testing.assert_allclose(V.T @ V, np.eye(2), atol=1e-12)
+    for i in range(2):
+        assert np.linalg.norm(D @ V[:, i] - th[i] * V[:, i]) <= 1e-9 * th[i]
+        assert abs(abs(V[:, i] @ E[:, i]) - 1.0) < 1e-10
+    # plain Lanczos with the same number of steps is far from converged
+    a2, b2, Q = O.lanczos_basis(Ah, I.lanczos_start(A.n, 0), 30)
+    t0, y0 = O.tridiag_eig(a2, b2[:-1], 0)
+    v = Q @ y0
+    assert np.linalg.norm(D @ v - t0 * v) > 1e3 * np.linalg.norm(D @ V[:, 0] - th[0] * V[:, 0])
+
+
+def test_correction_keeps_interval():
+    """The interval comes from the estimator alone; the correction adds
+    (3 + p) - 3 = p inner products per iteration and nothing else."""
+    A = I.diffusion3d(10, 2.0, seed=1)
+    b = I.rhs_normal(A.n, 1)
+    _, s0 = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), k=8, rtol=1e-10)
+    _, s1 = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), k=8, rtol=1e-10, lowrank=2, lowrank_steps=30)
+    assert (s1["alpha_hat"], s1["beta_hat"], s1["xi"]) == (s0["alpha_hat"], s0["beta_hat"], s0["xi"])
+    assert s1["status"] == 0 and s1["iterations"] <= s0["iterations"]
