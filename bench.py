@@ -7,8 +7,9 @@ set up and resident in HBM (seed scaling, SELL layout, Lanczos interval and
 coefficients done once before timing).  Default workload: 3-D 7-point
 variable-coefficient diffusion on a 192^3 grid, lognormal(0, 2)
 conductivities (seed 1), harmonic faces, N(0,1) right-hand side, FP64,
-SELL-C-sigma, k = 5 (the fastest degree of the sweep k in {5, ..., 160}),
-10 Lanczos steps, xi = clip(10 alpha/beta, 1e-6, 1e-2).
+SELL-C-sigma layout chosen by pp_autotune, k = 5 (the fastest degree of
+the sweep k in {5, ..., 160}), 60 Lanczos steps, xi = clip(10 alpha/beta,
+1e-6, 1e-2).
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -30,14 +31,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # k = 5: the fastest degree of the FP64 sweep k in {5, 10, 20, 40, 80, 160}
-    "diffusion192": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=10, fmt="sell", prec="f64"),
-    "diffusion192_f32": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=10, fmt="sell", prec="f32",
+    # k = 5: the fastest degree of the FP64 sweep k in {5, 10, 20, 40, 80, 160}; the interval from 60
+    # Lanczos steps (the fastest of the sweep 10, 30, 60, 100, 200 at k = 5)
+    "diffusion192": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=60, fmt="sell", prec="f64"),
+    "diffusion192_f32": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=60, fmt="sell", prec="f32",
                              flexible=1),
-    "diffusion192_bf16": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=10, fmt="sell", prec="bf16",
+    "diffusion192_bf16": dict(N=192, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=60, fmt="sell", prec="bf16",
                               flexible=1),
-    "diffusion128": dict(N=128, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=10, fmt="sell", prec="f64"),
-    "diffusion128_f32": dict(N=128, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=10, fmt="sell", prec="f32",
+    "diffusion128": dict(N=128, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=60, fmt="sell", prec="f64"),
+    "diffusion128_f32": dict(N=128, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=60, fmt="sell", prec="f32",
                              flexible=1),
     "poisson32": dict(N=32, sigma=0.0, seed=0, rhs="ones_noise", k=20, lanczos=10, fmt="csr", prec="f64"),
     "dfn200": dict(dfn=True, seed=2, k=40, lanczos=10, prec="f64"),
@@ -117,14 +119,16 @@ def measured_peak():
     return 6800.0, "fallback (6.8 TB/s)"
 
 
-def traffic_from_profile(workload: str, k: int, prec: str):
+def traffic_from_profile(workload: str, k: int, prec: str, layout: str):
+    """DRAM bytes per step launch from an ncu capture of the same kernel
+    sources, layout and degree (None when there is none)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         j = json.load(fh)
     e = j.get(f"{workload}/k{k}/{prec}")
-    if not e or e.get("source_sha") != source_sha():
+    if not e or e.get("source_sha") != source_sha() or e.get("layout") != layout:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -182,7 +186,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_iterations(workload: str, k: int):
+def oracle_iterations(workload: str, k: int, lanczos_steps: int):
     p = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
     if not os.path.exists(p):
         return None
@@ -190,7 +194,8 @@ def oracle_iterations(workload: str, k: int):
         table = json.load(fh)
     # the FP32/BF16 variants solve the same system; the oracle is FP64
     base = workload.replace("_f32", "").replace("_bf16", "")
-    return table.get(f"{workload}/k{k}", table.get(f"{base}/k{k}"))
+    key = f"k{k}/L{lanczos_steps}"
+    return table.get(f"{workload}/{key}", table.get(f"{base}/{key}"))
 
 
 def cpu_sample(A, b, w, k, alpha, beta, xi):
@@ -223,7 +228,7 @@ def run_reference(args, w, rank):
     a, bb = O.lanczos(A, I.lanczos_start(A.n, 0), w["lanczos"], val=vh)
     alpha, beta = O.tridiag_extremes(a, bb)
     xi = min(max(10 * alpha / beta, 1e-6), 1e-2)
-    iters = oracle_iterations(args.workload, k)
+    iters = oracle_iterations(args.workload, k, w["lanczos"])
     src = "oracle's own count (tests/golden/oracle_iterations.json)"
     if iters is None:
         iters, src = None, "unknown"
@@ -432,6 +437,8 @@ def main():
     ap.add_argument("--lowrank", type=int, default=0,
                     help="Section 3.1 low-rank correction with this many Ritz vectors (0: none)")
     ap.add_argument("--lanczos-steps", type=int, default=0, help="override the workload's Lanczos steps")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip pp_autotune (layout from --sell-C/--sell-sigma/--sell-variant or the defaults)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.batch_count:
@@ -478,9 +485,18 @@ def main():
     opts = dict(k=k, lanczos_steps=w["lanczos"], format=w["fmt"], apply_prec=w["prec"], rtol=1e-8,
                 check_every=args.check_every, use_graphs=args.graphs, flexible=w.get("flexible", 0),
                 sell_variant=args.sell_variant, sell_C=args.sell_C, sell_sigma=args.sell_sigma, lowrank=args.lowrank)
+    rp, ci, va = P.to_device_csr(A, dev)
+    tune = None
+    if not args.no_autotune and w["fmt"] == "sell":
+        # untimed setup: choose the step storage by timing every layout
+        chosen, table = P.autotune(rp, ci, va, A.n, **opts)
+        opts.update({key: chosen[key] for key in ("format", "sell_C", "sell_sigma", "sell_variant")})
+        tune = [[t["format"], t["sell_C"], t["sell_sigma"], t["sell_variant"], round(t["us_per_step"], 2)]
+                for t in table if t["status"] == 0]
     if args.k_sweep:
         return run_k_sweep(args, w, A, b, opts, dev)
-    S = P.Solver.from_host(A, device=dev, **opts)
+    S = P.Solver(rp, ci, va, A.n, **opts)
+    variant = opts.get("sell_variant", 0)
     info = S.info()
     bt = torch.as_tensor(b, device=dev)
     x = torch.zeros_like(bt)
@@ -536,14 +552,16 @@ def main():
     n_launch = sum(s["apply_launches"] for s in stats)
     bpl = bytes_per_step_launch(A.nnz, A.n, k, w["prec"])
     roof = None
+    layout = (f"SELL C={info['sell_C']} sigma={info['sell_sigma']} {'direct' if variant == 1 else 'tma'}"
+              if info["format"] == 2 else "CSR")
     if n_launch > 0 and t_apply > 0:
         avg_s = t_apply / 1e3 / n_launch
         peak, peak_src = measured_peak()
         ach = bpl / avg_s / 1e9
-        kname = (f"sell_step_{'tma_' if args.sell_variant != 1 else ''}kernel ({w['prec']}, C={info['sell_C']})"
+        kname = (f"sell_step_{'tma_' if variant != 1 else ''}kernel ({w['prec']}, C={info['sell_C']})"
                  if info["format"] == 2 else f"csr_step_kernel ({w['prec']})")
         hbm = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-               "traffic": traffic_from_profile(args.workload, k, w["prec"]), "peak_source": peak_src,
+               "traffic": traffic_from_profile(args.workload, k, w["prec"], layout), "peak_source": peak_src,
                "kernel": kname, "algorithmic_bytes_per_launch": int(bpl), "avg_launch_us": round(avg_s * 1e6, 2)}
         if w["prec"] == "f64":
             # FP64 arithmetic is scarce on GB300: the step kernel is bound by the
@@ -565,7 +583,7 @@ def main():
 
         O.build()
         t_it = cpu_sample(A, b, w, k, info["alpha_hat"], info["beta_hat"], info["xi"])
-        oi = oracle_iterations(args.workload, k)
+        oi = oracle_iterations(args.workload, k, w["lanczos"])
         its = oi if oi else statistics.median(it)
         src = "oracle's own iteration count" if oi else "the GPU iteration count"
         cpu = {"value": t_it * its, "unit": "s", "cores": 1, "kind": "oracle",
@@ -579,7 +597,10 @@ def main():
                    "sigma_ln": w["sigma"], "format": "SELL" if info["format"] == 2 else "CSR",
                    "sell_C": info["sell_C"], "lanczos_steps": w["lanczos"], "rtol": 1e-8,
                    "l2": "inputs larger than L2 (matrix >> 129 MB)" if A.nnz * 12 > 129e6 else "L2-resident inputs",
-                   "graphs": args.graphs, "sell_variant": "direct" if args.sell_variant == 1 else "tma",
+                   "graphs": args.graphs, "sell_variant": "direct" if variant == 1 else "tma",
+                   "sell_sigma": info["sell_sigma"],
+                   "autotune": ("pp_autotune: [format(1 CSR, 2 SELL), C, sigma, variant(1 direct, 2 TMA), "
+                                "us/step] " + json.dumps(tune)) if tune else "off",
                    "lowrank": args.lowrank,
                    "parallelism": f"replicas x{world}"},
         "iterations": int(statistics.median(it)), "setup_ms": round(info["t_setup_ms"], 2),

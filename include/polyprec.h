@@ -203,6 +203,38 @@ int pcg_solve(pp_ctx* ctx, const double* b, double* x, pp_stats* stats, void* st
  * PP_EUNSUPPORTED for batch contexts.  Synchronous. */
 int pp_set_lowrank(pp_ctx* ctx, const double* U, int p, long long ldu, void* stream);
 
+/* ---- autotuner of the step storage -------------------------------------- */
+
+/* One layout the autotuner tried: format (PP_FMT_CSR / PP_FMT_SELL), SELL
+ * chunk C (32, 64 or 128 rows per slice = 1, 2 or 4 rows per lane; 0 for
+ * CSR), sort window sigma (0: none), sell_variant (1 direct loads, 2
+ * TMA-staged slices), the measured device time of one fused degree step
+ * in microseconds, and PP_OK or why the layout was skipped (PP_EINVAL: it
+ * does not fit in the workspace). */
+typedef struct {
+  int format, sell_C, sell_sigma, sell_variant;
+  double us_per_step;
+  int status;
+} pp_tune_entry;
+
+/* Workspace bytes pp_autotune needs to try every layout (the largest
+ * pp_workspace_size over the candidates). */
+int pp_autotune_workspace_size(const pp_csr* A, const pp_options* opt, size_t* bytes);
+
+/* Choose the storage of the fused degree step (Algorithm 2) for A: build
+ * the seed-scaled matrix in each candidate layout (CSR; SELL-C-sigma with
+ * C in {32, 64, 128}, sigma in {none, 1024}, direct or TMA-staged loads)
+ * that fits in the workspace, time min(k, 8)-step applications of p_k in
+ * opt->apply_prec with CUDA events (one warm-up, 5 timed), and write the
+ * fastest layout into opt (format, sell_C, sell_sigma, sell_variant; the
+ * rest of opt is unchanged).  The method is unchanged by the choice.
+ * workspace: device scratch, 256-byte aligned.  entries (host, may be
+ * NULL) receives up to max_entries results in trial order; *count (may be
+ * NULL) the number of layouts tried.  PP_EINVAL if none fits.
+ * Synchronous. */
+int pp_autotune(const pp_csr* A, pp_options* opt, void* workspace, size_t ws_bytes,
+                pp_tune_entry* entries, int max_entries, int* count, void* stream);
+
 /* Context facts (host struct). */
 int pp_get_info(const pp_ctx* ctx, pp_info* info);
 

@@ -38,6 +38,7 @@ int num_sms();
 int setup_interval_and_coeffs(pp_ctx* c, cudaStream_t s);
 // y = p_k(A_hat) A_hat x on FP64 vectors (the polynomial in the apply precision)
 cudaError_t prec_op_apply(pp_ctx* c, const double* x, double* y, cudaStream_t s);
+int time_internal_apply(pp_ctx* c, int reps, cudaStream_t s, float* ms_per_apply);
 cudaError_t op_step(pp_ctx* c, bool apply_matrix, const StepParams& p, const Scalars* skip, unsigned int* counter,
                     cudaStream_t s);
 void destroy_ctx_resources(pp_ctx* c);

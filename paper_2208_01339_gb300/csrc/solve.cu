@@ -81,8 +81,9 @@ cudaError_t cheb_core(pp_ctx* c, const Scalars* skip, const void* rin, void* zou
 // z = p_k(A_hat) r on the internal FP64 vectors r, z, with (r, z) -> rz_new
 // and, for flexible CG, (q, z) -> zq.  With a low-rank correction in use
 // (Section 3.1) c = G^{-1} V^T r is formed first and z += V c, fused with
-// the inner products, follows the polynomial.
-cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s) {
+// the inner products, follows the polynomial.  ev0/ev1 (may be null) are
+// recorded around the k degree steps alone.
+cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   Scalars* sc = c->sc;
   VecLaunch L{c->grid_vec, c->partials, s};
   const double* q = c->opt.flexible ? c->q : nullptr;
@@ -93,13 +94,20 @@ cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s) {
   cudaError_t e = lr ? lowrank_coefs(c, skip, c->r, s) : cudaSuccess;
   if (e != cudaSuccess) return e;
   if (c->opt.k == 0) {
-    e = vec_scale_dot(L, c->n, skip, c->r, c->z, kF64, 1.0 / c->theta_bar, c->r, qd, rz, &sc->zq,
-                      &sc->counters[kCntVec]);
+    if (ev0) e = cudaEventRecord(ev0, s);
+    if (e == cudaSuccess)
+      e = vec_scale_dot(L, c->n, skip, c->r, c->z, kF64, 1.0 / c->theta_bar, c->r, qd, rz, &sc->zq,
+                        &sc->counters[kCntVec]);
+    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   } else if (!c->mixed) {
-    e = cheb_core(c, skip, c->r, c->z, nd, rz, qd, &sc->zq, s);
+    if (ev0) e = cudaEventRecord(ev0, s);
+    if (e == cudaSuccess) e = cheb_core(c, skip, c->r, c->z, nd, rz, qd, &sc->zq, s);
+    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   } else {
     e = vec_convert(L, c->n, c->r, kF64, c->r32, kF32, skip);
+    if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, s);
     if (e == cudaSuccess) e = cheb_core(c, skip, c->r32, c->z32, 0, nullptr, nullptr, nullptr, s);
+    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
     if (e == cudaSuccess)
       e = vec_from32_dot(L, c->n, skip, c->z32, c->z, c->r, qd, rz, &sc->zq, &sc->counters[kCntVec]);
   }
@@ -151,9 +159,7 @@ cudaError_t pcg_iteration(pp_ctx* c, cudaStream_t s, cudaEvent_t ev0, cudaEvent_
   p.dot_out0 = &sc->pq;
   cudaError_t e = op_step(c, false, p, sc, &sc->counters[kCntStep], s);
   if (e == cudaSuccess) e = vec_update_xr(L, c->n, sc, c->xh, c->r, c->p, c->q);
-  if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, s);
-  if (e == cudaSuccess) e = precond(c, sc, s);
-  if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+  if (e == cudaSuccess) e = precond(c, sc, s, ev0, ev1);
   if (e == cudaSuccess) e = vec_update_p(L, c->n, sc, c->z, c->p, 0);
   return e;
 }
@@ -289,6 +295,29 @@ void destroy_ctx_resources(pp_ctx* c) {
   c->batch = nullptr;
 }
 
+// Device time of one application of p_k on the internal vectors (r -> z,
+// in the apply precision), averaged over `reps` after one warm-up.
+int time_internal_apply(pp_ctx* c, int reps, cudaStream_t s, float* ms_per_apply) {
+  VecLaunch L{c->grid_vec, c->partials, s};
+  int rc = ensure_events(c, 2);
+  if (rc) return rc;
+  cudaError_t e = lanczos_start(L, c->n, c->n_pad, splitmix_key(c->opt.seed, 3), c->perm, c->r, &c->sc->vv,
+                                &c->sc->counters[kCntVec]);
+  if (e == cudaSuccess && c->mixed) e = vec_convert(L, c->n, c->r, kF64, c->r32, kF32, nullptr);
+  void* rin = c->mixed ? (void*)c->r32 : (void*)c->r;
+  void* zout = c->mixed ? (void*)c->z32 : (void*)c->z;
+  if (e == cudaSuccess) e = cheb_core(c, nullptr, rin, zout, 0, nullptr, nullptr, nullptr, s);
+  if (e == cudaSuccess) e = cudaEventRecord(c->events[0], s);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i) e = cheb_core(c, nullptr, rin, zout, 0, nullptr, nullptr, nullptr, s);
+  if (e == cudaSuccess) e = cudaEventRecord(c->events[1], s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c->events[1]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "timing p_k");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->events[0], c->events[1]);
+  *ms_per_apply = ms / (float)std::max(reps, 1);
+  return PP_OK;
+}
+
 }  // namespace pp
 
 // ---------------------------------------------------------------------------
@@ -396,9 +425,7 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
     if (e == cudaSuccess) e = op_step(c, false, p, nullptr, &sc->counters[kCntStep], s);
   }
   if (e == cudaSuccess) e = pcg_init(sc, c->opt.rtol, c->opt.maxit, c->opt.flexible, s);
-  if (e == cudaSuccess && !graphs) e = cudaEventRecord(ev_pair(B, 0), s);
-  if (e == cudaSuccess) e = precond(c, sc, s);
-  if (e == cudaSuccess && !graphs) e = cudaEventRecord(ev_pair(B, 1), s);
+  if (e == cudaSuccess) e = precond(c, sc, s, graphs ? nullptr : ev_pair(B, 0), graphs ? nullptr : ev_pair(B, 1));
   if (e == cudaSuccess) e = vec_update_p(L, c->n, sc, c->z, c->p, 1);
   if (e != cudaSuccess) return cuda_fail(c, e, "pcg_solve start");
 

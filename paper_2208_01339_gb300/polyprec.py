@@ -75,6 +75,14 @@ class Info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("format", ctypes.c_int), ("sell_C", ctypes.c_int), ("sell_sigma", ctypes.c_int),
+                ("sell_variant", ctypes.c_int), ("us_per_step", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nnz", ctypes.c_longlong), ("rowptr", _vp), ("col", _vp), ("val", _vp),
                 ("nrhs", ctypes.c_int)]
@@ -107,6 +115,10 @@ SIGNATURES = [
     ("pcg_solve", ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(Stats), _vp]),
     ("pp_get_info", ctypes.c_int, [_vp, ctypes.POINTER(Info)]),
     ("pp_set_lowrank", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_longlong, _vp]),
+    ("pp_autotune_workspace_size", ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Options),
+                                                  ctypes.POINTER(ctypes.c_size_t)]),
+    ("pp_autotune", ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Options), _vp, ctypes.c_size_t,
+                                   ctypes.POINTER(TuneEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp]),
     ("pp_destroy", ctypes.c_int, [_vp]),
     ("pp_last_error", ctypes.c_char_p, [_vp]),
     ("pp_schur_workspace_size", ctypes.c_int, [ctypes.POINTER(Dfn), ctypes.POINTER(Options),
@@ -228,6 +240,30 @@ def apply_csr_static(rowptr, col, val, n: int, alpha: float, beta: float, xi: fl
                                          xi, int(k), _ptr(r), _ptr(z), _stream(stream))
     _check(rc)
     return z
+
+
+FORMAT_NAME = {1: "csr", 2: "sell"}
+
+
+def autotune(rowptr, col, val, n: int, stream=None, **options):
+    """Time every storage layout of the fused degree step on this matrix
+    (pp_autotune) and return (options dict with the fastest layout, list of
+    per-layout results)."""
+    torch = _torch()
+    opts = make_options(**options)
+    csr = Csr(int(n), int(val.numel()), _ptr(rowptr), _ptr(col), _ptr(val))
+    nbytes = ctypes.c_size_t()
+    _check(lib().pp_autotune_workspace_size(ctypes.byref(csr), ctypes.byref(opts), ctypes.byref(nbytes)))
+    ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=val.device)
+    ent = (TuneEntry * 16)()
+    cnt = ctypes.c_int()
+    _check(lib().pp_autotune(ctypes.byref(csr), ctypes.byref(opts), _ptr(ws), ws.numel(), ent, 16, ctypes.byref(cnt),
+                             _stream(stream)))
+    del ws
+    chosen = dict(options)
+    chosen.update(format=FORMAT_NAME[opts.format], sell_C=opts.sell_C, sell_sigma=opts.sell_sigma,
+                  sell_variant=opts.sell_variant)
+    return chosen, [ent[i].as_dict() for i in range(cnt.value)]
 
 
 class Solver:

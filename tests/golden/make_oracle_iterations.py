@@ -1,6 +1,7 @@
 """Write tests/golden/oracle_iterations.json: PCG iteration counts of the CPU
-oracle on the benchmark workloads (FP64, Jacobi seed, 10 Lanczos steps from
-the shared start vector, xi = clip(10 alpha/beta, 1e-6, 1e-2), rtol 1e-8).
+oracle on the benchmark workloads (FP64, Jacobi seed, L Lanczos steps from
+the shared start vector, xi = clip(10 alpha/beta, 1e-6, 1e-2), rtol 1e-8),
+keyed "<workload>/k<degree>/L<steps>".
 
 Calls only oracle/ and the seeded input generators.  The reference arm of
 bench.py multiplies its timed per-iteration oracle work by these counts.
@@ -19,7 +20,7 @@ sys.path.insert(0, ROOT)
 import oracle as O  # noqa: E402
 from paper_2208_01339_gb300 import inputs as I  # noqa: E402
 
-CASES = [("poisson32", 20), ("diffusion192", 5), ("diffusion192", 20)]
+CASES = [("poisson32", 20, 10), ("diffusion192", 5, 10), ("diffusion192", 20, 10), ("diffusion192", 5, 60)]
 
 
 def problem(name):
@@ -36,13 +37,13 @@ def main():
     if os.path.exists(out_path):
         with open(out_path) as fh:
             res = json.load(fh)
-    for name, k in CASES:
-        key = f"{name}/k{k}"
+    for name, k, steps in CASES:
+        key = f"{name}/k{k}/L{steps}"
         if key in res:
             continue
         A, b = problem(name)
         t0 = time.perf_counter()
-        _, st = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), k=k, lanczos_steps=10, rtol=1e-8)
+        _, st = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), k=k, lanczos_steps=steps, rtol=1e-8)
         res[key] = st["iterations"]
         print(key, st["iterations"], st["status"], f"{time.perf_counter() - t0:.1f}s", flush=True)
         with open(out_path, "w") as fh:

@@ -49,6 +49,7 @@ def test_struct_layouts_match_c(tmp_path):
         "pp_info": [f for f, _ in P.Info._fields_],
         "pp_dfn": [f for f, _ in P.Dfn._fields_],
         "pp_batch_item": [f for f, _ in P.BatchItem._fields_],
+        "pp_tune_entry": [f for f, _ in P.TuneEntry._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for st, fs in fields.items():
@@ -62,7 +63,7 @@ def test_struct_layouts_match_c(tmp_path):
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
     c = {k: int(v) for k, v in (ln.split() for ln in out if ln.strip())}
     for st, cls in (("pp_csr", P.Csr), ("pp_options", P.Options), ("pp_stats", P.Stats), ("pp_info", P.Info),
-                    ("pp_dfn", P.Dfn), ("pp_batch_item", P.BatchItem)):
+                    ("pp_dfn", P.Dfn), ("pp_batch_item", P.BatchItem), ("pp_tune_entry", P.TuneEntry)):
         assert c[st] == ctypes.sizeof(cls), st
         for f, _ in cls._fields_:
             assert c[f"{st}.{f}"] == getattr(cls, f).offset, f"{st}.{f}"
@@ -107,4 +108,8 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.pcg_solve(None, None, None, None, None) == P.PP_EINVAL
     assert lib.polyprec_apply(None, None, None, 1, None) == P.PP_EINVAL
     assert lib.pp_destroy(None) == P.PP_OK
+    assert lib.pp_autotune(None, None, None, 0, None, 0, None, None) == P.PP_EINVAL
+    assert lib.pp_autotune(ctypes.byref(csr), ctypes.byref(o), ctypes.c_void_p(8), 1 << 20, None, 0, None,
+                           None) == P.PP_EINVAL  # unaligned workspace
+    assert lib.pp_set_lowrank(None, None, 0, 0, None) == P.PP_EINVAL
     assert b"NULL" in lib.pp_last_error(None)
