@@ -70,18 +70,21 @@ def build_problem(w):
     return A, b
 
 
-def bytes_per_step_launch(nnz: int, n: int, k: int, prec: str) -> float:
+def bytes_per_step_launch(nnz: int, n: int, k: int, prec: str, ndiag: int = 0) -> float:
     """Algorithmic bytes of one fused degree step, averaged over the k steps
-    of one application: every step streams the matrix once (value + int32
-    column index per nonzero) and touches n-vectors: step 1 reads r and
-    writes y (2), step 2 reads x, r and writes y (3; x_old = r/theta is not
-    stored), steps 3..k read x, x_old, r and write y (4).  Gathered x
-    entries are counted once (L2 reuse); padding is excluded."""
+    of one application: every step streams the matrix once -- value + int32
+    column index per nonzero (CSR, SELL), or the ndiag stored diagonals of n
+    values each (symmetric DIA: main and upper diagonals, no indices) -- and
+    touches n-vectors: step 1 reads r and writes y (2), step 2 reads x, r
+    and writes y (3; x_old = r/theta is not stored), steps 3..k read x,
+    x_old, r and write y (4).  Gathered x entries and the lower-triangle
+    rereads of DIA are counted once (L2 reuse); padding is excluded."""
     sa, sv = VAL_BYTES[prec], VEC_BYTES[prec]
     if k <= 0:
         return 0.0
     vec_passes = 2 if k == 1 else 2 + 3 + 4 * (k - 2)
-    return (k * nnz * (sa + 4) + n * sv * vec_passes) / k
+    mat = ndiag * n * sa if ndiag else nnz * (sa + 4)
+    return (k * mat + n * sv * vec_passes) / k
 
 
 def flops_per_step_launch(nnz: int, n: int, k: int) -> float:
@@ -550,16 +553,18 @@ def main():
     it = [s["iterations"] for s in stats]
     t_apply = sum(s["t_apply_ms"] for s in stats)
     n_launch = sum(s["apply_launches"] for s in stats)
-    bpl = bytes_per_step_launch(A.nnz, A.n, k, w["prec"])
+    bpl = bytes_per_step_launch(A.nnz, A.n, k, w["prec"], info["ndiag"] if info["format"] == 3 else 0)
     roof = None
+    fmt_name = {1: "CSR", 2: "SELL", 3: "DIA"}[info["format"]]
     layout = (f"SELL C={info['sell_C']} sigma={info['sell_sigma']} {'direct' if variant == 1 else 'tma'}"
-              if info["format"] == 2 else "CSR")
+              if info["format"] == 2 else (f"DIA ndiag={info['ndiag']}" if info["format"] == 3 else "CSR"))
     if n_launch > 0 and t_apply > 0:
         avg_s = t_apply / 1e3 / n_launch
         peak, peak_src = measured_peak()
         ach = bpl / avg_s / 1e9
-        kname = (f"sell_step_{'tma_' if variant != 1 else ''}kernel ({w['prec']}, C={info['sell_C']})"
-                 if info["format"] == 2 else f"csr_step_kernel ({w['prec']})")
+        kname = {2: f"sell_step_{'tma_' if variant != 1 else ''}kernel ({w['prec']}, C={info['sell_C']})",
+                 3: f"dia_step_kernel ({w['prec']}, {info['ndiag']} stored diagonals)",
+                 1: f"csr_step_kernel ({w['prec']})"}[info["format"]]
         hbm = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                "traffic": traffic_from_profile(args.workload, k, w["prec"], layout), "peak_source": peak_src,
                "kernel": kname, "algorithmic_bytes_per_launch": int(bpl), "avg_launch_us": round(avg_s * 1e6, 2)}
@@ -594,12 +599,11 @@ def main():
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": w["prec"], "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w['N']}^3", "n": A.n, "nnz": A.nnz, "k": k,
-                   "sigma_ln": w["sigma"], "format": "SELL" if info["format"] == 2 else "CSR",
-                   "sell_C": info["sell_C"], "lanczos_steps": w["lanczos"], "rtol": 1e-8,
+                   "sigma_ln": w["sigma"], "format": fmt_name,
+                   "lanczos_steps": w["lanczos"], "rtol": 1e-8,
                    "l2": "inputs larger than L2 (matrix >> 129 MB)" if A.nnz * 12 > 129e6 else "L2-resident inputs",
-                   "graphs": args.graphs, "sell_variant": "direct" if variant == 1 else "tma",
-                   "sell_sigma": info["sell_sigma"],
-                   "autotune": ("pp_autotune: [format(1 CSR, 2 SELL), C, sigma, variant(1 direct, 2 TMA), "
+                   "graphs": args.graphs, "layout": layout,
+                   "autotune": ("pp_autotune: [format(1 CSR, 2 SELL, 3 DIA), C, sigma, variant(1 direct, 2 TMA), "
                                 "us/step] " + json.dumps(tune)) if tune else "off",
                    "lowrank": args.lowrank,
                    "parallelism": f"replicas x{world}"},

@@ -60,6 +60,10 @@ extern "C" {
 #define PP_FMT_AUTO 0
 #define PP_FMT_CSR 1          /* CSR kernel (row groups of lanes)              */
 #define PP_FMT_SELL 2         /* SELL-C-sigma kernel (warp per slice)          */
+#define PP_FMT_DIA 3          /* symmetric diagonal storage without column
+                                 indices (banded / structured-grid matrices with
+                                 at most 16 distinct upper offsets and
+                                 symmetric values); PP_EUNSUPPORTED otherwise */
 #define PP_PREC_F64 0         /* p_k applied in FP64                           */
 #define PP_PREC_F32 1         /* p_k applied with FP32 values and vectors      */
 #define PP_PREC_BF16 2        /* p_k applied with BF16 values, FP32 vectors    */
@@ -130,13 +134,14 @@ typedef struct {
 
 typedef struct {
   int n;              /* operator size                                     */
-  int format;         /* PP_FMT_CSR / PP_FMT_SELL actually used            */
+  int format;         /* PP_FMT_CSR / PP_FMT_SELL / PP_FMT_DIA actually used */
   int sell_C, sell_sigma;
   long long nnz, nnz_padded;
   double alpha_hat, beta_hat, xi, theta_bar, delta, sigma_bar;
   int k, apply_prec, lanczos_steps_done;
   double t_setup_ms;
   int grid_blocks;    /* blocks of the persistent step kernels             */
+  int ndiag;          /* DIA: stored diagonals (main + upper); else 0      */
   int lowrank;        /* vectors of the low-rank correction in use         */
   int lowrank_steps_done; /* Lanczos steps run for them at setup           */
   double ritz_resid;  /* max over them of ||A_hat v - theta v|| / theta,
@@ -205,12 +210,12 @@ int pp_set_lowrank(pp_ctx* ctx, const double* U, int p, long long ldu, void* str
 
 /* ---- autotuner of the step storage -------------------------------------- */
 
-/* One layout the autotuner tried: format (PP_FMT_CSR / PP_FMT_SELL), SELL
+/* One layout the autotuner tried: format (PP_FMT_CSR / _SELL / _DIA), SELL
  * chunk C (32, 64 or 128 rows per slice = 1, 2 or 4 rows per lane; 0 for
  * CSR), sort window sigma (0: none), sell_variant (1 direct loads, 2
  * TMA-staged slices), the measured device time of one fused degree step
  * in microseconds, and PP_OK or why the layout was skipped (PP_EINVAL: it
- * does not fit in the workspace). */
+ * does not fit in the workspace; PP_EUNSUPPORTED: DIA does not apply). */
 typedef struct {
   int format, sell_C, sell_sigma, sell_variant;
   double us_per_step;
@@ -222,9 +227,9 @@ typedef struct {
 int pp_autotune_workspace_size(const pp_csr* A, const pp_options* opt, size_t* bytes);
 
 /* Choose the storage of the fused degree step (Algorithm 2) for A: build
- * the seed-scaled matrix in each candidate layout (CSR; SELL-C-sigma with
- * C in {32, 64, 128}, sigma in {none, 1024}, direct or TMA-staged loads)
- * that fits in the workspace, time min(k, 8)-step applications of p_k in
+ * the seed-scaled matrix in each candidate layout (CSR; DIA when the matrix
+ * is symmetric-banded; SELL-C-sigma with C in {32, 64, 128}, sigma in
+ * {none, 1024}, direct or TMA-staged loads) that fits in the workspace, time min(k, 8)-step applications of p_k in
  * opt->apply_prec with CUDA events (one warm-up, 5 timed), and write the
  * fastest layout into opt (format, sell_C, sell_sigma, sell_variant; the
  * rest of opt is unchanged).  The method is unchanged by the choice.

@@ -143,7 +143,7 @@ int validate_options(pp_ctx* c, const pp_options* o) {
     return fail(c, PP_EUNSUPPORTED, "apply_prec not supported");
   if (o->seed_scaling != PP_SEED_NONE && o->seed_scaling != PP_SEED_JACOBI)
     return fail(c, PP_EINVAL, "seed_scaling must be PP_SEED_NONE or PP_SEED_JACOBI");
-  if (o->format < PP_FMT_AUTO || o->format > PP_FMT_SELL) return fail(c, PP_EUNSUPPORTED, "format not supported");
+  if (o->format < PP_FMT_AUTO || o->format > PP_FMT_DIA) return fail(c, PP_EUNSUPPORTED, "format not supported");
   if (!(o->rtol >= 0.0)) return fail(c, PP_EINVAL, "rtol must be >= 0");
   if (o->check_every < 0 || o->check_every > kMaxCheck) return fail(c, PP_EINVAL, "check_every must be in [0, 64]");
   if (o->sell_sigma < 0) return fail(c, PP_EINVAL, "sell_sigma must be >= 0");
@@ -217,12 +217,67 @@ SellPlan plan_sell(const std::vector<int>& rowptr, int n, int C, int sigma) {
 }
 
 int choose_format(const pp_options& o, int n) {
-  if (o.format == PP_FMT_CSR || o.format == PP_FMT_SELL) return o.format;
+  if (o.format == PP_FMT_CSR || o.format == PP_FMT_SELL || o.format == PP_FMT_DIA) return o.format;
   return n < 262144 ? PP_FMT_CSR : PP_FMT_SELL;
 }
 
 int choose_C(const pp_options& o) {
   return (o.sell_C == 32 || o.sell_C == 64 || o.sell_C == 128) ? o.sell_C : 64;
+}
+
+struct DiaPlan {
+  int nd = 0;
+  int doff[kMaxDiag] = {0};
+  long long dpad = 0;
+};
+
+// Symmetric diagonal storage applies when every row has its diagonal entry,
+// no entry is repeated, the entries lie on at most kMaxDiag upper offsets
+// (and their mirrors) and a(j, i) == a(i, j) exactly.  Reads the column
+// indices and values to the host (synchronous).
+int plan_dia(const pp_csr* A, const std::vector<int>& rp, DiaPlan& P, cudaStream_t s, pp_ctx* c) {
+  const long long nnz = A->nnz;
+  std::vector<int> col((size_t)std::max<long long>(nnz, 1));
+  std::vector<double> val((size_t)std::max<long long>(nnz, 1));
+  cudaError_t e = cudaMemcpyAsync(col.data(), A->col, sizeof(int) * nnz, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(val.data(), A->val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reading the matrix for DIA planning");
+  std::vector<long long> offs;
+  const int n = A->n;
+  for (int i = 0; i < n; ++i) {
+    bool diag = false;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = col[p];
+      if (j < 0 || j >= n) return fail(c, PP_EINVAL, "column index out of range");
+      for (int q = rp[i]; q < p; ++q)
+        if (col[q] == j) return fail(c, PP_EUNSUPPORTED, "DIA: repeated entry in a row");
+      const long long d = (long long)j - i;
+      if (d == 0) diag = true;
+      if (d < 0) {  // mirror entry a(j, i) must exist with the same value
+        bool found = false;
+        for (int q = rp[j]; q < rp[j + 1]; ++q)
+          if (col[q] == i) {
+            found = val[q] == val[p];
+            break;
+          }
+        if (!found) return fail(c, PP_EUNSUPPORTED, "DIA: the matrix is not symmetric");
+        continue;
+      }
+      if (std::find(offs.begin(), offs.end(), d) == offs.end()) {
+        if ((int)offs.size() == kMaxDiag) return fail(c, PP_EUNSUPPORTED, "DIA: more than 16 upper diagonals");
+        offs.push_back(d);
+      }
+    }
+    if (!diag) return fail(c, PP_EUNSUPPORTED, "DIA: a row has no diagonal entry");
+  }
+  std::sort(offs.begin(), offs.end());
+  if (offs.empty() || offs[0] != 0 || offs.back() > 0x7fffffffLL)
+    return fail(c, PP_EUNSUPPORTED, "DIA: unsupported diagonal offsets");
+  P.nd = (int)offs.size();
+  for (int t = 0; t < P.nd; ++t) P.doff[t] = (int)offs[t];
+  P.dpad = (offs.back() + 31) / 32 * 32;
+  return PP_OK;
 }
 
 int read_rowptr(const pp_csr* A, std::vector<int>& h, cudaStream_t s, pp_ctx* c) {
@@ -244,12 +299,19 @@ int check_csr(const pp_csr* A, pp_ctx* c) {
   return PP_OK;
 }
 
-void init_desc(pp_ctx* c, const pp_csr* A, const SellPlan& P) {
+void init_desc(pp_ctx* c, const pp_csr* A, const SellPlan& P, const DiaPlan& D) {
   c->A64 = MatDesc{};
   c->A64.format = choose_format(c->opt, A->n);
   c->A64.n = A->n;
   c->A64.prec = kF64;
-  if (c->A64.format == PP_FMT_SELL) {
+  if (c->A64.format == PP_FMT_DIA) {
+    c->n_pad = ((long long)A->n + 127) / 128 * 128;
+    c->A64.ndiag = D.nd;
+    for (int t = 0; t < kMaxDiag; ++t) c->A64.doff[t] = t < D.nd ? D.doff[t] : 0;
+    c->A64.dpad = D.dpad;
+    c->A64.dstride = D.dpad + c->n_pad;
+    c->nnz_pad = (long long)D.nd * c->A64.dstride;
+  } else if (c->A64.format == PP_FMT_SELL) {
     c->A64.C = P.C;
     c->A64.nslices = P.nslices;
     c->A64.tma = c->opt.sell_variant != 1;
@@ -274,7 +336,10 @@ size_t layout(pp_ctx* c, void* base, const SellPlan& P) {
   c->sc = B.take<Scalars>(1);
   c->partials = B.take<double>(2LL * kMaxGrid);
   c->w = B.take<double>(n_pad);
-  if (c->A64.format == PP_FMT_SELL) {
+  if (c->A64.format == PP_FMT_DIA) {
+    c->A64.val = B.take<double>(c->nnz_pad);
+    c->perm = c->iperm = nullptr;
+  } else if (c->A64.format == PP_FMT_SELL) {
     c->A64.slice_ptr = B.take<long long>(P.nslices + 1);
     c->A64.col = B.take<int>(P.nnz_pad);
     c->A64.val = B.take<double>(P.nnz_pad);
@@ -323,12 +388,15 @@ extern "C" int pp_workspace_size(const pp_csr* A, const pp_options* opt, size_t*
   if (!bytes) return fail(nullptr, PP_EINVAL, "bytes is NULL");
   tmp.opt = *opt;
   SellPlan P;
-  if (choose_format(*opt, A->n) == PP_FMT_SELL) {
+  DiaPlan D;
+  const int fmt = choose_format(*opt, A->n);
+  if (fmt == PP_FMT_SELL || fmt == PP_FMT_DIA) {
     std::vector<int> h;
     if ((rc = read_rowptr(A, h, nullptr, &tmp))) return rc;
-    P = plan_sell(h, A->n, choose_C(*opt), opt->sell_sigma);
+    if (fmt == PP_FMT_SELL) P = plan_sell(h, A->n, choose_C(*opt), opt->sell_sigma);
+    if (fmt == PP_FMT_DIA && (rc = plan_dia(A, h, D, nullptr, &tmp))) return rc;
   }
-  init_desc(&tmp, A, P);
+  init_desc(&tmp, A, P, D);
   *bytes = layout(&tmp, nullptr, P);
   return PP_OK;
 }
@@ -360,8 +428,10 @@ extern "C" int pcg_setup(pp_ctx** out, const pp_csr* A, const pp_options* opt, v
   std::vector<int> h;
   if ((rc = read_rowptr(A, h, s, c))) return bail(rc);
   SellPlan P;
+  DiaPlan D;
   if (choose_format(*opt, A->n) == PP_FMT_SELL) P = plan_sell(h, A->n, choose_C(*opt), opt->sell_sigma);
-  init_desc(c, A, P);
+  if (choose_format(*opt, A->n) == PP_FMT_DIA && (rc = plan_dia(A, h, D, s, c))) return bail(rc);
+  init_desc(c, A, P, D);
   const size_t need = layout(c, nullptr, P);
   if (ws_bytes < need) return bail(fail(c, PP_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes"));
   layout(c, ws, P);
@@ -392,7 +462,11 @@ extern "C" int pcg_setup(pp_ctx** out, const pp_csr* A, const pp_options* opt, v
       return bail(fail(c, PP_EINVAL, "non-positive diagonal at row " + std::to_string(bad) + " (Jacobi seed)"));
   }
 
-  if (c->A64.format == PP_FMT_SELL) {
+  if (c->A64.format == PP_FMT_DIA) {
+    e = cudaMemsetAsync(const_cast<void*>(c->A64.val), 0, sizeof(double) * (size_t)c->nnz_pad, s);
+    if (e == cudaSuccess) e = dia_fill(c->A64, A->rowptr, A->col, A->val, w_orig, s);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "building the DIA matrix"));
+  } else if (c->A64.format == PP_FMT_SELL) {
     e = cudaMemcpyAsync((void*)c->A64.slice_ptr, P.sptr.data(), sizeof(long long) * P.sptr.size(),
                         cudaMemcpyHostToDevice, s);
     std::vector<int> ip;
@@ -422,7 +496,9 @@ extern "C" int pcg_setup(pp_ctx** out, const pp_csr* A, const pp_options* opt, v
   }
   {
     const int mb = step_max_blocks_per_sm(c->A64, kChebK, 0);
-    const long long work = c->A64.format == PP_FMT_SELL ? c->A64.nslices * 32 : (long long)A->n * c->A64.csr_group;
+    const long long work = c->A64.format == PP_FMT_SELL  ? c->A64.nslices * 32
+                           : c->A64.format == PP_FMT_DIA ? (long long)A->n
+                                                         : (long long)A->n * c->A64.csr_group;
     const long long want = (work + kBlock - 1) / kBlock;
     c->grid_step = (int)std::max(1LL, std::min<long long>(std::min(kMaxGrid, c->num_sms * mb), want));
   }
@@ -460,6 +536,7 @@ extern "C" int pp_get_info(const pp_ctx* c, pp_info* info) {
   info->lanczos_steps_done = c->lanczos_steps_done;
   info->t_setup_ms = c->t_setup_ms;
   info->grid_blocks = c->grid_step;
+  info->ndiag = c->A64.format == PP_FMT_DIA ? c->A64.ndiag : 0;
   info->lowrank = c->lr_p;
   info->ritz_resid = c->lr_ritz_resid;
   info->lowrank_steps_done = c->lr_steps_done;

@@ -26,8 +26,10 @@ enum Prec { kF64 = 0, kF32 = 1, kBF16 = 2 };
 //   kSpmv: (x, y)   kResid: (y, y), (r, r)   kCheb*: (r, y), (aux, y)   kLanczos: (y, x)
 enum StepMode { kSpmv = 0, kResid = 1, kCheb1 = 2, kCheb2 = 3, kChebK = 4, kLanczos = 5 };
 
+constexpr int kMaxDiag = 16;  // stored diagonals of the symmetric DIA format
+
 struct MatDesc {
-  int format;  // 1 CSR, 2 SELL
+  int format;  // 1 CSR, 2 SELL, 3 DIA
   int n;
   long long n_pad;
   // SELL-C-sigma: slice s holds rows [s*C, (s+1)*C), C = 32*VW; entry j of
@@ -41,6 +43,14 @@ struct MatDesc {
   int csr_group;         // CSR: lanes per row (1, 8, 32)
   int prec;
   int tma;               // SELL: stage slices through shared memory with cp.async.bulk
+  // DIA (symmetric; rows in natural order): the main diagonal and the upper
+  // diagonals t = 0..ndiag-1 at offsets doff[t] (doff[0] = 0).  Entry
+  // (i, i + doff[t]) sits at val[t * dstride + dpad + i]; positions
+  // -dpad..-1 and entries outside the matrix hold 0.  Row i takes its lower
+  // entries (i, i - doff[t]) from val[t * dstride + dpad + i - doff[t]].
+  int ndiag;
+  int doff[kMaxDiag];
+  long long dstride, dpad;
 };
 
 // Folded coefficients of degree step j of Algorithm 2 (j >= 1): with
@@ -132,5 +142,13 @@ cudaError_t sell_fill(const MatDesc& dst, const int* perm, const int* iperm, con
 cudaError_t csr_fill(int n, const int* rowptr, const int* col, const double* val, const double* w, int* out_rowptr,
                      int* out_col, void* out_val, int out_prec, long long nnz, cudaStream_t s);
 cudaError_t sell_convert_values(long long nnz_pad, const double* in, void* out, int out_prec, cudaStream_t s);
+// DIA fill from CSR (entries with col >= row): val[t * dstride + dpad + row] = w_row a w_col (w may be null).
+cudaError_t dia_fill(const MatDesc& dst, const int* rowptr, const int* col, const double* val, const double* w,
+                     cudaStream_t s);
+
+// DIA step kernels (step_dia.cu).
+cudaError_t launch_step_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, double* partials,
+                            unsigned int* counter, int grid, cudaStream_t s);
+int step_blocks_per_sm_dia(const MatDesc& A);
 
 }  // namespace pp

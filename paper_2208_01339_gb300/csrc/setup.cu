@@ -85,6 +85,31 @@ __global__ void csr_fill_kernel(int n, const int* __restrict__ rowptr, const int
   }
 }
 
+struct DiaFillArgs {
+  int nd;
+  int doff[kMaxDiag];
+  long long dstride, dpad;
+};
+
+// One thread per row: entries with col >= row go to their diagonal.
+__global__ void dia_fill_kernel(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ w, DiaFillArgs d,
+                                double* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double wi = w ? w[i] : 1.0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int c = col[p];
+      const long long off = (long long)c - i;
+      if (off < 0) continue;
+      for (int t = 0; t < d.nd; ++t)
+        if (d.doff[t] == off) {
+          out[(long long)t * d.dstride + d.dpad + i] = w ? (wi * val[p]) * w[c] : val[p];
+          break;
+        }
+    }
+  }
+}
+
 template <typename TV>
 __global__ void convert_values_kernel(long long m, const double* __restrict__ in, TV* __restrict__ out) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
@@ -133,6 +158,17 @@ cudaError_t csr_fill(int n, const int* rowptr, const int* col, const double* val
   else
     csr_fill_kernel<__nv_bfloat16><<<g, kBlock, 0, s>>>(n, rowptr, col, val, w, out_rowptr, out_col,
                                                         (__nv_bfloat16*)out_val);
+  return cudaGetLastError();
+}
+
+cudaError_t dia_fill(const MatDesc& dst, const int* rowptr, const int* col, const double* val, const double* w,
+                     cudaStream_t s) {
+  DiaFillArgs d;
+  d.nd = dst.ndiag;
+  for (int t = 0; t < kMaxDiag; ++t) d.doff[t] = t < dst.ndiag ? dst.doff[t] : -1;
+  d.dstride = dst.dstride;
+  d.dpad = dst.dpad;
+  dia_fill_kernel<<<grid_for(dst.n), kBlock, 0, s>>>(dst.n, rowptr, col, val, w, d, (double*)const_cast<void*>(dst.val));
   return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@ cudaError_t launch_step(const MatDesc& A, const StepParams& p, const Scalars* sc
                         unsigned int* counter, int grid, cudaStream_t s) {
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   if (p.ndot == 2 && p.mode != kResid && p.aux == nullptr) return cudaErrorInvalidValue;
+  if (A.format == 3) return launch_step_dia(A, p, sc, partials, counter, grid, s);
   if (A.prec == kF64) return launch_step_f64(A, p, sc, partials, counter, grid, s);
   return launch_step_lp(A, p, sc, partials, counter, grid, s);
 }
@@ -21,6 +22,7 @@ cudaError_t launch_step(const MatDesc& A, const StepParams& p, const Scalars* sc
 int step_max_blocks_per_sm(const MatDesc& A, int mode, int ndot) {
   (void)mode;
   (void)ndot;
+  if (A.format == 3) return step_blocks_per_sm_dia(A);
   return step_blocks_per_sm_f64(A);
 }
 

@@ -1,0 +1,145 @@
+// Fused degree-step kernels on the symmetric diagonal (DIA) storage: the
+// same modes and fused inner products as the SELL/CSR kernels
+// (step_impl.cuh), for matrices whose nonzeros lie on a few diagonals --
+// the 7-point stencil of a structured 3-D grid has 4 stored diagonals
+// (offsets 0, 1, N, N^2).  No column indices are stored, and of each pair
+// of symmetric off-diagonals only the upper one: row i reads its upper
+// entries at position i of each diagonal and its lower entries at position
+// i - offset, which another thread of the same sweep has just read, so the
+// second read is served by L2.  One row per thread, consecutive rows on
+// consecutive lanes: every stream is coalesced.
+#include "step_impl.cuh"
+
+namespace pp {
+namespace {
+
+struct DiaArgs {
+  int nd;
+  int doff[kMaxDiag];
+  long long dstride, dpad, n_pad;
+};
+
+template <typename TV, typename TX>
+__device__ __forceinline__ TX ldv(const TV* p) {
+  if constexpr (std::is_same<TV, __nv_bfloat16>::value) {
+    const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(p));
+    return (TX)__uint_as_float(((unsigned int)u) << 16);
+  } else {
+    return (TX)__ldg(p);
+  }
+}
+
+// ND > 0: that many stored diagonals, unrolled; ND = 0: d.nd at run time.
+template <typename TV, typename TX, int ND, int MODE, int NDOT>
+__global__ void __launch_bounds__(kBlock) dia_step_kernel(int n, DiaArgs d, const TV* __restrict__ val,
+                                                          StepArgs<TX> a, const Scalars* sc, double* partials,
+                                                          unsigned int* counter) {
+  if (sc && load_done(sc)) return;
+  double dot[NDOT > 0 ? NDOT : 1];
+#pragma unroll
+  for (int i = 0; i < (NDOT > 0 ? NDOT : 1); ++i) dot[i] = 0.0;
+  const TX lan = lanczos_coef<TX, MODE>(a);
+  const int nd = ND > 0 ? ND : d.nd;
+  const long long last = d.n_pad - 1;
+  const TV* base = val + d.dpad;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TX xs = __ldg(a.x + i);
+    TX acc = ldv<TV, TX>(base + i) * xs;
+#pragma unroll
+    for (int t = 1; t < (ND > 0 ? ND : kMaxDiag); ++t) {
+      if (ND == 0 && t >= nd) break;
+      const long long o = d.doff[t];
+      const TV* vt = base + (long long)t * d.dstride;
+      const TX up = ldv<TV, TX>(vt + i);      // a(i, i + o); 0 past the last row
+      const TX lo = ldv<TV, TX>(vt + i - o);  // a(i - o, i) = a(i, i - o); 0 in the front pad
+      const long long ju = i + o < last ? i + o : last;
+      const long long jl = i - o > 0 ? i - o : 0;
+      acc = fma(up, __ldg(a.x + ju), acc);
+      acc = fma(lo, __ldg(a.x + jl), acc);
+    }
+    TX rs = (TX)0, xo = (TX)0;
+    if constexpr (mode_needs_r<MODE>()) rs = a.r[i];
+    if constexpr (mode_needs_xold<MODE>()) {
+      if (MODE == kChebK || a.xold) xo = a.xold[i];
+    }
+    const TX y = row_value<TX, MODE>(a, acc, xs, rs, xo, lan);
+    a.y[i] = y;
+    row_dots<TX, MODE, NDOT>(a, i, y, xs, rs, dot);
+  }
+  finish_dots<TX, NDOT>(a, dot, partials, counter);
+}
+
+DiaArgs dia_args(const MatDesc& A) {
+  DiaArgs d;
+  d.nd = A.ndiag;
+  for (int t = 0; t < kMaxDiag; ++t) d.doff[t] = t < A.ndiag ? A.doff[t] : 0;
+  d.dstride = A.dstride;
+  d.dpad = A.dpad;
+  d.n_pad = A.n_pad;
+  return d;
+}
+
+template <typename TV, typename TX, int MODE, int NDOT>
+cudaError_t go_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, double* partials, unsigned int* cnt,
+                   int grid, cudaStream_t s) {
+  if constexpr (!step_variant_used<TX, MODE, NDOT>()) {
+    return cudaErrorNotSupported;
+  } else {
+    const TV* v = static_cast<const TV*>(A.val);
+    if (A.ndiag == 4)
+      dia_step_kernel<TV, TX, 4, MODE, NDOT><<<grid, kBlock, 0, s>>>(A.n, dia_args(A), v, make_args<TX>(p), sc,
+                                                                     partials, cnt);
+    else
+      dia_step_kernel<TV, TX, 0, MODE, NDOT><<<grid, kBlock, 0, s>>>(A.n, dia_args(A), v, make_args<TX>(p), sc,
+                                                                     partials, cnt);
+    return cudaGetLastError();
+  }
+}
+
+template <typename TV, typename TX, int MODE>
+cudaError_t dia_ndot(const MatDesc& A, const StepParams& p, const Scalars* sc, double* partials, unsigned int* cnt,
+                     int grid, cudaStream_t s) {
+  switch (p.ndot) {
+    case 0: return go_dia<TV, TX, MODE, 0>(A, p, sc, partials, cnt, grid, s);
+    case 1: return go_dia<TV, TX, MODE, 1>(A, p, sc, partials, cnt, grid, s);
+    case 2: return go_dia<TV, TX, MODE, 2>(A, p, sc, partials, cnt, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename TV, typename TX>
+cudaError_t dia_mode(const MatDesc& A, const StepParams& p, const Scalars* sc, double* partials, unsigned int* cnt,
+                     int grid, cudaStream_t s) {
+  switch (p.mode) {
+    case kSpmv: return dia_ndot<TV, TX, kSpmv>(A, p, sc, partials, cnt, grid, s);
+    case kResid: return dia_ndot<TV, TX, kResid>(A, p, sc, partials, cnt, grid, s);
+    case kCheb1: return dia_ndot<TV, TX, kCheb1>(A, p, sc, partials, cnt, grid, s);
+    case kCheb2: return dia_ndot<TV, TX, kCheb2>(A, p, sc, partials, cnt, grid, s);
+    case kChebK: return dia_ndot<TV, TX, kChebK>(A, p, sc, partials, cnt, grid, s);
+    case kLanczos: return dia_ndot<TV, TX, kLanczos>(A, p, sc, partials, cnt, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_step_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, double* partials,
+                            unsigned int* counter, int grid, cudaStream_t s) {
+  if (A.ndiag < 1 || A.ndiag > kMaxDiag) return cudaErrorInvalidValue;
+  if (A.prec == kF64) return dia_mode<double, double>(A, p, sc, partials, counter, grid, s);
+  if (A.prec == kF32) return dia_mode<float, float>(A, p, sc, partials, counter, grid, s);
+  return dia_mode<__nv_bfloat16, float>(A, p, sc, partials, counter, grid, s);
+}
+
+int step_blocks_per_sm_dia(const MatDesc& A) {
+  int nb = 0;
+  cudaError_t e;
+  if (A.ndiag == 4)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 4, kChebK, 0>, kBlock, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 0, kChebK, 0>, kBlock, 0);
+  return (e == cudaSuccess && nb > 0) ? nb : 2;
+}
+
+}  // namespace pp

@@ -1,9 +1,10 @@
 // Autotuner of the storage of the fused degree step: it builds the matrix
-// in every candidate layout that fits in the caller's workspace (CSR, and
-// SELL-C-sigma with C = 32, 64, 128 rows per slice -- 1, 2 or 4 rows per
-// lane -- and sort windows sigma = C or 1024, with direct loads or
-// TMA-staged slices), times applications of p_k on it with CUDA events
-// and reports the fastest.  Nothing of the method changes: every layout
+// in every candidate layout that applies and fits in the caller's
+// workspace (CSR; symmetric DIA for banded matrices; SELL-C-sigma with
+// C = 32, 64, 128 rows per slice -- 1, 2 or 4 rows per lane -- and sort
+// windows sigma = C or 1024, with direct loads or TMA-staged slices),
+// times applications of p_k on it with CUDA events and reports the
+// fastest.  Nothing of the method changes: every layout
 // holds the same seed-scaled matrix, and the iterates agree to rounding.
 #include <algorithm>
 #include <cmath>
@@ -23,6 +24,7 @@ struct Candidate {
 std::vector<Candidate> candidates() {
   std::vector<Candidate> out;
   out.push_back({PP_FMT_CSR, 0, 0, 0});
+  out.push_back({PP_FMT_DIA, 0, 0, 0});
   for (int C : {32, 64, 128})
     for (int sigma : {0, 1024})
       for (int variant : {1, 2}) out.push_back({PP_FMT_SELL, C, sigma, variant});
@@ -56,6 +58,7 @@ extern "C" int pp_autotune_workspace_size(const pp_csr* A, const pp_options* opt
     pp_options o = candidate_options(*opt, cd);
     size_t b = 0;
     const int rc = pp_workspace_size(A, &o, &b);
+    if (rc == PP_EUNSUPPORTED) continue;  // layout not applicable to this matrix
     if (rc) return rc;
     most = std::max(most, b);
   }

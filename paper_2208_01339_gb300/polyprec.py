@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libpolyprec.so")
 
 PP_OK, PP_MAXIT, PP_EINVAL, PP_EBREAKDOWN, PP_ENONFINITE, PP_ECUDA, PP_ETIMEOUT, PP_EUNSUPPORTED = 0, 1, -1, -2, -3, -4, -5, -6
 INTERVAL = {"lanczos": 0, "given": 1}
-FORMAT = {"auto": 0, "csr": 1, "sell": 2}
+FORMAT = {"auto": 0, "csr": 1, "sell": 2, "dia": 3}
 PREC = {"f64": 0, "f32": 1, "bf16": 2}
 SEED = {"none": 0, "jacobi": 1}
 
@@ -68,7 +68,7 @@ class Info(ctypes.Structure):
                 ("beta_hat", ctypes.c_double), ("xi", ctypes.c_double), ("theta_bar", ctypes.c_double),
                 ("delta", ctypes.c_double), ("sigma_bar", ctypes.c_double), ("k", ctypes.c_int),
                 ("apply_prec", ctypes.c_int), ("lanczos_steps_done", ctypes.c_int), ("t_setup_ms", ctypes.c_double),
-                ("grid_blocks", ctypes.c_int), ("lowrank", ctypes.c_int),
+                ("grid_blocks", ctypes.c_int), ("ndiag", ctypes.c_int), ("lowrank", ctypes.c_int),
                 ("lowrank_steps_done", ctypes.c_int), ("ritz_resid", ctypes.c_double), ("theta_min", ctypes.c_double)]
 
     def as_dict(self) -> dict:
@@ -242,7 +242,7 @@ def apply_csr_static(rowptr, col, val, n: int, alpha: float, beta: float, xi: fl
     return z
 
 
-FORMAT_NAME = {1: "csr", 2: "sell"}
+FORMAT_NAME = {1: "csr", 2: "sell", 3: "dia"}
 
 
 def autotune(rowptr, col, val, n: int, stream=None, **options):

@@ -31,6 +31,7 @@ LAYOUTS = [
     dict(format="sell", sell_C=64, sell_variant=2),
     dict(format="sell", sell_C=64, sell_sigma=256, sell_variant=1),
     dict(format="sell", sell_C=64, sell_sigma=256, sell_variant=2),
+    dict(format="dia"),
 ]
 
 
@@ -84,6 +85,11 @@ def test_apply_wide_slices(layout, which):
     """Slices of width 8 (straight-line path) and 60 (wider than the shared
     memory staging buffer: direct-load fallback inside the TMA kernel)."""
     A = width8_matrix() if which == "w8" else I.dense_to_csr(I.random_spd(60, seed=3, cond=30.0))
+    if which == "dense60" and LAYOUTS[layout]["format"] == "dia":
+        with pytest.raises(P.PolyPrecError) as ei:  # 60 diagonals: DIA does not apply
+            P.Solver.from_host(A, k=6, interval="given", alpha=0.05, beta=1.95, **LAYOUTS[layout])
+        assert ei.value.status == P.PP_EUNSUPPORTED
+        return
     S = P.Solver.from_host(A, k=6, interval="given", alpha=0.05, beta=1.95, xi=1e-3, **LAYOUTS[layout])
     r = I.rhs_normal(A.n, 2)
     z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
@@ -135,7 +141,7 @@ def test_operator_product(layout):
 def test_ragged_sizes_and_tiny():
     for n in (1, 2, 63, 65, 127, 129):
         A = I.diagonal(n)
-        for fmt in ("csr", "sell"):
+        for fmt in ("csr", "sell", "dia"):
             S = P.Solver.from_host(A, k=3, interval="given", alpha=1.0, beta=float(n) + 1.0, xi=0.0,
                                    seed_scaling=False, format=fmt)
             r = I.rhs_uniform(n, 2)
@@ -151,3 +157,26 @@ def test_invalid_setup_reports_error():
     B = I.dense_to_csr(np.diag([1.0, -1.0, 2.0]))
     with pytest.raises(P.PolyPrecError):
         P.Solver.from_host(B, k=3)
+
+
+def test_dia_rejects_unsymmetric_and_missing_diagonal():
+    D = I.poisson3d(4).to_dense()
+    D[0, 1] = -0.9  # a(0,1) != a(1,0)
+    with pytest.raises(P.PolyPrecError) as ei:
+        P.Solver.from_host(I.dense_to_csr(D), k=3, format="dia")
+    assert ei.value.status == P.PP_EUNSUPPORTED
+    E = np.diag([2.0, 2.0, 2.0])
+    E[0, 1] = E[1, 0] = -1.0
+    A = I.dense_to_csr(E)
+    A.val[0] = 2.0  # keep values; drop nothing: this one is fine
+    S = P.Solver.from_host(A, k=2, format="dia", interval="given", alpha=0.5, beta=3.5)
+    assert S.info()["format"] == 3 and S.info()["ndiag"] == 2
+
+
+def test_dia_uses_four_diagonals_for_the_7_point_stencil():
+    A = I.diffusion3d(17, 2.0, seed=5)
+    S = P.Solver.from_host(A, k=5, format="dia")
+    info = S.info()
+    assert info["format"] == 3 and info["ndiag"] == 4
+    x = I.rhs_normal(A.n, 6)
+    assert rel(to_np(S.operator(torch.as_tensor(x, device="cuda"))), A.matvec(x)) <= 1e-13

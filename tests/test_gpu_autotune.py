@@ -29,7 +29,7 @@ def test_autotune_picks_fastest_and_solves(prec):
     rp, ci, va = P.to_device_csr(A)
     base = dict(k=6, rtol=1e-10, apply_prec=prec, flexible=1 if prec != "f64" else 0)
     chosen, table = P.autotune(rp, ci, va, A.n, **base)
-    assert len(table) == 13
+    assert len(table) == 14  # CSR, DIA and 12 SELL layouts
     assert all(t["status"] == 0 and t["us_per_step"] > 0 for t in table)
     fastest = min(table, key=lambda t: t["us_per_step"])
     assert (P.FORMAT_NAME[fastest["format"]], fastest["sell_C"], fastest["sell_sigma"], fastest["sell_variant"]) == (

@@ -71,6 +71,16 @@ def test_mixed_apply_matches_rounded_oracle(prec, C, var, k):
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("k", [0, 1, 2, 7])
+def test_mixed_dia_apply(prec, k):
+    A = I.diffusion3d(17, 2.0, seed=1)
+    S = P.Solver.from_host(A, k=k, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="dia", apply_prec=prec)
+    r = I.rhs_normal(A.n, 3)
+    z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
+    assert rel(z, oracle_apply_rounded(A, r, 0.05, 1.95, 1e-3, k, prec)) <= 2e-5
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
 def test_mixed_csr_apply(prec):
     A = I.diffusion3d(9, 1.0, seed=2)
     S = P.Solver.from_host(A, k=6, interval="given", alpha=0.1, beta=1.9, xi=1e-3, format="csr", apply_prec=prec)

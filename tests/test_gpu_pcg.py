@@ -69,7 +69,8 @@ def test_tight_solve_matches_dense():
 
 
 @pytest.mark.parametrize("fmt,C,sigma,var", [("csr", 0, 0, 0), ("sell", 32, 0, 1), ("sell", 64, 0, 1),
-                                             ("sell", 32, 0, 2), ("sell", 64, 0, 2), ("sell", 64, 512, 2)])
+                                             ("sell", 32, 0, 2), ("sell", 64, 0, 2), ("sell", 64, 512, 2),
+                                             ("dia", 0, 0, 0)])
 def test_fixed_iterations_iterates(fmt, C, sigma, var):
     A = I.diffusion3d(20, 2.0, seed=1)
     b = I.rhs_normal(A.n, 1)
