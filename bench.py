@@ -440,6 +440,10 @@ def main():
     ap.add_argument("--lowrank", type=int, default=0,
                     help="Section 3.1 low-rank correction with this many Ritz vectors (0: none)")
     ap.add_argument("--lanczos-steps", type=int, default=0, help="override the workload's Lanczos steps")
+    ap.add_argument("--format", default="", choices=["", "csr", "sell", "dia"],
+                    help="force the step storage (skips pp_autotune)")
+    ap.add_argument("--grid", type=int, default=0, help="override the grid size N of a diffusion workload "
+                                                        "(smaller cases for profiler captures)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip pp_autotune (layout from --sell-C/--sell-sigma/--sell-variant or the defaults)")
     args = ap.parse_args()
@@ -450,6 +454,10 @@ def main():
         w["nmax"] = args.batch_nmax
     if args.lanczos_steps:
         w["lanczos"] = args.lanczos_steps
+    if args.grid and "N" in w:
+        w["N"] = args.grid
+    if args.format:
+        w["fmt"] = args.format
 
     from paper_2208_01339_gb300 import replicas
 
@@ -490,7 +498,7 @@ def main():
                 sell_variant=args.sell_variant, sell_C=args.sell_C, sell_sigma=args.sell_sigma, lowrank=args.lowrank)
     rp, ci, va = P.to_device_csr(A, dev)
     tune = None
-    if not args.no_autotune and w["fmt"] == "sell":
+    if not args.no_autotune and not args.format and w["fmt"] == "sell":
         # untimed setup: choose the step storage by timing every layout
         chosen, table = P.autotune(rp, ci, va, A.n, **opts)
         opts.update({key: chosen[key] for key in ("format", "sell_C", "sell_sigma", "sell_variant")})

@@ -6,8 +6,8 @@
 // of symmetric off-diagonals only the upper one: row i reads its upper
 // entries at position i of each diagonal and its lower entries at position
 // i - offset, which another thread of the same sweep has just read, so the
-// second read is served by L2.  One row per thread, consecutive rows on
-// consecutive lanes: every stream is coalesced.
+// second read is served by L2.  Consecutive row groups on consecutive
+// lanes: every stream is coalesced.
 #include "step_impl.cuh"
 
 namespace pp {
@@ -29,10 +29,55 @@ __device__ __forceinline__ TX ldv(const TV* p) {
   }
 }
 
+// R consecutive rows per thread (R = 2 for FP64, 4 for FP32/BF16): the
+// aligned streams (the stored diagonals at the thread's rows, its own x, r,
+// x_old and y) move as one vector access each, and the thread keeps R times
+// more loads in flight.  (Aligned vector loads of the partners at offsets
+// that are multiples of R, and lane shuffles for offset 1, measured slower:
+// they doubled the registers per thread and cost occupancy.)  Rows run over [0, n_pad): padding rows have zero
+// entries and zero vectors, so they produce y = 0 and add nothing to the
+// inner products.
+template <typename T, int R>
+struct Vec;
+template <>
+struct Vec<double, 2> {
+  __device__ static void ld(const double* p, double (&o)[2]) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = t.x;
+    o[1] = t.y;
+  }
+  __device__ static void st(double* p, const double (&v)[2]) { *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]); }
+};
+template <>
+struct Vec<float, 4> {
+  __device__ static void ld(const float* p, float (&o)[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = t.x;
+    o[1] = t.y;
+    o[2] = t.z;
+    o[3] = t.w;
+  }
+  __device__ static void st(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <typename TV, typename TX, int R>
+__device__ __forceinline__ void ldvals(const TV* p, TX (&o)[R]) {
+  if constexpr (std::is_same<TV, __nv_bfloat16>::value) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    o[0] = (TX)bf16_lo(u.x);
+    o[1] = (TX)bf16_hi(u.x);
+    o[2] = (TX)bf16_lo(u.y);
+    o[3] = (TX)bf16_hi(u.y);
+  } else {
+    Vec<TX, R>::ld(p, o);
+  }
+}
+
 // ND > 0: that many stored diagonals, unrolled; ND = 0: d.nd at run time.
-template <typename TV, typename TX, int ND, int MODE, int NDOT>
-__global__ void __launch_bounds__(kBlock) dia_step_kernel(int n, DiaArgs d, const TV* __restrict__ val,
-                                                          StepArgs<TX> a, const Scalars* sc, double* partials,
+template <typename TV, typename TX, int R, int ND, int MODE, int NDOT>
+__global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* __restrict__ val, StepArgs<TX> a,
+                                                          const Scalars* sc, double* partials,
                                                           unsigned int* counter) {
   if (sc && load_done(sc)) return;
   double dot[NDOT > 0 ? NDOT : 1];
@@ -42,30 +87,42 @@ __global__ void __launch_bounds__(kBlock) dia_step_kernel(int n, DiaArgs d, cons
   const int nd = ND > 0 ? ND : d.nd;
   const long long last = d.n_pad - 1;
   const TV* base = val + d.dpad;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const TX xs = __ldg(a.x + i);
-    TX acc = ldv<TV, TX>(base + i) * xs;
+  for (long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R; i0 < d.n_pad;
+       i0 += (long long)gridDim.x * blockDim.x * R) {
+    TX xs[R], acc[R], u[R];
+    Vec<TX, R>::ld(a.x + i0, xs);
+    ldvals<TV, TX, R>(base + i0, u);
+#pragma unroll
+    for (int e = 0; e < R; ++e) acc[e] = u[e] * xs[e];
 #pragma unroll
     for (int t = 1; t < (ND > 0 ? ND : kMaxDiag); ++t) {
       if (ND == 0 && t >= nd) break;
       const long long o = d.doff[t];
       const TV* vt = base + (long long)t * d.dstride;
-      const TX up = ldv<TV, TX>(vt + i);      // a(i, i + o); 0 past the last row
-      const TX lo = ldv<TV, TX>(vt + i - o);  // a(i - o, i) = a(i, i - o); 0 in the front pad
-      const long long ju = i + o < last ? i + o : last;
-      const long long jl = i - o > 0 ? i - o : 0;
-      acc = fma(up, __ldg(a.x + ju), acc);
-      acc = fma(lo, __ldg(a.x + jl), acc);
+      ldvals<TV, TX, R>(vt + i0, u);  // a(i, i + o); 0 past the last row
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        const long long i = i0 + e;
+        const TX lo = ldv<TV, TX>(vt + i - o);  // a(i - o, i) = a(i, i - o); 0 in the front pad
+        const long long ju = i + o < last ? i + o : last;
+        const long long jl = i - o > 0 ? i - o : 0;
+        acc[e] = fma(u[e], __ldg(a.x + ju), acc[e]);
+        acc[e] = fma(lo, __ldg(a.x + jl), acc[e]);
+      }
     }
-    TX rs = (TX)0, xo = (TX)0;
-    if constexpr (mode_needs_r<MODE>()) rs = a.r[i];
+    TX rs[R], xo[R], y[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) rs[e] = xo[e] = (TX)0;
+    if constexpr (mode_needs_r<MODE>()) Vec<TX, R>::ld(a.r + i0, rs);
     if constexpr (mode_needs_xold<MODE>()) {
-      if (MODE == kChebK || a.xold) xo = a.xold[i];
+      if (MODE == kChebK || a.xold) Vec<TX, R>::ld(a.xold + i0, xo);
     }
-    const TX y = row_value<TX, MODE>(a, acc, xs, rs, xo, lan);
-    a.y[i] = y;
-    row_dots<TX, MODE, NDOT>(a, i, y, xs, rs, dot);
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      y[e] = row_value<TX, MODE>(a, acc[e], xs[e], rs[e], xo[e], lan);
+      row_dots<TX, MODE, NDOT>(a, i0 + e, y[e], xs[e], rs[e], dot);
+    }
+    Vec<TX, R>::st(a.y + i0, y);
   }
   finish_dots<TX, NDOT>(a, dot, partials, counter);
 }
@@ -86,13 +143,14 @@ cudaError_t go_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, dou
   if constexpr (!step_variant_used<TX, MODE, NDOT>()) {
     return cudaErrorNotSupported;
   } else {
+    constexpr int R = std::is_same<TX, double>::value ? 2 : 4;
     const TV* v = static_cast<const TV*>(A.val);
     if (A.ndiag == 4)
-      dia_step_kernel<TV, TX, 4, MODE, NDOT><<<grid, kBlock, 0, s>>>(A.n, dia_args(A), v, make_args<TX>(p), sc,
-                                                                     partials, cnt);
+      dia_step_kernel<TV, TX, R, 4, MODE, NDOT><<<grid, kBlock, 0, s>>>(dia_args(A), v, make_args<TX>(p), sc,
+                                                                        partials, cnt);
     else
-      dia_step_kernel<TV, TX, 0, MODE, NDOT><<<grid, kBlock, 0, s>>>(A.n, dia_args(A), v, make_args<TX>(p), sc,
-                                                                     partials, cnt);
+      dia_step_kernel<TV, TX, R, 0, MODE, NDOT><<<grid, kBlock, 0, s>>>(dia_args(A), v, make_args<TX>(p), sc,
+                                                                        partials, cnt);
     return cudaGetLastError();
   }
 }
@@ -136,9 +194,9 @@ int step_blocks_per_sm_dia(const MatDesc& A) {
   int nb = 0;
   cudaError_t e;
   if (A.ndiag == 4)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 4, kChebK, 0>, kBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 2, 4, kChebK, 0>, kBlock, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 0, kChebK, 0>, kBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 2, 0, kChebK, 0>, kBlock, 0);
   return (e == cudaSuccess && nb > 0) ? nb : 2;
 }
 

@@ -180,3 +180,19 @@ def test_dia_uses_four_diagonals_for_the_7_point_stencil():
     assert info["format"] == 3 and info["ndiag"] == 4
     x = I.rhs_normal(A.n, 6)
     assert rel(to_np(S.operator(torch.as_tensor(x, device="cuda"))), A.matvec(x)) <= 1e-13
+
+
+@pytest.mark.parametrize("N", [16, 17, 18, 20])
+@pytest.mark.parametrize("k", [1, 6])
+def test_dia_partner_paths(N, k):
+    """Grid sizes whose offsets N, N^2 are (16, 20), are not (17) or are only
+    for pairs of rows (18) multiples of the rows per thread: aligned vector,
+    scalar and shuffle partner paths of the DIA kernel, FP64 (2 rows per
+    thread) against the oracle."""
+    A = I.diffusion3d(N, 2.0, seed=N)
+    S = P.Solver.from_host(A, k=k, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="dia")
+    r = I.rhs_normal(A.n, 8)
+    z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
+    assert rel(z, oracle_apply(A, r, 0.05, 1.95, 1e-3, k)) <= APPLY_TOL
+    x = I.rhs_normal(A.n, 9)
+    assert rel(to_np(S.operator(torch.as_tensor(x, device="cuda"))), A.matvec(x)) <= 1e-13

@@ -72,8 +72,10 @@ def test_mixed_apply_matches_rounded_oracle(prec, C, var, k):
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("k", [0, 1, 2, 7])
-def test_mixed_dia_apply(prec, k):
-    A = I.diffusion3d(17, 2.0, seed=1)
+@pytest.mark.parametrize("N", [16, 17, 18])
+def test_mixed_dia_apply(prec, k, N):
+    """4 rows per thread: offsets N, N^2 multiples of 4 (16), not (17, 18)."""
+    A = I.diffusion3d(N, 2.0, seed=1)
     S = P.Solver.from_host(A, k=k, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="dia", apply_prec=prec)
     r = I.rhs_normal(A.n, 3)
     z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
