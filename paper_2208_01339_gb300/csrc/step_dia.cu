@@ -29,7 +29,8 @@ __device__ __forceinline__ TX ldv(const TV* p) {
   }
 }
 
-// R consecutive rows per thread (R = 2 for FP64, 4 for FP32/BF16): the
+// R consecutive rows per thread (R = 4 for FP64, 2 for FP32/BF16, the
+// fastest of R in {2, 4, 8} at 192^3): the
 // aligned streams (the stored diagonals at the thread's rows, its own x, r,
 // x_old and y) move as one vector access each, and the thread keeps R times
 // more loads in flight.  (Aligned vector loads of the partners at offsets
@@ -49,6 +50,49 @@ struct Vec<double, 2> {
   __device__ static void st(double* p, const double (&v)[2]) { *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]); }
 };
 template <>
+struct Vec<double, 4> {
+  __device__ static void ld(const double* p, double (&o)[4]) {
+    const double2 t0 = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 t1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = t0.x;
+    o[1] = t0.y;
+    o[2] = t1.x;
+    o[3] = t1.y;
+  }
+  __device__ static void st(double* p, const double (&v)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+template <>
+struct Vec<float, 2> {
+  __device__ static void ld(const float* p, float (&o)[2]) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    o[0] = t.x;
+    o[1] = t.y;
+  }
+  __device__ static void st(float* p, const float (&v)[2]) { *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]); }
+};
+template <>
+struct Vec<float, 8> {
+  __device__ static void ld(const float* p, float (&o)[8]) {
+    const float4 t0 = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 t1 = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    o[0] = t0.x;
+    o[1] = t0.y;
+    o[2] = t0.z;
+    o[3] = t0.w;
+    o[4] = t1.x;
+    o[5] = t1.y;
+    o[6] = t1.z;
+    o[7] = t1.w;
+  }
+  __device__ static void st(float* p, const float (&v)[8]) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+};
+template <>
 struct Vec<float, 4> {
   __device__ static void ld(const float* p, float (&o)[4]) {
     const float4 t = __ldg(reinterpret_cast<const float4*>(p));
@@ -64,11 +108,25 @@ struct Vec<float, 4> {
 template <typename TV, typename TX, int R>
 __device__ __forceinline__ void ldvals(const TV* p, TX (&o)[R]) {
   if constexpr (std::is_same<TV, __nv_bfloat16>::value) {
-    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-    o[0] = (TX)bf16_lo(u.x);
-    o[1] = (TX)bf16_hi(u.x);
-    o[2] = (TX)bf16_lo(u.y);
-    o[3] = (TX)bf16_hi(u.y);
+    if constexpr (R == 2) {
+      const unsigned int u = __ldg(reinterpret_cast<const unsigned int*>(p));
+      o[0] = (TX)bf16_lo(u);
+      o[1] = (TX)bf16_hi(u);
+    } else if constexpr (R == 4) {
+      const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+      o[0] = (TX)bf16_lo(u.x);
+      o[1] = (TX)bf16_hi(u.x);
+      o[2] = (TX)bf16_lo(u.y);
+      o[3] = (TX)bf16_hi(u.y);
+    } else {
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+      const unsigned int w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        o[2 * q] = (TX)bf16_lo(w[q]);
+        o[2 * q + 1] = (TX)bf16_hi(w[q]);
+      }
+    }
   } else {
     Vec<TX, R>::ld(p, o);
   }
@@ -143,7 +201,7 @@ cudaError_t go_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, dou
   if constexpr (!step_variant_used<TX, MODE, NDOT>()) {
     return cudaErrorNotSupported;
   } else {
-    constexpr int R = std::is_same<TX, double>::value ? 2 : 4;
+    constexpr int R = std::is_same<TX, double>::value ? 4 : 2;
     const TV* v = static_cast<const TV*>(A.val);
     if (A.ndiag == 4)
       dia_step_kernel<TV, TX, R, 4, MODE, NDOT><<<grid, kBlock, 0, s>>>(dia_args(A), v, make_args<TX>(p), sc,
@@ -194,9 +252,9 @@ int step_blocks_per_sm_dia(const MatDesc& A) {
   int nb = 0;
   cudaError_t e;
   if (A.ndiag == 4)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 2, 4, kChebK, 0>, kBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 4, 4, kChebK, 0>, kBlock, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 2, 0, kChebK, 0>, kBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 4, 0, kChebK, 0>, kBlock, 0);
   return (e == cudaSuccess && nb > 0) ? nb : 2;
 }
 
