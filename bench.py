@@ -106,7 +106,7 @@ def fp64_peak_tflops() -> float:
 def source_sha() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2208_01339_gb300", "csrc")
-    for f in ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_f64.cu", "step_lp.cu"):
+    for f in ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_f64.cu", "step_lp.cu", "step_dia.cu"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -231,7 +231,8 @@ int pp_autotune_workspace_size(const pp_csr* A, const pp_options* opt, size_t* b
  * is symmetric-banded; SELL-C-sigma with C in {32, 64, 128}, sigma in
  * {none, 1024}, direct or TMA-staged loads) that fits in the workspace, time min(k, 8)-step applications of p_k in
  * opt->apply_prec with CUDA events (one warm-up, 5 timed), and write the
- * fastest layout into opt (format, sell_C, sell_sigma, sell_variant; the
+ * fastest layout into opt (timings within 3% of the fastest count as a tie,
+ * won by the first in the order DIA, SELL C = 32 .. 128, CSR) (format, sell_C, sell_sigma, sell_variant; the
  * rest of opt is unchanged).  The method is unchanged by the choice.
  * workspace: device scratch, 256-byte aligned.  entries (host, may be
  * NULL) receives up to max_entries results in trial order; *count (may be

@@ -501,6 +501,9 @@ extern "C" int pcg_setup(pp_ctx** out, const pp_csr* A, const pp_options* opt, v
                                                          : (long long)A->n * c->A64.csr_group;
     const long long want = (work + kBlock - 1) / kBlock;
     c->grid_step = (int)std::max(1LL, std::min<long long>(std::min(kMaxGrid, c->num_sms * mb), want));
+    // DIA kernels size their grid per variant (one resident wave); this is the cap
+    if (c->A64.format == PP_FMT_DIA) c->grid_step = (int)std::max(1LL, std::min<long long>(kMaxGrid, want));
+    c->grid_step_lp = c->grid_step;
   }
   rc = setup_interval_and_coeffs(c, s);
   if (rc) return bail(rc);

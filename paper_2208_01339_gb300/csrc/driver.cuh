@@ -84,6 +84,7 @@ struct pp_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int num_sms = 152, grid_step = 1, grid_vec = 1;
+  int grid_step_lp = 1;  // blocks of the step kernels on the apply-precision matrix (mixed)
   double alpha_hat = 0, beta_hat = 0, xi = 0, theta_bar = 0, delta = 0, sigma_bar = 0;
   std::vector<double> rho;
   int lanczos_steps_done = 0;

@@ -24,7 +24,8 @@ cudaError_t op_step(pp_ctx* c, bool apply_matrix, const StepParams& p, const Sca
   if (c->kind == 1) return schur_scaled_step(c, p, skip, counter, s);
   StepParams q = p;
   q.err = &c->sc->dev_error;
-  return launch_step(apply_matrix ? c->Ap : c->A64, q, skip, c->partials, counter, c->grid_step, s);
+  const bool lp = apply_matrix && c->mixed;
+  return launch_step(lp ? c->Ap : c->A64, q, skip, c->partials, counter, lp ? c->grid_step_lp : c->grid_step, s);
 }
 
 namespace {

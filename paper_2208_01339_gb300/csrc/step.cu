@@ -23,7 +23,7 @@ int step_max_blocks_per_sm(const MatDesc& A, int mode, int ndot) {
   (void)mode;
   (void)ndot;
   if (A.format == 3) return step_blocks_per_sm_dia(A);
-  return step_blocks_per_sm_f64(A);
+  return step_blocks_per_sm_f64(A);  // SELL/CSR: the FP64 kernel's occupancy for every precision
 }
 
 }  // namespace pp

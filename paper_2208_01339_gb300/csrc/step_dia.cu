@@ -185,6 +185,29 @@ __global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* _
   finish_dots<TX, NDOT>(a, dot, partials, counter);
 }
 
+// Whole resident waves per launch: the grid-stride loops split the rows evenly
+// over the blocks, so a grid that is not a whole number of waves leaves a
+// partly filled last wave.  The variants differ in registers (the ones that
+// reduce inner products hold more), hence in resident blocks per SM, so the
+// grid is taken per instantiation, capped by the caller's grid.
+constexpr int kWaves = 2;  // resident waves per launch (measured: 2 beats 1 and equals 3)
+
+template <typename TV, typename TX, int R, int ND, int MODE, int NDOT>
+int wave_grid(int cap) {
+  static int blocks = 0;  // one cache per kernel instantiation
+  if (blocks == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dia_step_kernel<TV, TX, R, ND, MODE, NDOT>, kBlock,
+                                                      0) != cudaSuccess ||
+        per_sm <= 0)
+      per_sm = 1;
+    blocks = sms * per_sm * kWaves;
+  }
+  return blocks < cap ? blocks : cap;
+}
+
 DiaArgs dia_args(const MatDesc& A) {
   DiaArgs d;
   d.nd = A.ndiag;
@@ -204,11 +227,11 @@ cudaError_t go_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, dou
     constexpr int R = std::is_same<TX, double>::value ? 4 : 2;
     const TV* v = static_cast<const TV*>(A.val);
     if (A.ndiag == 4)
-      dia_step_kernel<TV, TX, R, 4, MODE, NDOT><<<grid, kBlock, 0, s>>>(dia_args(A), v, make_args<TX>(p), sc,
-                                                                        partials, cnt);
+      dia_step_kernel<TV, TX, R, 4, MODE, NDOT><<<wave_grid<TV, TX, R, 4, MODE, NDOT>(grid), kBlock, 0, s>>>(
+          dia_args(A), v, make_args<TX>(p), sc, partials, cnt);
     else
-      dia_step_kernel<TV, TX, R, 0, MODE, NDOT><<<grid, kBlock, 0, s>>>(dia_args(A), v, make_args<TX>(p), sc,
-                                                                        partials, cnt);
+      dia_step_kernel<TV, TX, R, 0, MODE, NDOT><<<wave_grid<TV, TX, R, 0, MODE, NDOT>(grid), kBlock, 0, s>>>(
+          dia_args(A), v, make_args<TX>(p), sc, partials, cnt);
     return cudaGetLastError();
   }
 }
@@ -251,7 +274,12 @@ cudaError_t launch_step_dia(const MatDesc& A, const StepParams& p, const Scalars
 int step_blocks_per_sm_dia(const MatDesc& A) {
   int nb = 0;
   cudaError_t e;
-  if (A.ndiag == 4)
+  if (A.prec == kF32)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<float, float, 2, 4, kChebK, 0>, kBlock, 0);
+  else if (A.prec == kBF16)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<__nv_bfloat16, float, 2, 4, kChebK, 0>,
+                                                      kBlock, 0);
+  else if (A.ndiag == 4)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 4, 4, kChebK, 0>, kBlock, 0);
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 4, 0, kChebK, 0>, kBlock, 0);

@@ -22,12 +22,13 @@ struct Candidate {
 };
 
 std::vector<Candidate> candidates() {
+  // preference order for ties: fewest bytes per step first
   std::vector<Candidate> out;
-  out.push_back({PP_FMT_CSR, 0, 0, 0});
   out.push_back({PP_FMT_DIA, 0, 0, 0});
   for (int C : {32, 64, 128})
     for (int sigma : {0, 1024})
       for (int variant : {1, 2}) out.push_back({PP_FMT_SELL, C, sigma, variant});
+  out.push_back({PP_FMT_CSR, 0, 0, 0});
   return out;
 }
 
@@ -119,6 +120,13 @@ extern "C" int pp_autotune(const pp_csr* A, pp_options* opt, void* ws, size_t ws
     for (int i = 0; i < (int)res.size() && i < max_entries; ++i) entries[i] = res[i];
   if (count) *count = tried;
   if (best < 0) return fail(nullptr, PP_EINVAL, "no candidate layout fits in the workspace");
+  // timings within 3% of the fastest are a tie: take the first in preference
+  // order, so that the choice does not flip on timing noise
+  for (int i = 0; i < (int)res.size(); ++i)
+    if (res[i].status == PP_OK && res[i].us_per_step <= 1.03 * best_us) {
+      best = i;
+      break;
+    }
   opt->format = res[best].format;
   opt->sell_C = res[best].sell_C;
   opt->sell_sigma = res[best].sell_sigma;

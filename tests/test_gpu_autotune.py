@@ -31,9 +31,11 @@ def test_autotune_picks_fastest_and_solves(prec):
     chosen, table = P.autotune(rp, ci, va, A.n, **base)
     assert len(table) == 14  # CSR, DIA and 12 SELL layouts
     assert all(t["status"] == 0 and t["us_per_step"] > 0 for t in table)
-    fastest = min(table, key=lambda t: t["us_per_step"])
-    assert (P.FORMAT_NAME[fastest["format"]], fastest["sell_C"], fastest["sell_sigma"], fastest["sell_variant"]) == (
+    best = min(t["us_per_step"] for t in table)
+    pick = next(t for t in table if t["us_per_step"] <= 1.03 * best)  # ties within 3%: first in order
+    assert (P.FORMAT_NAME[pick["format"]], pick["sell_C"], pick["sell_sigma"], pick["sell_variant"]) == (
         chosen["format"], chosen["sell_C"], chosen["sell_sigma"], chosen["sell_variant"])
+    assert table[0]["format"] == 3 and table[-1]["format"] == 1  # DIA first, CSR last
     S = P.Solver(rp, ci, va, A.n, **chosen)
     x, st = S.solve(torch.as_tensor(b, device="cuda"))
     xo, so = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), k=6, rtol=1e-10, flexible=prec != "f64")
@@ -65,5 +67,7 @@ def test_autotune_skips_layouts_that_do_not_fit():
     assert rc == 0
     st = [ent[i].status for i in range(cnt.value)]
     assert 0 in st and P.PP_EINVAL in st
-    best = min((ent[i] for i in range(cnt.value) if ent[i].status == 0), key=lambda e: e.us_per_step)
+    ok = [ent[i] for i in range(cnt.value) if ent[i].status == 0]
+    fastest = min(e.us_per_step for e in ok)
+    best = next(e for e in ok if e.us_per_step <= 1.03 * fastest)
     assert (o.format, o.sell_C, o.sell_variant) == (best.format, best.sell_C, best.sell_variant)
