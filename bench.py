@@ -41,7 +41,9 @@ WORKLOADS = {
     "diffusion128": dict(N=128, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=60, fmt="sell", prec="f64"),
     "diffusion128_f32": dict(N=128, sigma=2.0, seed=1, rhs="normal", k=5, lanczos=60, fmt="sell", prec="f32",
                              flexible=1),
-    "poisson32": dict(N=32, sigma=0.0, seed=0, rhs="ones_noise", k=20, lanczos=10, fmt="csr", prec="f64"),
+    # 32^3 Poisson is L2-resident and launch-bound: 10-iteration blocks replayed as CUDA graphs
+    "poisson32": dict(N=32, sigma=0.0, seed=0, rhs="ones_noise", k=20, lanczos=10, fmt="csr", prec="f64",
+                      graphs=1, check_every=10),
     "dfn200": dict(dfn=True, seed=2, k=40, lanczos=10, prec="f64"),
     "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32"),
 }
@@ -427,11 +429,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="diffusion192", choices=list(WORKLOADS))
     ap.add_argument("--k", type=int, default=None)
-    ap.add_argument("--graphs", type=int, default=0)
+    ap.add_argument("--graphs", type=int, default=-1, help="CUDA graphs for PCG blocks (default: per workload)")
     ap.add_argument("--sell-variant", type=int, default=0, help="0 auto, 1 direct loads, 2 TMA-staged")
     ap.add_argument("--sell-C", type=int, default=0)
     ap.add_argument("--sell-sigma", type=int, default=0)
-    ap.add_argument("--check-every", type=int, default=8)
+    ap.add_argument("--check-every", type=int, default=0, help="PCG iterations per host check (default: per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--k-sweep", default="", help="comma-separated degrees: time one solve per degree instead")
@@ -486,15 +488,18 @@ def main():
         return run_batch(args, w, A, k, dev, world, rank)
     if w.get("dfn"):
         net = A
-        dopts = dict(lanczos_steps=w["lanczos"], rtol=1e-8, check_every=args.check_every, use_graphs=args.graphs,
+        dopts = dict(lanczos_steps=w["lanczos"], rtol=1e-8, check_every=args.check_every or 8,
+                     use_graphs=max(args.graphs, 0),
                      maxit=5000, lowrank=args.lowrank)
         if args.k_sweep:
             return run_dfn_sweep(args, w, net, dopts, dev)
         S = P.SchurSolver(net, device=dev, k=k, **dopts)
         bt = S.rhs(torch.as_tensor(net.q, device=dev))
         return run_dfn(args, w, net, S, bt, k, dev, world, rank, dist)
+    graphs = args.graphs if args.graphs >= 0 else w.get("graphs", 0)
+    check_every = args.check_every if args.check_every > 0 else w.get("check_every", 8)
     opts = dict(k=k, lanczos_steps=w["lanczos"], format=w["fmt"], apply_prec=w["prec"], rtol=1e-8,
-                check_every=args.check_every, use_graphs=args.graphs, flexible=w.get("flexible", 0),
+                check_every=check_every, use_graphs=graphs, flexible=w.get("flexible", 0),
                 sell_variant=args.sell_variant, sell_C=args.sell_C, sell_sigma=args.sell_sigma, lowrank=args.lowrank)
     rp, ci, va = P.to_device_csr(A, dev)
     tune = None
@@ -610,7 +615,7 @@ def main():
                    "sigma_ln": w["sigma"], "format": fmt_name,
                    "lanczos_steps": w["lanczos"], "rtol": 1e-8,
                    "l2": "inputs larger than L2 (matrix >> 129 MB)" if A.nnz * 12 > 129e6 else "L2-resident inputs",
-                   "graphs": args.graphs, "layout": layout,
+                   "graphs": graphs, "check_every": check_every, "layout": layout,
                    "autotune": ("pp_autotune: [format(1 CSR, 2 SELL, 3 DIA), C, sigma, variant(1 direct, 2 TMA), "
                                 "us/step] " + json.dumps(tune)) if tune else "off",
                    "lowrank": args.lowrank,
