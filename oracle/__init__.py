@@ -24,7 +24,10 @@ Parity status of each routine (how it is pinned independently of itself):
                             (eigenvalue + 1, Section 3.1), invariance
                             under V -> V R, symmetry
   pcg_csr                   dense solves, Table 1 iteration counts,
-                            Table 4 work counts
+                            Table 4 work counts; FCG(m) equals PCG for a
+                            fixed SPD preconditioner
+  fcg_dense                 A-orthogonality of the last m directions and
+                            finite termination with a nonsymmetric M
   schur_*                   dense S_u from its expansion, diag, dense K_0
                             solve of the saddle-point system
 """
@@ -107,6 +110,8 @@ def lib():
                                              ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, _d]
         L.oracle_lowrank_apply.argtypes = [ctypes.c_int, _i, _i, _d, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_int, ctypes.c_int, _d, _d, _d]
+        L.oracle_fcg_dense.argtypes = [ctypes.c_int, _d, _d, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_double, _d,
+                                       ctypes.POINTER(Stats)]
         L.oracle_pcg_csr.argtypes = [ctypes.c_int, _i, _i, _d, _d, _d, _d, ctypes.POINTER(Options),
                                      ctypes.POINTER(Stats)]
         L.oracle_schur_create.argtypes = [ctypes.POINTER(Dfn)]
@@ -295,6 +300,21 @@ def make_options(k=20, xi=-1.0, interval="lanczos", alpha=0.0, beta=0.0, lanczos
         o.lowrank = lr_V.shape[1]
         o.lr_V = _p(o._keep, ctypes.c_double)
     return o
+
+
+def fcg_dense(A, M, b, m: int, maxit: int, rtol: float = 0.0, x0=None):
+    """FCG(m) (m >= 2) on dense A with the dense preconditioner M.
+    Returns (x, directions [iterations+1 x n], stats dict)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    n = A.shape[0]
+    b = _f64(b)
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    dirs = np.zeros((maxit + 1, n))
+    st = Stats()
+    lib().oracle_fcg_dense(n, _p(A, ctypes.c_double), _p(M, ctypes.c_double), _p(b, ctypes.c_double),
+                           _p(x, ctypes.c_double), m, maxit, rtol, _p(dirs, ctypes.c_double), ctypes.byref(st))
+    return x, dirs[:st.iterations + 1], st.as_dict()
 
 
 def pcg_csr(A, b, x0=None, v0=None, **opts):

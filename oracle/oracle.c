@@ -556,8 +556,152 @@ static int prec_apply(const op_t* A, const cheb_t* P, const double* r, double* z
   return all_finite(A->n, z) ? 0 : -3;
 }
 
+/* Truncated flexible CG, FCG(m) (Notay 2000), for m >= 2: from x0,
+ * r = b - A x, z = M r, p_0 = z; each iteration q_i = A p_i,
+ * alpha = (r, p_i)/(p_i, q_i), x += alpha p_i, r -= alpha q_i, stop when
+ * ||r||/||b|| <= rtol, z = M r, and the next direction is z made
+ * A-orthogonal to the last m directions:
+ *   p_{i+1} = z - sum_{j = max(0, i-m+1)}^{i} (z, q_j)/(p_j, q_j) p_j.
+ * M may be any operator (a variable or nonsymmetric preconditioner too).
+ * Inner products per iteration: (p, q), (r, r), m of (z, q_j) (fewer in the
+ * first m - 1 iterations) and (r, p); counted in dots.  dirs (may be NULL)
+ * receives the directions p_0, p_1, ... (n each, at most maxit + 1). */
+static int fcgm_core(const op_t* A, const op_t* M, const double* b, double* x, int m, int maxit,
+                     double rtol, oracle_stats* st, double* dirs, long long* mvp_out,
+                     long long* dots_out) {
+  int n = A->n;
+  double* r = (double*)malloc(sizeof(double) * (size_t)n);
+  double* z = (double*)malloc(sizeof(double) * (size_t)n);
+  double* P = (double*)calloc((size_t)n * m, sizeof(double));
+  double* Q = (double*)calloc((size_t)n * m, sizeof(double));
+  double* pq = (double*)calloc((size_t)m, sizeof(double));
+  double* pn = (double*)malloc(sizeof(double) * (size_t)n);
+  long long mvp = 0, dots = 0;
+  int rc = 0, it = 0;
+  double bnorm = sqrt(dot(n, b, b));
+  int x_zero = 1;
+  for (int i = 0; i < n; ++i)
+    if (x[i] != 0.0) { x_zero = 0; break; }
+  if (x_zero) {
+    memcpy(r, b, sizeof(double) * (size_t)n);
+  } else {
+    A->apply(A->ctx, x, r);
+    ++mvp;
+    for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
+  }
+  double rel = (bnorm > 0.0) ? sqrt(dot(n, r, r)) / bnorm : 0.0;
+  if (bnorm == 0.0 || rel <= rtol) goto done;
+  M->apply(M->ctx, r, z);
+  memcpy(P, z, sizeof(double) * (size_t)n); /* p_0 in slot 0 */
+  if (dirs) memcpy(dirs, z, sizeof(double) * (size_t)n);
+  double rp = dot(n, r, P);
+  ++dots;
+  rc = 1;
+  while (it < maxit) {
+    int s = it % m;
+    double* p = P + (size_t)s * n;
+    double* q = Q + (size_t)s * n;
+    A->apply(A->ctx, p, q);
+    ++mvp;
+    pq[s] = dot(n, p, q);
+    ++dots;
+    if (!(pq[s] > 0.0)) { rc = isfinite(pq[s]) ? -2 : -3; break; }
+    double alpha = rp / pq[s];
+    for (int i = 0; i < n; ++i) x[i] += alpha * p[i];
+    for (int i = 0; i < n; ++i) r[i] -= alpha * q[i];
+    ++it;
+    double rr = dot(n, r, r);
+    ++dots;
+    if (!isfinite(rr)) { rc = -3; break; }
+    rel = sqrt(rr) / bnorm;
+    if (rel <= rtol) { rc = 0; break; }
+    M->apply(M->ctx, r, z);
+    memcpy(pn, z, sizeof(double) * (size_t)n);
+    int nv = it < m ? it : m; /* directions p_{it-nv} .. p_{it-1} */
+    for (int t = 0; t < nv; ++t) {
+      int sj = (s - t + m) % m;
+      double beta = -dot(n, z, Q + (size_t)sj * n) / pq[sj];
+      ++dots;
+      for (int i = 0; i < n; ++i) pn[i] += beta * P[(size_t)sj * n + i];
+    }
+    int s_new = it % m;
+    memcpy(P + (size_t)s_new * n, pn, sizeof(double) * (size_t)n);
+    if (dirs) memcpy(dirs + (size_t)it * n, pn, sizeof(double) * (size_t)n);
+    rp = dot(n, r, pn);
+    ++dots;
+    if (!isfinite(rp)) { rc = -3; break; }
+    rc = 1;
+  }
+done:
+  if (st) {
+    st->iterations = it;
+    st->rel_res = rel;
+    st->status = rc;
+  }
+  if (mvp_out) *mvp_out = mvp;
+  if (dots_out) *dots_out = dots;
+  free(r);
+  free(z);
+  free(P);
+  free(Q);
+  free(pq);
+  free(pn);
+  return rc;
+}
+
+/* The solve's preconditioner as an operator (for FCG(m)); counts work. */
+typedef struct {
+  const op_t* A;
+  const cheb_t* P;
+  long long mvp, dots;
+} precond_op_t;
+
+static void precond_op_apply(const void* c, const double* x, double* y) {
+  precond_op_t* pc = (precond_op_t*)c;
+  prec_apply(pc->A, pc->P, x, y, &pc->mvp, &pc->dots);
+}
+
+typedef struct {
+  int n;
+  const double* D; /* row-major n x n */
+} dense_t;
+
+static void dense_apply(const void* c, const double* x, double* y) {
+  const dense_t* d = (const dense_t*)c;
+  for (int i = 0; i < d->n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < d->n; ++j) s += d->D[(size_t)i * d->n + j] * x[j];
+    y[i] = s;
+  }
+}
+
+int oracle_fcg_dense(int n, const double* A, const double* M, const double* b, double* x, int m,
+                     int maxit, double rtol, double* dirs, oracle_stats* st) {
+  if (n <= 0 || m < 2 || maxit < 0) return -1;
+  dense_t da = {n, A}, dm = {n, M};
+  op_t opA = {dense_apply, &da, n}, opM = {dense_apply, &dm, n};
+  long long mvp = 0, dots = 0;
+  int rc = fcgm_core(&opA, &opM, b, x, m, maxit, rtol, st, dirs, &mvp, &dots);
+  if (st) {
+    st->mvp = mvp;
+    st->dots = dots;
+  }
+  return rc;
+}
+
 static int pcg_op(const op_t* A, const cheb_t* P, const double* b, double* x, int flexible,
                   int maxit, double rtol, oracle_stats* st) {
+  if (flexible >= 2) {
+    precond_op_t pc = {A, P, 0, 0};
+    op_t M = {precond_op_apply, &pc, A->n};
+    long long mvp = 0, dots = 0;
+    int rc2 = fcgm_core(A, &M, b, x, flexible, maxit, rtol, st, NULL, &mvp, &dots);
+    if (st) {
+      st->mvp = mvp + pc.mvp;
+      st->dots = dots + pc.dots;
+    }
+    return rc2;
+  }
   int n = A->n;
   double* r = (double*)malloc(sizeof(double) * (size_t)n);
   double* z = (double*)malloc(sizeof(double) * (size_t)n);

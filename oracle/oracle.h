@@ -23,7 +23,9 @@
  *   oracle_tridiag_eig     eigenpair of T_m: bisection + inverse iteration
  *   oracle_lowrank_vectors leftmost eigenvectors by Lanczos on p_k(A) A
  *   oracle_lowrank_apply   Section 3.1: P = P_0 + V (V^T A V)^{-1} V^T
- *   oracle_pcg_csr         PCG (Section 1) with P = W p_k(A_hat) W^T
+ *   oracle_pcg_csr         PCG (Section 1) with P = W p_k(A_hat) W^T, or
+ *                          flexible CG, FCG(1) or truncated FCG(m)
+ *   oracle_fcg_dense       FCG(m) with any dense preconditioner (pins)
  *   oracle_schur_*         Section 4.2: Algorithm 3 (y = S_u r), Algorithm 4
  *                          (D_S = diag S_u), the right-hand side
  *                          r = W^T M^{-1} f_1 and the recovery of h and p,
@@ -85,7 +87,9 @@ int oracle_lowrank_apply(int n, const int* rowptr, const int* col, const double*
 
 /* Options of the full solve.  interval: 0 = Lanczos on A_hat from v0,
  * 1 = given (alpha, beta).  xi < 0 selects xi = clip(10 alpha/beta, 1e-6, 1e-2).
- * seed_scaling: 0 none, 1 Jacobi.  flexible: 0 plain PCG, 1 flexible CG.
+ * seed_scaling: 0 none, 1 Jacobi.  flexible: 0 plain PCG, 1 flexible CG
+ * (FCG(1)), m >= 2 truncated flexible CG FCG(m) (A-orthogonal to the last
+ * m directions; alpha = (r, p)/(p, A p)).
  * lowrank = p > 0 adds the Section 3.1 correction V (V^T A_hat V)^{-1} V^T
  * with V = lr_V (n x p, seed-scaled space) or, when lr_V is NULL, the Ritz
  * vectors of the p smallest Ritz values of lowrank_steps (0: 30) Lanczos
@@ -105,6 +109,12 @@ typedef struct {
   int lowrank_steps;
   const double* lr_V;
 } oracle_options;
+
+/* FCG(m), m >= 2, on dense row-major A (n x n) with the dense operator M as
+ * the (possibly nonsymmetric) preconditioner; dirs (may be NULL, n x
+ * (maxit + 1)) receives the search directions. */
+int oracle_fcg_dense(int n, const double* A, const double* M, const double* b, double* x, int m,
+                     int maxit, double rtol, double* dirs, oracle_stats* st);
 
 int oracle_pcg_csr(int n, const int* rowptr, const int* col, const double* val,
                    const double* b, double* x, const double* v0, const oracle_options* opt,
