@@ -442,6 +442,8 @@ def main():
     ap.add_argument("--lowrank", type=int, default=0,
                     help="Section 3.1 low-rank correction with this many Ritz vectors (0: none)")
     ap.add_argument("--lanczos-steps", type=int, default=0, help="override the workload's Lanczos steps")
+    ap.add_argument("--flexible", type=int, default=-1,
+                    help="outer iteration: 0 PCG, 1 FCG(1), m >= 2 FCG(m) (default: per workload)")
     ap.add_argument("--format", default="", choices=["", "csr", "sell", "dia"],
                     help="force the step storage (skips pp_autotune)")
     ap.add_argument("--grid", type=int, default=0, help="override the grid size N of a diffusion workload "
@@ -456,6 +458,8 @@ def main():
         w["nmax"] = args.batch_nmax
     if args.lanczos_steps:
         w["lanczos"] = args.lanczos_steps
+    if args.flexible >= 0:
+        w["flexible"] = args.flexible
     if args.grid and "N" in w:
         w["N"] = args.grid
     if args.format:
@@ -616,6 +620,7 @@ def main():
                    "lanczos_steps": w["lanczos"], "rtol": 1e-8,
                    "l2": "inputs larger than L2 (matrix >> 129 MB)" if A.nnz * 12 > 129e6 else "L2-resident inputs",
                    "graphs": graphs, "check_every": check_every, "layout": layout,
+                   "outer": {0: "PCG", 1: "FCG(1)"}.get(w.get("flexible", 0), f"FCG({w.get('flexible', 0)})"),
                    "autotune": ("pp_autotune: [format(1 CSR, 2 SELL, 3 DIA), C, sigma, variant(1 direct, 2 TMA), "
                                 "us/step] " + json.dumps(tune)) if tune else "off",
                    "lowrank": args.lowrank,

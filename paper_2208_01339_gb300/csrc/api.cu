@@ -149,6 +149,7 @@ int validate_options(pp_ctx* c, const pp_options* o) {
   if (o->sell_sigma < 0) return fail(c, PP_EINVAL, "sell_sigma must be >= 0");
   if (o->sell_variant < 0 || o->sell_variant > 2) return fail(c, PP_EINVAL, "sell_variant must be 0, 1 or 2");
   if (o->lowrank < 0 || o->lowrank > kMaxLowRank) return fail(c, PP_EINVAL, "lowrank must be in [0, 32]");
+  if (o->flexible < 0 || o->flexible > kMaxFcg) return fail(c, PP_EINVAL, "flexible must be in [0, 8]");
   if (o->lowrank > 0 && o->lowrank_steps != 0 && (o->lowrank_steps < o->lowrank || o->lowrank_steps > kMaxLanczos))
     return fail(c, PP_EINVAL, "lowrank > 0 needs lowrank <= lowrank_steps <= 512 (0: 30)");
   if (o->lowrank > 30 && o->lowrank_steps == 0)
@@ -369,6 +370,12 @@ size_t layout(pp_ctx* c, void* base, const SellPlan& P) {
     c->u32 = B.take<float>(n_pad);
     c->v32 = B.take<float>(n_pad);
     c->z32 = B.take<float>(n_pad);
+  }
+  c->fcg_m = c->opt.flexible >= 2 ? c->opt.flexible : 0;
+  if (c->fcg_m) {
+    c->Pring = B.take<double>((long long)c->fcg_m * n_pad);
+    c->Qring = B.take<double>((long long)c->fcg_m * n_pad);
+    c->fcg_part = B.take<double>((long long)kMaxFcg * kMaxGrid);
   }
   c->vec_end = reinterpret_cast<void*>(B.base + B.off);
   c->lr_cap = c->opt.lowrank;

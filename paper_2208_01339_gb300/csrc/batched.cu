@@ -963,6 +963,8 @@ int check_batch_opts(const pp_options* o) {
   int rc = validate_options(nullptr, o);
   if (rc == PP_OK && o->lowrank != 0)
     rc = fail(nullptr, PP_EUNSUPPORTED, "the low-rank correction is not available for batch contexts");
+  if (rc == PP_OK && o->flexible > 1)
+    rc = fail(nullptr, PP_EUNSUPPORTED, "pp_batch: flexible must be 0 or 1 (FCG(1))");
   if (rc) return rc;
   if (o->apply_prec == PP_PREC_BF16) return fail(nullptr, PP_EUNSUPPORTED, "pp_batch: apply_prec must be F64 or F32");
   if (o->seed_scaling != PP_SEED_JACOBI) return fail(nullptr, PP_EUNSUPPORTED, "pp_batch: Jacobi seed only");

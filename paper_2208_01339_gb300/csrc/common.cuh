@@ -12,6 +12,7 @@ constexpr int kMaxDots = 3;        // values reduced by one fused kernel
 constexpr int kMaxLanczos = 512;   // Lanczos steps kept on the device
 constexpr int kBlock = 256;        // threads per block of the streaming kernels
 constexpr int kMaxLowRank = 32;    // vectors of the low-rank correction (Section 3.1)
+constexpr int kMaxFcg = 8;         // window of truncated flexible CG, FCG(m)
 
 // PCG / Lanczos state kept on the device so that a block of iterations can
 // run (or be replayed as a CUDA graph) without host round trips.  Kernels
@@ -34,6 +35,8 @@ struct Scalars {
   int dev_error;   // 1: a bounded wait inside a kernel expired (PP_ETIMEOUT)
   int pad_;
   unsigned int counters[8];
+  double fcg_pq[kMaxFcg];  // FCG(m): (p_j, A p_j) of the directions in the window, by ring slot
+  double fcg_zq[kMaxFcg];  // FCG(m): (z, A p_j) of the latest preconditioned residual, by ring slot
   double lan_a[kMaxLanczos];
   double lan_b2[kMaxLanczos];
 };

@@ -46,6 +46,10 @@ void destroy_ctx_resources(pp_ctx* c);
 // batched.cu
 void batch_free(pp_batch_state* b);
 
+// fcg.cu: FCG(m) window products and direction update
+cudaError_t fcg_dots(pp_ctx* c, int s_cur, cudaStream_t s);
+cudaError_t fcg_update_p(pp_ctx* c, int s_cur, int s_new, int first, cudaStream_t s);
+
 // lowrank.cu (Section 3.1)
 size_t lowrank_bytes(int cap, int m, long long n_pad, int grid_max);
 void lowrank_carve(pp_ctx* c, void* base);
@@ -104,6 +108,10 @@ struct pp_ctx {
   double *V = nullptr, *Q = nullptr, *lr_Y = nullptr, *lr_part = nullptr;
   void* lr_base = nullptr;
   int lr_steps_done = 0;
+  // truncated flexible CG, FCG(m) for m = opt.flexible >= 2: ring of the last
+  // m directions P and their products Q = A P (slot j at j * n_pad)
+  int fcg_m = 0;
+  double *Pring = nullptr, *Qring = nullptr, *fcg_part = nullptr;
   double lr_ritz_resid = 0;
   std::vector<double> lr_theta;  // Rayleigh quotients v^T A_hat v of the vectors
 };

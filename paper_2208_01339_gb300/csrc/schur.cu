@@ -624,6 +624,12 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
   c->t1 = B.take<double>(n_pad);
   c->t2 = B.take<double>(n_pad);
   c->bh = B.take<double>(n_pad);
+  c->fcg_m = c->opt.flexible >= 2 ? c->opt.flexible : 0;
+  if (c->fcg_m) {
+    c->Pring = B.take<double>((long long)c->fcg_m * n_pad);
+    c->Qring = B.take<double>((long long)c->fcg_m * n_pad);
+    c->fcg_part = B.take<double>((long long)kMaxFcg * kMaxGrid);
+  }
   c->vec_end = reinterpret_cast<void*>(B.base + B.off);
   c->lr_cap = c->opt.lowrank;
   c->lr_m = c->lr_cap > 0 ? (c->opt.lowrank_steps > 0 ? c->opt.lowrank_steps : 30) : 0;

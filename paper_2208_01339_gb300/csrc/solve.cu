@@ -87,11 +87,14 @@ cudaError_t cheb_core(pp_ctx* c, const Scalars* skip, const void* rin, void* zou
 cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   Scalars* sc = c->sc;
   VecLaunch L{c->grid_vec, c->partials, s};
-  const double* q = c->opt.flexible ? c->q : nullptr;
+  // FCG(m), m >= 2, needs no inner product here: its own kernels form them
+  const bool fcgm = c->fcg_m > 0;
+  const double* q = (c->opt.flexible == 1) ? c->q : nullptr;
   const bool lr = c->lr_p > 0;
-  const int nd = lr ? 0 : (q ? 2 : 1);
-  double* rz = lr ? nullptr : &sc->rz_new;
-  const double* qd = lr ? nullptr : q;
+  const bool nodot = lr || fcgm;
+  const int nd = nodot ? 0 : (q ? 2 : 1);
+  double* rz = nodot ? nullptr : &sc->rz_new;
+  const double* qd = nodot ? nullptr : q;
   cudaError_t e = lr ? lowrank_coefs(c, skip, c->r, s) : cudaSuccess;
   if (e != cudaSuccess) return e;
   if (c->opt.k == 0) {
@@ -112,7 +115,8 @@ cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s, cudaEvent_t 
     if (e == cudaSuccess)
       e = vec_from32_dot(L, c->n, skip, c->z32, c->z, c->r, qd, rz, &sc->zq, &sc->counters[kCntVec]);
   }
-  if (e == cudaSuccess && lr) e = lowrank_update(c, skip, c->z, c->r, q, &sc->rz_new, &sc->zq, s);
+  if (e == cudaSuccess && lr)
+    e = lowrank_update(c, skip, c->z, c->r, fcgm ? nullptr : q, fcgm ? nullptr : &sc->rz_new, &sc->zq, s);
   return e;
 }
 
@@ -148,20 +152,30 @@ long long precond_launches(const pp_ctx* c) {
   return n;
 }
 
-// One PCG iteration (q = A p; x, r update; z = P r; p update).
-cudaError_t pcg_iteration(pp_ctx* c, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+// One PCG iteration (q = A p; x, r update; z = P r; p update).  b is the
+// iteration's index within its block: FCG(m) takes its ring slot b mod m.
+cudaError_t pcg_iteration(pp_ctx* c, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int b) {
   Scalars* sc = c->sc;
   VecLaunch L{c->grid_vec, c->partials, s};
+  const int m = c->fcg_m;
+  const int s_cur = m ? b % m : 0;
+  double* pv = m ? c->Pring + (long long)s_cur * c->n_pad : c->p;
+  double* qv = m ? c->Qring + (long long)s_cur * c->n_pad : c->q;
   StepParams p;
   p.mode = kSpmv;
   p.ndot = 1;
-  p.x = c->p;
-  p.y = c->q;
+  p.x = pv;
+  p.y = qv;
   p.dot_out0 = &sc->pq;
   cudaError_t e = op_step(c, false, p, sc, &sc->counters[kCntStep], s);
-  if (e == cudaSuccess) e = vec_update_xr(L, c->n, sc, c->xh, c->r, c->p, c->q);
+  if (e == cudaSuccess) e = vec_update_xr(L, c->n, sc, c->xh, c->r, pv, qv);
   if (e == cudaSuccess) e = precond(c, sc, s, ev0, ev1);
-  if (e == cudaSuccess) e = vec_update_p(L, c->n, sc, c->z, c->p, 0);
+  if (m) {
+    if (e == cudaSuccess) e = fcg_dots(c, s_cur, s);
+    if (e == cudaSuccess) e = fcg_update_p(c, s_cur, (b + 1) % m, 0, s);
+  } else if (e == cudaSuccess) {
+    e = vec_update_p(L, c->n, sc, c->z, c->p, 0);
+  }
   return e;
 }
 
@@ -187,7 +201,7 @@ int build_graph(pp_ctx* c, int B) {
   e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
   cudaError_t e2 = cudaSuccess;
-  for (int b = 0; b < B && e2 == cudaSuccess; ++b) e2 = pcg_iteration(c, c->cap_stream, nullptr, nullptr);
+  for (int b = 0; b < B && e2 == cudaSuccess; ++b) e2 = pcg_iteration(c, c->cap_stream, nullptr, nullptr, b);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(c->cap_stream, &g);
   if (e2 != cudaSuccess) {
@@ -401,7 +415,8 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
   cudaStream_t s = (cudaStream_t)stream;
   Scalars* sc = c->sc;
   VecLaunch L{c->grid_vec, c->partials, s};
-  const int B = std::max(1, std::min(c->opt.check_every, kMaxCheck));
+  int B = std::max(1, std::min(c->opt.check_every, kMaxCheck));
+  if (c->fcg_m) B = std::min(kMaxCheck / c->fcg_m * c->fcg_m, (B + c->fcg_m - 1) / c->fcg_m * c->fcg_m);
   const bool graphs = c->opt.use_graphs != 0;
   if ((rc = ensure_events(c, 2 + 2 * (size_t)(B + 1)))) return rc;
   cudaEvent_t ev_start = c->events[0], ev_end = c->events[1];
@@ -427,7 +442,8 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
   }
   if (e == cudaSuccess) e = pcg_init(sc, c->opt.rtol, c->opt.maxit, c->opt.flexible, s);
   if (e == cudaSuccess) e = precond(c, sc, s, graphs ? nullptr : ev_pair(B, 0), graphs ? nullptr : ev_pair(B, 1));
-  if (e == cudaSuccess) e = vec_update_p(L, c->n, sc, c->z, c->p, 1);
+  if (e == cudaSuccess)
+    e = c->fcg_m ? fcg_update_p(c, 0, 0, 1, s) : vec_update_p(L, c->n, sc, c->z, c->p, 1);
   if (e != cudaSuccess) return cuda_fail(c, e, "pcg_solve start");
 
   const long long pre = precond_launches(c);
@@ -438,11 +454,11 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
   bool first_block = true;
   int iter_before = 0;
   for (;;) {
-    launches += (long long)B * (c->op_launches + 2 + pre);
+    launches += (long long)B * (c->op_launches + 2 + pre + (c->fcg_m ? 2 : 0));
     if (graphs) {
       e = cudaGraphLaunch(c->graph_exec, s);
     } else {
-      for (int bi = 0; bi < B && e == cudaSuccess; ++bi) e = pcg_iteration(c, s, ev_pair(bi, 0), ev_pair(bi, 1));
+      for (int bi = 0; bi < B && e == cudaSuccess; ++bi) e = pcg_iteration(c, s, ev_pair(bi, 0), ev_pair(bi, 1), bi);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, &sc->done, sizeof(host), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -479,7 +495,7 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
     std::memset(st, 0, sizeof(*st));
     st->iterations = iters;
     st->mvp = (long long)iters * (c->opt.k + 1) + (c->opt.zero_guess ? 0 : 1);
-    st->dots = (3LL + c->lr_p) * iters;
+    st->dots = (3LL + c->lr_p + c->fcg_m) * iters;
     st->rel_res = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
     st->alpha_hat = c->alpha_hat;
     st->beta_hat = c->beta_hat;
