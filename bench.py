@@ -275,7 +275,8 @@ def run_k_sweep(args, w, A, b, opts, dev):
             ts.append(st["t_solve_ms"])
         apply_us = st["t_apply_ms"] / max(1, st["apply_launches"]) * 1e3
         info = S.info()
-        print(json.dumps({"workload": args.workload, "prec": w["prec"], "k": k, "iterations": st["iterations"],
+        print(json.dumps({"workload": args.workload, "prec": w["prec"], "poly": args.poly, "k": k,
+                          "iterations": st["iterations"],
                           "time_s": statistics.median(ts) / 1e3, "mvp": st["mvp"], "dots": st["dots"],
                           "step_us": round(apply_us, 2), "status": st["status"], "lowrank": info["lowrank"],
                           "alpha_hat": info["alpha_hat"], "setup_ms": round(info["t_setup_ms"], 2),
@@ -300,7 +301,7 @@ def run_dfn_sweep(args, w, net, dopts, dev):
             _, st = S.solve(bt)
             ts.append(st["t_solve_ms"])
         info = S.info()
-        print(json.dumps({"workload": args.workload, "k": k, "lowrank": dopts["lowrank"],
+        print(json.dumps({"workload": args.workload, "k": k, "poly": dopts["poly"], "lowrank": dopts["lowrank"],
                           "lanczos_steps": dopts["lanczos_steps"], "iterations": st["iterations"],
                           "time_s": statistics.median(ts) / 1e3, "mvp": st["mvp"], "dots": st["dots"],
                           "setup_ms": round(info["t_setup_ms"], 2), "alpha_hat": info["alpha_hat"],
@@ -442,6 +443,8 @@ def main():
     ap.add_argument("--lowrank", type=int, default=0,
                     help="Section 3.1 low-rank correction with this many Ritz vectors (0: none)")
     ap.add_argument("--lanczos-steps", type=int, default=0, help="override the workload's Lanczos steps")
+    ap.add_argument("--poly", default="cheb", choices=["cheb", "newton"],
+                    help="Algorithm 2 (three-term recurrence) or Algorithm 1 (Newton form, k = 2^nlev - 1)")
     ap.add_argument("--flexible", type=int, default=-1,
                     help="outer iteration: 0 PCG, 1 FCG(1), m >= 2 FCG(m) (default: per workload)")
     ap.add_argument("--format", default="", choices=["", "csr", "sell", "dia"],
@@ -494,7 +497,7 @@ def main():
         net = A
         dopts = dict(lanczos_steps=w["lanczos"], rtol=1e-8, check_every=args.check_every or 8,
                      use_graphs=max(args.graphs, 0),
-                     maxit=5000, lowrank=args.lowrank)
+                     maxit=5000, lowrank=args.lowrank, poly=args.poly)
         if args.k_sweep:
             return run_dfn_sweep(args, w, net, dopts, dev)
         S = P.SchurSolver(net, device=dev, k=k, **dopts)
@@ -504,7 +507,8 @@ def main():
     check_every = args.check_every if args.check_every > 0 else w.get("check_every", 8)
     opts = dict(k=k, lanczos_steps=w["lanczos"], format=w["fmt"], apply_prec=w["prec"], rtol=1e-8,
                 check_every=check_every, use_graphs=graphs, flexible=w.get("flexible", 0),
-                sell_variant=args.sell_variant, sell_C=args.sell_C, sell_sigma=args.sell_sigma, lowrank=args.lowrank)
+                sell_variant=args.sell_variant, sell_C=args.sell_C, sell_sigma=args.sell_sigma, lowrank=args.lowrank,
+                poly=args.poly)
     rp, ci, va = P.to_device_csr(A, dev)
     tune = None
     if not args.no_autotune and not args.format and w["fmt"] == "sell":

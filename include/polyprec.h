@@ -64,6 +64,8 @@ extern "C" {
                                  indices (banded / structured-grid matrices with
                                  at most 16 distinct upper offsets and
                                  symmetric values); PP_EUNSUPPORTED otherwise */
+#define PP_POLY_CHEB 0        /* Algorithm 2 (three-term recurrence)           */
+#define PP_POLY_NEWTON 1      /* Algorithm 1 (Newton form, degree 2^nlev - 1)  */
 #define PP_PREC_F64 0         /* p_k applied in FP64                           */
 #define PP_PREC_F32 1         /* p_k applied with FP32 values and vectors      */
 #define PP_PREC_BF16 2        /* p_k applied with BF16 values, FP32 vectors    */
@@ -115,6 +117,10 @@ typedef struct {
                          Workspace: (lowrank_steps + 1 + p) n doubles
                          more.  0: no correction                           */
   int lowrank_steps;  /* Lanczos steps for those vectors, >= lowrank; 0: 30 */
+  int poly;           /* PP_POLY_CHEB: the three-term recurrence of
+                         Algorithm 2; PP_POLY_NEWTON: the Newton form of
+                         Algorithm 1 (k = 2^nlev - 1, FP64 apply only;
+                         2 nlev n doubles more workspace)                  */
 } pp_options;
 
 typedef struct {

@@ -150,6 +150,11 @@ int validate_options(pp_ctx* c, const pp_options* o) {
   if (o->sell_variant < 0 || o->sell_variant > 2) return fail(c, PP_EINVAL, "sell_variant must be 0, 1 or 2");
   if (o->lowrank < 0 || o->lowrank > kMaxLowRank) return fail(c, PP_EINVAL, "lowrank must be in [0, 32]");
   if (o->flexible < 0 || o->flexible > kMaxFcg) return fail(c, PP_EINVAL, "flexible must be in [0, 8]");
+  if (o->poly != PP_POLY_CHEB && o->poly != PP_POLY_NEWTON) return fail(c, PP_EINVAL, "poly must be CHEB or NEWTON");
+  if (o->poly == PP_POLY_NEWTON && (newton_levels(o->k) < 0 || o->k > 16383))
+    return fail(c, PP_EINVAL, "the Newton form needs k = 2^nlev - 1 <= 16383");
+  if (o->poly == PP_POLY_NEWTON && o->apply_prec != PP_PREC_F64)
+    return fail(c, PP_EUNSUPPORTED, "the Newton form is applied in FP64 only");
   if (o->lowrank > 0 && o->lowrank_steps != 0 && (o->lowrank_steps < o->lowrank || o->lowrank_steps > kMaxLanczos))
     return fail(c, PP_EINVAL, "lowrank > 0 needs lowrank <= lowrank_steps <= 512 (0: 30)");
   if (o->lowrank > 30 && o->lowrank_steps == 0)
@@ -371,6 +376,9 @@ size_t layout(pp_ctx* c, void* base, const SellPlan& P) {
     c->v32 = B.take<float>(n_pad);
     c->z32 = B.take<float>(n_pad);
   }
+  c->newton_buf = c->opt.poly == PP_POLY_NEWTON && newton_levels(c->opt.k) > 0
+                      ? B.take<double>(2LL * newton_levels(c->opt.k) * n_pad)
+                      : nullptr;
   c->fcg_m = c->opt.flexible >= 2 ? c->opt.flexible : 0;
   if (c->fcg_m) {
     c->Pring = B.take<double>((long long)c->fcg_m * n_pad);

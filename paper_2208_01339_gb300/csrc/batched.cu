@@ -963,6 +963,8 @@ int check_batch_opts(const pp_options* o) {
   int rc = validate_options(nullptr, o);
   if (rc == PP_OK && o->lowrank != 0)
     rc = fail(nullptr, PP_EUNSUPPORTED, "the low-rank correction is not available for batch contexts");
+  if (rc == PP_OK && o->poly != PP_POLY_CHEB)
+    rc = fail(nullptr, PP_EUNSUPPORTED, "pp_batch: the Chebyshev recurrence only");
   if (rc == PP_OK && o->flexible > 1)
     rc = fail(nullptr, PP_EUNSUPPORTED, "pp_batch: flexible must be 0 or 1 (FCG(1))");
   if (rc) return rc;

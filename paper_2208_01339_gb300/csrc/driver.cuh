@@ -46,6 +46,14 @@ void destroy_ctx_resources(pp_ctx* c);
 // batched.cu
 void batch_free(pp_batch_state* b);
 
+// newton.cu: Algorithm 1 (Newton form of the polynomial)
+int newton_levels(int k);  // nlev with k = 2^nlev - 1, or -1
+void newton_coeffs(pp_ctx* c);
+long long newton_launches(const pp_ctx* c);
+cudaError_t newton_apply(pp_ctx* c, const Scalars* skip, const double* r, double* z, cudaStream_t s);
+cudaError_t newton_dots(pp_ctx* c, const Scalars* skip, const double* z, const double* r, const double* q,
+                        double* rz_out, double* zq_out, cudaStream_t s);
+
 // fcg.cu: FCG(m) window products and direction update
 cudaError_t fcg_dots(pp_ctx* c, int s_cur, cudaStream_t s);
 cudaError_t fcg_update_p(pp_ctx* c, int s_cur, int s_new, int first, cudaStream_t s);
@@ -111,6 +119,9 @@ struct pp_ctx {
   // truncated flexible CG, FCG(m) for m = opt.flexible >= 2: ring of the last
   // m directions P and their products Q = A P (slot j at j * n_pad)
   int fcg_m = 0;
+  // Newton form (Algorithm 1): zeta_0..zeta_nlev and 2 nlev level vectors
+  std::vector<double> zeta;
+  double* newton_buf = nullptr;
   double *Pring = nullptr, *Qring = nullptr, *fcg_part = nullptr;
   double lr_ritz_resid = 0;
   std::vector<double> lr_theta;  // Rayleigh quotients v^T A_hat v of the vectors

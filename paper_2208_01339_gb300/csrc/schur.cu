@@ -624,6 +624,9 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
   c->t1 = B.take<double>(n_pad);
   c->t2 = B.take<double>(n_pad);
   c->bh = B.take<double>(n_pad);
+  c->newton_buf = c->opt.poly == PP_POLY_NEWTON && newton_levels(c->opt.k) > 0
+                      ? B.take<double>(2LL * newton_levels(c->opt.k) * n_pad)
+                      : nullptr;
   c->fcg_m = c->opt.flexible >= 2 ? c->opt.flexible : 0;
   if (c->fcg_m) {
     c->Pring = B.take<double>((long long)c->fcg_m * n_pad);

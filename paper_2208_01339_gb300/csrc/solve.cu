@@ -97,7 +97,12 @@ cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s, cudaEvent_t 
   const double* qd = nodot ? nullptr : q;
   cudaError_t e = lr ? lowrank_coefs(c, skip, c->r, s) : cudaSuccess;
   if (e != cudaSuccess) return e;
-  if (c->opt.k == 0) {
+  if (c->opt.poly == PP_POLY_NEWTON) {
+    if (ev0) e = cudaEventRecord(ev0, s);
+    if (e == cudaSuccess) e = newton_apply(c, skip, c->r, c->z, s);
+    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess && !nodot) e = newton_dots(c, skip, c->z, c->r, qd, rz, &sc->zq, s);
+  } else if (c->opt.k == 0) {
     if (ev0) e = cudaEventRecord(ev0, s);
     if (e == cudaSuccess)
       e = vec_scale_dot(L, c->n, skip, c->r, c->z, kF64, 1.0 / c->theta_bar, c->r, qd, rz, &sc->zq,
@@ -148,6 +153,7 @@ namespace {
 long long precond_launches(const pp_ctx* c) {
   const long long k = c->opt.k;
   long long n = k == 0 ? 1 : (c->mixed ? k * c->op_launches + 2 : k * c->op_launches);
+  if (c->opt.poly == PP_POLY_NEWTON) n = newton_launches(c) + ((c->lr_p > 0 || c->fcg_m > 0) ? 0 : 1);
   if (c->lr_p > 0) n += 3;
   return n;
 }
@@ -287,6 +293,7 @@ int setup_interval_and_coeffs(pp_ctx* c, cudaStream_t s) {
     c->rho.assign((size_t)c->opt.k + 2, 0.0);
     if (polyprec_coeffs(lo, hi, c->xi, c->opt.k, &c->theta_bar, &c->delta, &c->sigma_bar, c->rho.data()) != PP_OK)
       return fail(c, PP_EINVAL, "invalid spectral interval for the coefficients");
+    if (c->opt.poly == PP_POLY_NEWTON) newton_coeffs(c);
     return PP_OK;
   };
   int rc = set_coeffs(a, b);
@@ -355,7 +362,9 @@ extern "C" int polyprec_apply(pp_ctx* c, const double* r, double* z, int nrhs, v
       if (e == cudaSuccess && c->mixed) e = vec_convert(L, c->n, c->r, kF64, c->r32, kF32, nullptr);
       if (e == cudaSuccess) e = lowrank_coefs(c, nullptr, c->r, s);
       if (e == cudaSuccess) {
-        if (c->opt.k == 0)
+        if (c->opt.poly == PP_POLY_NEWTON)
+          e = newton_apply(c, nullptr, c->r, c->z, s);
+        else if (c->opt.k == 0)
           e = vec_scale_dot(L, c->n, nullptr, rin, zin, prec, 1.0 / c->theta_bar, nullptr, nullptr, nullptr, nullptr,
                             nullptr);
         else
@@ -369,7 +378,9 @@ extern "C" int polyprec_apply(pp_ctx* c, const double* r, double* z, int nrhs, v
       continue;
     }
     cudaError_t e = vec_scale_in(L, c->n, c->n_pad, c->w, c->perm, rj, rin, prec, nullptr, nullptr);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && c->opt.poly == PP_POLY_NEWTON) {
+      e = newton_apply(c, nullptr, (const double*)rin, (double*)zin, s);
+    } else if (e == cudaSuccess) {
       if (c->opt.k == 0)
         e = vec_scale_dot(L, c->n, nullptr, rin, zin, prec, 1.0 / c->theta_bar, nullptr, nullptr, nullptr, nullptr,
                           nullptr);

@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
                 ("flexible", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("zero_guess", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("sell_variant", ctypes.c_int), ("lowrank", ctypes.c_int),
-                ("lowrank_steps", ctypes.c_int)]
+                ("lowrank_steps", ctypes.c_int), ("poly", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -195,6 +195,8 @@ def make_options(**kw) -> Options:
             v = FORMAT[v] if isinstance(v, str) else v
         elif key == "apply_prec":
             v = PREC[v] if isinstance(v, str) else v
+        elif key == "poly":
+            v = {"cheb": 0, "newton": 1}[v] if isinstance(v, str) else v
         elif key == "seed_scaling":
             v = SEED[v] if isinstance(v, str) else (1 if v is True else (0 if v is False else v))
         elif isinstance(v, bool):
