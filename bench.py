@@ -44,7 +44,9 @@ WORKLOADS = {
     # 32^3 Poisson is L2-resident and launch-bound: 10-iteration blocks replayed as CUDA graphs
     "poisson32": dict(N=32, sigma=0.0, seed=0, rhs="ones_noise", k=20, lanczos=10, fmt="csr", prec="f64",
                       graphs=1, check_every=10),
-    "dfn200": dict(dfn=True, seed=2, k=40, lanczos=10, prec="f64"),
+    # fracture network: the time to rtol is flat over k = 1..7 (products dominate); k = 3 with a
+    # 30-step Lanczos interval is the fastest measured setting
+    "dfn200": dict(dfn=True, seed=2, k=3, lanczos=30, prec="f64"),
     "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32"),
 }
 METRIC = "PCG time-to-rtol-1e-8 (s) and polyprec_apply HBM GB/s vs plain FP64, 1 GB300"
@@ -247,8 +249,9 @@ def run_reference(args, w, rank):
     sample = (f"1 PCG iteration's operator work (p_{k} apply + 1 product by A_hat) on the full {A.n}-row matrix, "
               f"single thread, x {iters} iterations ({src})")
     out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": t_it * 1e3, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "warmup": args.warmup, "ms_per_step": value * 1e3 if value else None, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "oracle_ms_per_iteration": t_it * 1e3,
            "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "k": k},
            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
