@@ -20,7 +20,8 @@ sys.path.insert(0, ROOT)
 import oracle as O  # noqa: E402
 from paper_2208_01339_gb300 import inputs as I  # noqa: E402
 
-CASES = [("poisson32", 20, 10), ("diffusion192", 5, 10), ("diffusion192", 20, 10), ("diffusion192", 5, 60)]
+CASES = [("poisson32", 20, 10), ("diffusion192", 5, 10), ("diffusion192", 20, 10), ("diffusion192", 5, 60),
+         ("diffusion192", 20, 60)]
 
 
 def problem(name):
