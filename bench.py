@@ -49,6 +49,8 @@ WORKLOADS = {
     # fracture network: the time to rtol is flat over k = 1..7 (products dominate); k = 3 with a
     # 30-step Lanczos interval is the fastest measured setting
     "dfn200": dict(dfn=True, seed=2, k=3, lanczos=30, prec="f64"),
+    # p_k(S_hat) with the FP32 copy of the trace blocks, outer FP64 FCG(1)
+    "dfn200_f32": dict(dfn=True, seed=2, k=15, lanczos=30, prec="f32", flexible=1),
     "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32"),
 }
 METRIC = "PCG time-to-rtol-1e-8 (s) and polyprec_apply HBM GB/s vs plain FP64, 1 GB300"
@@ -417,7 +419,7 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
     if rank == 0:
         out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "vs_baseline": None, "dtype": w["prec"], "data": "synthetic",
                "config": {"workload": args.workload, "n_f": net.n_f, "n_h": net.n_h, "n_u": net.n_u, "k": k,
                           "trace_block_entries": info["nnz"], "alpha_reg": net.alpha,
                           "lanczos_steps": w["lanczos"], "lowrank": args.lowrank},
@@ -502,7 +504,7 @@ def main():
     if w.get("dfn"):
         net = A
         dopts = dict(lanczos_steps=w["lanczos"], rtol=1e-8, check_every=args.check_every or 8,
-                     use_graphs=max(args.graphs, 0),
+                     use_graphs=max(args.graphs, 0), apply_prec=w["prec"], flexible=w.get("flexible", 0),
                      maxit=5000, lowrank=args.lowrank, poly=args.poly)
         if args.k_sweep:
             return run_dfn_sweep(args, w, net, dopts, dev)

@@ -286,7 +286,9 @@ int pp_schur_workspace_size(const pp_dfn* d, const pp_options* opt, size_t* byte
 /* Schur context: D_S = diag(S_u) by Algorithm 4 (restricted to the trace
  * rows that C, B and G^h touch), the scaling S_hat = D_S^{-1/2} S_u
  * D_S^{-1/2}, the Lanczos interval of S_hat and the coefficients.
- * Synchronous. */
+ * apply_prec = PP_PREC_F32 applies p_k(S_hat) with an FP32 copy of the
+ * trace blocks and FP32 vectors (use flexible >= 1); the outer products,
+ * D_S and the interval stay FP64.  BF16 is PP_EUNSUPPORTED.  Synchronous. */
 int schur_setup(pp_ctx** ctx, const pp_dfn* d, const pp_options* opt, void* workspace,
                 size_t ws_bytes, void* stream);
 

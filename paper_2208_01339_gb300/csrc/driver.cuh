@@ -68,7 +68,8 @@ cudaError_t lowrank_update(pp_ctx* c, const Scalars* skip, double* z, const doub
                            double* rz_out, double* zq_out, cudaStream_t s);
 
 // schur.cu
-cudaError_t schur_scaled_step(pp_ctx* c, const StepParams& p, const Scalars* skip, unsigned int* counter,
+// lp = true: the FP32 operator (the preconditioner's degree steps, FP32 vectors)
+cudaError_t schur_scaled_step(pp_ctx* c, bool lp, const StepParams& p, const Scalars* skip, unsigned int* counter,
                               cudaStream_t s);
 void schur_free(SchurImpl* s);
 

@@ -60,6 +60,10 @@ struct SchurImpl {
   DCsr C, B, Gh, CT, BT;
   // scratch
   double *vT = nullptr, *zT = nullptr, *tT = nullptr, *wT = nullptr, *gT = nullptr, *w2T = nullptr;
+  // FP32 copy of M and FP32 trace-space scratch for the preconditioner applied
+  // in FP32 (apply_prec = F32; the outer products stay FP64)
+  float* M32 = nullptr;
+  float *vT32 = nullptr, *zT32 = nullptr, *tT32 = nullptr, *wT32 = nullptr, *gT32 = nullptr, *w2T32 = nullptr;
   double *fa = nullptr, *fb = nullptr, *fc = nullptr, *fd = nullptr;
   double* ds = nullptr;  // diag(S_u)
 };
@@ -208,17 +212,19 @@ __global__ void schur_diag_kernel(int n_u, int nf, const long long* toff, const 
 
 // ------------------------------------------------------------ apply --------
 // vT = C_T (w o x), zT = B_T (w o x): trace-space gathers (thread per row).
+// T is the vector type: double, or float for the FP32 preconditioner.
+template <typename T>
 __global__ void trace_gather_kernel(int n_T, DCsr C_T, DCsr B_T, const double* __restrict__ w,
-                                    const double* __restrict__ x, double* __restrict__ vT, double* __restrict__ zT) {
+                                    const T* __restrict__ x, T* __restrict__ vT, T* __restrict__ zT) {
   for (long long r = gtid(); r < n_T; r += gstride()) {
-    double v = 0.0, z = 0.0;
+    T v = (T)0, z = (T)0;
     for (int p = C_T.rowptr[r]; p < C_T.rowptr[r + 1]; ++p) {
       const int c = C_T.col[p];
-      v += C_T.val[p] * (w ? w[c] * x[c] : x[c]);
+      v += (T)C_T.val[p] * (w ? (T)w[c] * x[c] : x[c]);
     }
     for (int p = B_T.rowptr[r]; p < B_T.rowptr[r + 1]; ++p) {
       const int c = B_T.col[p];
-      z += B_T.val[p] * (w ? w[c] * x[c] : x[c]);
+      z += (T)B_T.val[p] * (w ? (T)w[c] * x[c] : x[c]);
     }
     vT[r] = v;
     zT[r] = z;
@@ -226,36 +232,44 @@ __global__ void trace_gather_kernel(int n_T, DCsr C_T, DCsr B_T, const double* _
 }
 
 // gT = Gh_T tT
-__global__ void trace_gh_kernel(int n_T, DCsr Gh_T, const double* __restrict__ tT, double* __restrict__ gT) {
+template <typename T>
+__global__ void trace_gh_kernel(int n_T, DCsr Gh_T, const T* __restrict__ tT, T* __restrict__ gT) {
   for (long long r = gtid(); r < n_T; r += gstride()) {
-    double g = 0.0;
-    for (int p = Gh_T.rowptr[r]; p < Gh_T.rowptr[r + 1]; ++p) g += Gh_T.val[p] * tT[Gh_T.col[p]];
+    T g = (T)0;
+    for (int p = Gh_T.rowptr[r]; p < Gh_T.rowptr[r + 1]; ++p) g += (T)Gh_T.val[p] * tT[Gh_T.col[p]];
     gT[r] = g;
   }
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
 // y_k = M x_k for NR right-hand sides: one warp per trace row, fixed order.
-template <int NR>
+template <int NR, typename T>
 __global__ void __launch_bounds__(kBlock) m_apply_kernel(int n_T, int nf, const long long* __restrict__ toff,
                                                          const long long* __restrict__ moff,
-                                                         const int* __restrict__ tfrac, const double* __restrict__ M,
-                                                         const double* __restrict__ x0, const double* __restrict__ x1,
-                                                         double* __restrict__ y0, double* __restrict__ y1) {
+                                                         const int* __restrict__ tfrac, const T* __restrict__ M,
+                                                         const T* __restrict__ x0, const T* __restrict__ x1,
+                                                         T* __restrict__ y0, T* __restrict__ y1) {
   const int lane = threadIdx.x & 31;
   const long long gw = gtid() >> 5, nw = gstride() >> 5;
   for (long long r = gw; r < n_T; r += nw) {
     const int f = tfrac[r];
     const long long t0 = toff[f];
     const int t = (int)(toff[f + 1] - t0);
-    const double* row = M + moff[f] + (r - t0) * t;
-    double a0 = 0.0, a1 = 0.0;
+    const T* row = M + moff[f] + (r - t0) * t;
+    T a0 = (T)0, a1 = (T)0;
     for (int b = lane; b < t; b += 32) {
-      const double m = __ldcs(row + b);
+      const T m = __ldcs(row + b);
       a0 = fma(m, __ldg(x0 + t0 + b), a0);
       if (NR > 1) a1 = fma(m, __ldg(x1 + t0 + b), a1);
     }
-    a0 = warp_sum(a0);
-    if (NR > 1) a1 = warp_sum(a1);
+    a0 = warp_sum_t(a0);
+    if (NR > 1) a1 = warp_sum_t(a1);
     if (lane == 0) {
       y0[r] = a0;
       if (NR > 1) y1[r] = a1;
@@ -265,41 +279,41 @@ __global__ void __launch_bounds__(kBlock) m_apply_kernel(int n_T, int nf, const 
 
 // Final sparse products in u space fused with the caller's step epilogue:
 // s = w o (G^u (w o x) - alpha (BT_T t + CT_T w1) + CT_T w2) = (S_hat x)_row.
-template <int MODE, int NDOT>
+template <int MODE, int NDOT, typename T>
 __global__ void __launch_bounds__(kBlock) schur_final_kernel(int n_u, DCsr Gu, DCsr BT_T, DCsr CT_T, double alpha,
-                                                             const double* __restrict__ w, const double* __restrict__ tT,
-                                                             const double* __restrict__ wT,
-                                                             const double* __restrict__ w2T, StepArgs<double> a,
-                                                             const Scalars* sc, double* partials,
+                                                             const double* __restrict__ w, const T* __restrict__ tT,
+                                                             const T* __restrict__ wT, const T* __restrict__ w2T,
+                                                             StepArgs<T> a, const Scalars* sc, double* partials,
                                                              unsigned int* counter) {
   if (sc && load_done(sc)) return;
   double dot[NDOT > 0 ? NDOT : 1];
   for (int i = 0; i < (NDOT > 0 ? NDOT : 1); ++i) dot[i] = 0.0;
-  const double lan = lanczos_coef<double, MODE>(a);
+  const T lan = lanczos_coef<T, MODE>(a);
+  const T al = (T)alpha;
   for (long long i = gtid(); i < n_u; i += gstride()) {
-    double gu = 0.0, bt = 0.0, ct = 0.0;
+    T gu = (T)0, bt = (T)0, ct = (T)0;
     for (int p = Gu.rowptr[i]; p < Gu.rowptr[i + 1]; ++p) {
       const int c = Gu.col[p];
-      gu += Gu.val[p] * (w ? w[c] * a.x[c] : a.x[c]);
+      gu += (T)Gu.val[p] * (w ? (T)w[c] * a.x[c] : a.x[c]);
     }
-    for (int p = BT_T.rowptr[i]; p < BT_T.rowptr[i + 1]; ++p) bt += BT_T.val[p] * tT[BT_T.col[p]];
+    for (int p = BT_T.rowptr[i]; p < BT_T.rowptr[i + 1]; ++p) bt += (T)BT_T.val[p] * tT[BT_T.col[p]];
     for (int p = CT_T.rowptr[i]; p < CT_T.rowptr[i + 1]; ++p) {
       const int c = CT_T.col[p];
-      ct += CT_T.val[p] * (w2T[c] - alpha * wT[c]);
+      ct += (T)CT_T.val[p] * (w2T[c] - al * wT[c]);
     }
-    double s = gu - alpha * bt + ct;
-    if (w) s *= w[i];
-    double xs = 0.0, rs = 0.0, xo = 0.0;
+    T s = gu - al * bt + ct;
+    if (w) s *= (T)w[i];
+    T xs = (T)0, rs = (T)0, xo = (T)0;
     if constexpr (mode_needs_xown<MODE, NDOT>()) xs = a.x[i];
     if constexpr (mode_needs_r<MODE>()) rs = a.r[i];
     if constexpr (mode_needs_xold<MODE>()) {
       if (MODE == kChebK || a.xold) xo = a.xold[i];
     }
-    const double y = row_value<double, MODE>(a, s, xs, rs, xo, lan);
+    const T y = row_value<T, MODE>(a, s, xs, rs, xo, lan);
     a.y[i] = y;
-    row_dots<double, MODE, NDOT>(a, i, y, xs, rs, dot);
+    row_dots<T, MODE, NDOT>(a, i, y, xs, rs, dot);
   }
-  finish_dots<double, NDOT>(a, dot, partials, counter);
+  finish_dots<T, NDOT>(a, dot, partials, counter);
 }
 
 // ------------------------------------------------ fast diagonalisation ----
@@ -615,6 +629,16 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
   S->fb = B.take<double>(d->n_h);
   S->fc = B.take<double>(d->n_h);
   S->fd = B.take<double>(d->n_h);
+  c->mixed = c->opt.apply_prec == PP_PREC_F32;
+  if (c->mixed) {
+    S->M32 = B.take<float>(P.m_elems);
+    S->vT32 = B.take<float>(P.n_T);
+    S->zT32 = B.take<float>(P.n_T);
+    S->tT32 = B.take<float>(P.n_T);
+    S->wT32 = B.take<float>(P.n_T);
+    S->gT32 = B.take<float>(P.n_T);
+    S->w2T32 = B.take<float>(P.n_T);
+  }
   c->vec_begin = B.here();
   c->xh = B.take<double>(n_pad);
   c->r = B.take<double>(n_pad);
@@ -624,6 +648,12 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
   c->t1 = B.take<double>(n_pad);
   c->t2 = B.take<double>(n_pad);
   c->bh = B.take<double>(n_pad);
+  if (c->mixed) {
+    c->r32 = B.take<float>(n_pad);
+    c->u32 = B.take<float>(n_pad);
+    c->v32 = B.take<float>(n_pad);
+    c->z32 = B.take<float>(n_pad);
+  }
   c->newton_buf = c->opt.poly == PP_POLY_NEWTON && newton_levels(c->opt.k) > 0
                       ? B.take<double>(2LL * newton_levels(c->opt.k) * n_pad)
                       : nullptr;
@@ -655,52 +685,92 @@ cudaError_t ainv_full(const SchurImpl* S, const double* v, double* y, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t m_apply(const SchurImpl* S, const double* x0, const double* x1, double* y0, double* y1, cudaStream_t s) {
+template <typename T>
+cudaError_t m_apply(const SchurImpl* S, const T* M, const T* x0, const T* x1, T* y0, T* y1, cudaStream_t s) {
   const int g = grid_of((long long)S->n_T * 32);
   if (x1)
-    m_apply_kernel<2><<<g, kBlock, 0, s>>>(S->n_T, S->n_f, S->toff, S->moff, S->tfrac, S->M, x0, x1, y0, y1);
+    m_apply_kernel<2, T><<<g, kBlock, 0, s>>>(S->n_T, S->n_f, S->toff, S->moff, S->tfrac, M, x0, x1, y0, y1);
   else
-    m_apply_kernel<1><<<g, kBlock, 0, s>>>(S->n_T, S->n_f, S->toff, S->moff, S->tfrac, S->M, x0, nullptr, y0, nullptr);
+    m_apply_kernel<1, T><<<g, kBlock, 0, s>>>(S->n_T, S->n_f, S->toff, S->moff, S->tfrac, M, x0, nullptr, y0, nullptr);
   return cudaGetLastError();
 }
 
-template <int MODE, int NDOT>
+cudaError_t m_apply(const SchurImpl* S, const double* x0, const double* x1, double* y0, double* y1, cudaStream_t s) {
+  return m_apply<double>(S, S->M, x0, x1, y0, y1, s);
+}
+
+// Trace-space scratch and M in the vector type T.
+template <typename T>
+struct SchurBufs;
+template <>
+struct SchurBufs<double> {
+  static const double* M(const SchurImpl* S) { return S->M; }
+  static double* v(const SchurImpl* S) { return S->vT; }
+  static double* z(const SchurImpl* S) { return S->zT; }
+  static double* t(const SchurImpl* S) { return S->tT; }
+  static double* w(const SchurImpl* S) { return S->wT; }
+  static double* g(const SchurImpl* S) { return S->gT; }
+  static double* w2(const SchurImpl* S) { return S->w2T; }
+};
+template <>
+struct SchurBufs<float> {
+  static const float* M(const SchurImpl* S) { return S->M32; }
+  static float* v(const SchurImpl* S) { return S->vT32; }
+  static float* z(const SchurImpl* S) { return S->zT32; }
+  static float* t(const SchurImpl* S) { return S->tT32; }
+  static float* w(const SchurImpl* S) { return S->wT32; }
+  static float* g(const SchurImpl* S) { return S->gT32; }
+  static float* w2(const SchurImpl* S) { return S->w2T32; }
+};
+
+template <int MODE, int NDOT, typename T>
 cudaError_t final_go(pp_ctx* c, const double* w, const StepParams& p, const Scalars* skip, unsigned int* counter,
                      cudaStream_t s) {
   SchurImpl* S = c->schur;
-  StepArgs<double> a = make_args<double>(p);
-  schur_final_kernel<MODE, NDOT><<<c->grid_vec, kBlock, 0, s>>>(S->n_u, S->Gu, S->BT_T, S->CT_T, S->alpha, w, S->tT,
-                                                                S->wT, S->w2T, a, skip, c->partials, counter);
+  using B = SchurBufs<T>;
+  StepArgs<T> a = make_args<T>(p);
+  schur_final_kernel<MODE, NDOT, T><<<c->grid_vec, kBlock, 0, s>>>(S->n_u, S->Gu, S->BT_T, S->CT_T, S->alpha, w,
+                                                                   B::t(S), B::w(S), B::w2(S), a, skip, c->partials,
+                                                                   counter);
   return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, typename T>
 cudaError_t final_ndot(pp_ctx* c, const double* w, const StepParams& p, const Scalars* skip, unsigned int* counter,
                        cudaStream_t s) {
-  if (p.ndot == 0) return final_go<MODE, 0>(c, w, p, skip, counter, s);
-  if (p.ndot == 1) return final_go<MODE, 1>(c, w, p, skip, counter, s);
-  return final_go<MODE, 2>(c, w, p, skip, counter, s);
+  if constexpr (std::is_same<T, float>::value) {
+    // the FP32 operator serves the preconditioner's degree steps only
+    if (p.ndot != 0 || !(MODE == kCheb1 || MODE == kCheb2 || MODE == kChebK)) return cudaErrorNotSupported;
+    return final_go<MODE, 0, T>(c, w, p, skip, counter, s);
+  } else {
+    if (p.ndot == 0) return final_go<MODE, 0, T>(c, w, p, skip, counter, s);
+    if (p.ndot == 1) return final_go<MODE, 1, T>(c, w, p, skip, counter, s);
+    return final_go<MODE, 2, T>(c, w, p, skip, counter, s);
+  }
 }
 
 // Operator step with the (optionally scaled) Schur complement: the five
 // launches described at the top of this file.  w = nullptr gives S_u itself.
+// T = float runs the whole step on the FP32 copy of M (preconditioner only).
+template <typename T>
 cudaError_t schur_step(pp_ctx* c, const double* w, const StepParams& p, const Scalars* skip, unsigned int* counter,
                        cudaStream_t s) {
   SchurImpl* S = c->schur;
-  const double* x = static_cast<const double*>(p.x);
-  trace_gather_kernel<<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->C_T, S->B_T, w, x, S->vT, S->zT);
-  cudaError_t e = m_apply(S, S->vT, S->zT, S->tT, S->wT, s);  // [t, w] = A^{-1} [v, z]
+  using B = SchurBufs<T>;
+  const T* x = static_cast<const T*>(p.x);
+  trace_gather_kernel<T><<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->C_T, S->B_T, w, x, B::v(S), B::z(S));
+  cudaError_t e = m_apply<T>(S, B::M(S), B::v(S), B::z(S), B::t(S), B::w(S), s);  // [t, w] = A^{-1} [v, z]
   if (e != cudaSuccess) return e;
-  trace_gh_kernel<<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->Gh_T, S->tT, S->gT);  // v = G^h t
-  e = m_apply(S, S->gT, nullptr, S->w2T, nullptr, s);                                  // w = A^{-1} v
+  trace_gh_kernel<T><<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->Gh_T, B::t(S), B::g(S));  // v = G^h t
+  e = m_apply<T>(S, B::M(S), B::g(S), nullptr, B::w2(S), nullptr, s);                        // w = A^{-1} v
   if (e != cudaSuccess) return e;
   switch (p.mode) {
-    case kSpmv: return final_ndot<kSpmv>(c, w, p, skip, counter, s);
-    case kResid: return final_ndot<kResid>(c, w, p, skip, counter, s);
-    case kCheb1: return final_ndot<kCheb1>(c, w, p, skip, counter, s);
-    case kCheb2: return final_ndot<kCheb2>(c, w, p, skip, counter, s);
-    case kChebK: return final_ndot<kChebK>(c, w, p, skip, counter, s);
-    case kLanczos: return final_ndot<kLanczos>(c, w, p, skip, counter, s);
+    case kSpmv: return final_ndot<kSpmv, T>(c, w, p, skip, counter, s);
+    case kResid: return final_ndot<kResid, T>(c, w, p, skip, counter, s);
+    case kCheb1: return final_ndot<kCheb1, T>(c, w, p, skip, counter, s);
+    case kCheb2: return final_ndot<kCheb2, T>(c, w, p, skip, counter, s);
+    case kChebK: return final_ndot<kChebK, T>(c, w, p, skip, counter, s);
+    case kLanczos: return final_ndot<kLanczos, T>(c, w, p, skip, counter, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -710,9 +780,10 @@ cudaError_t schur_step(pp_ctx* c, const double* w, const StepParams& p, const Sc
 
 namespace pp {
 
-cudaError_t schur_scaled_step(pp_ctx* c, const StepParams& p, const Scalars* skip, unsigned int* counter,
+cudaError_t schur_scaled_step(pp_ctx* c, bool lp, const StepParams& p, const Scalars* skip, unsigned int* counter,
                               cudaStream_t s) {
-  return schur_step(c, c->w, p, skip, counter, s);
+  if (lp) return schur_step<float>(c, c->w, p, skip, counter, s);
+  return schur_step<double>(c, c->w, p, skip, counter, s);
 }
 
 void schur_free(SchurImpl* s) { delete s; }
@@ -745,7 +816,8 @@ int prepare(pp_ctx* c, SchurImpl* S, const pp_dfn* d, TracePlan& P, void* base, 
 int check_schur_opts(const pp_options* o) {
   int rc = validate_options(nullptr, o);
   if (rc) return rc;
-  if (o->apply_prec != PP_PREC_F64) return fail(nullptr, PP_EUNSUPPORTED, "the Schur operator is applied in FP64 only");
+  if (o->apply_prec == PP_PREC_BF16)
+    return fail(nullptr, PP_EUNSUPPORTED, "the Schur operator is applied in FP64, or in FP32 inside p_k");
   return PP_OK;
 }
 
@@ -833,6 +905,8 @@ extern "C" int schur_setup(pp_ctx** out, const pp_dfn* d, const pp_options* opt,
   cheb_u_kernel<<<grid_of(S->u_elems), kBlock, 0, s>>>(S->n_f, S->nx, S->ny, S->loff, S->uoff, S->lam, S->U);
   m_blocks_kernel<<<grid_of(S->m_elems), kBlock, 0, s>>>(S->n_f, S->toff, S->moff, S->nx, S->ny, S->T, S->soff,
                                                          S->uoff, S->tloc, S->S, S->U, S->M);
+  if (c->mixed) e = sell_convert_values(S->m_elems, S->M, S->M32, kF32, s);  // M rounded to FP32
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "FP32 copy of M"));
   int* d_bad = reinterpret_cast<int*>(c->t1);
   e = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
   const size_t dsm = (size_t)std::max(S->max_t, 1) * sizeof(double);
@@ -884,7 +958,7 @@ extern "C" int schur_apply(pp_ctx* c, const double* r, double* y, void* stream) 
   p.mode = kSpmv;
   p.x = r;
   p.y = y;
-  cudaError_t e = schur_step(c, nullptr, p, nullptr, &c->sc->counters[kCntSchur], (cudaStream_t)stream);
+  cudaError_t e = schur_step<double>(c, nullptr, p, nullptr, &c->sc->counters[kCntSchur], (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "schur_apply");
   return PP_OK;
 }
@@ -916,7 +990,7 @@ extern "C" int schur_rhs(pp_ctx* c, const double* q, double* r, void* stream) {
   cudaError_t e = ainv_full(S, q, S->fa, s);
   if (e == cudaSuccess) {
     trace_restrict_kernel<<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->tnode, S->fa, S->tT);
-    trace_gh_kernel<<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->Gh_T, S->tT, S->gT);
+    trace_gh_kernel<double><<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->Gh_T, S->tT, S->gT);
     e = m_apply(S, S->gT, nullptr, S->w2T, nullptr, s);
   }
   if (e == cudaSuccess) {

@@ -21,7 +21,7 @@ namespace pp {
 
 cudaError_t op_step(pp_ctx* c, bool apply_matrix, const StepParams& p, const Scalars* skip, unsigned int* counter,
                     cudaStream_t s) {
-  if (c->kind == 1) return schur_scaled_step(c, p, skip, counter, s);
+  if (c->kind == 1) return schur_scaled_step(c, apply_matrix && c->mixed, p, skip, counter, s);
   StepParams q = p;
   q.err = &c->sc->dev_error;
   const bool lp = apply_matrix && c->mixed;

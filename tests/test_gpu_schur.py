@@ -141,10 +141,11 @@ def test_end_to_end_matches_dense_K0():
     assert rel(to_np(p), sol[nh + nu:]) <= 1e-9
 
 
-def test_schur_rejects_mixed_precision():
+def test_schur_rejects_bf16():
+    """FP32 trace blocks are supported inside p_k; BF16 is not."""
     net = I.tiny_fracture_network()
     with pytest.raises(P.PolyPrecError) as ei:
-        P.SchurSolver(net, apply_prec="f32")
+        P.SchurSolver(net, apply_prec="bf16", flexible=1)
     assert ei.value.status == P.PP_EUNSUPPORTED
 
 
@@ -170,3 +171,25 @@ def test_full_size_network_properties():
     assert st["status"] == 0
     res = to_np(r) - to_np(S.schur_apply(u))
     assert np.linalg.norm(res) / np.linalg.norm(to_np(r)) <= 1e-6
+
+
+@pytest.mark.parametrize("k", [3, 8])
+def test_fp32_schur_preconditioner(pair, k):
+    """p_k(S_hat) applied with the FP32 copy of the trace blocks (FP32 vectors,
+    FP32 accumulation): within FP32 rounding of the FP64 apply; the outer
+    flexible CG in FP64 still reaches the FP64 oracle's solution."""
+    net, ref = pair
+    S64 = P.SchurSolver(net, k=k, interval="given", alpha=0.05, beta=2.5, xi=1e-3)
+    S32 = P.SchurSolver(net, k=k, interval="given", alpha=0.05, beta=2.5, xi=1e-3, apply_prec="f32", flexible=1)
+    r = I.rhs_normal(net.n_u, 9)
+    z64 = to_np(S64.apply(dev(r)))
+    z32 = to_np(S32.apply(dev(r)))
+    assert rel(z32, z64) <= 1e-4
+    steps = min(10, net.n_u)
+    Sm = P.SchurSolver(net, k=k, lanczos_steps=steps, rtol=1e-10, maxit=800, apply_prec="f32", flexible=1)
+    rr = ref.rhs(net.q)
+    u, st = Sm.solve(dev(rr))
+    uo, so = ref.pcg(ref.diag(), rr, v0=I.lanczos_start(net.n_u, 0), k=k, lanczos_steps=steps, rtol=1e-12,
+                     maxit=5000)
+    assert st["status"] == 0 and so["status"] == 0
+    assert rel(to_np(u), uo) <= 1e-7
