@@ -312,11 +312,14 @@ void init_desc(pp_ctx* c, const pp_csr* A, const SellPlan& P, const DiaPlan& D) 
   c->A64.prec = kF64;
   if (c->A64.format == PP_FMT_DIA) {
     c->n_pad = ((long long)A->n + 127) / 128 * 128;
-    c->A64.ndiag = D.nd;
-    for (int t = 0; t < kMaxDiag; ++t) c->A64.doff[t] = t < D.nd ? D.doff[t] : 0;
+    // with the Jacobi seed the scaled diagonal is 1 by construction: not stored
+    const int unit = c->opt.seed_scaling == PP_SEED_JACOBI ? 1 : 0;
+    c->A64.dia_unit = unit;
+    c->A64.ndiag = D.nd - unit;
+    for (int t = 0; t < kMaxDiag; ++t) c->A64.doff[t] = t < D.nd - unit ? D.doff[t + unit] : 0;
     c->A64.dpad = D.dpad;
     c->A64.dstride = D.dpad + c->n_pad;
-    c->nnz_pad = (long long)D.nd * c->A64.dstride;
+    c->nnz_pad = (long long)std::max(1, D.nd - unit) * c->A64.dstride;
   } else if (c->A64.format == PP_FMT_SELL) {
     c->A64.C = P.C;
     c->A64.nslices = P.nslices;

@@ -43,12 +43,15 @@ struct MatDesc {
   int csr_group;         // CSR: lanes per row (1, 8, 32)
   int prec;
   int tma;               // SELL: stage slices through shared memory with cp.async.bulk
-  // DIA (symmetric; rows in natural order): the main diagonal and the upper
-  // diagonals t = 0..ndiag-1 at offsets doff[t] (doff[0] = 0).  Entry
-  // (i, i + doff[t]) sits at val[t * dstride + dpad + i]; positions
-  // -dpad..-1 and entries outside the matrix hold 0.  Row i takes its lower
-  // entries (i, i - doff[t]) from val[t * dstride + dpad + i - doff[t]].
+  // DIA (symmetric; rows in natural order): the stored diagonals t =
+  // 0..ndiag-1 at offsets doff[t] -- the main diagonal (doff[0] = 0) and the
+  // upper ones, or, with dia_unit = 1 (Jacobi-scaled matrix, whose diagonal
+  // is 1 by construction), the upper ones only.  Entry (i, i + doff[t]) sits
+  // at val[t * dstride + dpad + i]; positions -dpad..-1 and entries outside
+  // the matrix hold 0.  Row i takes its lower entries (i, i - doff[t]) from
+  // val[t * dstride + dpad + i - doff[t]].
   int ndiag;
+  int dia_unit;
   int doff[kMaxDiag];
   long long dstride, dpad;
 };

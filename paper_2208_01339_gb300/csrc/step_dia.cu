@@ -15,6 +15,7 @@ namespace {
 
 struct DiaArgs {
   int nd;
+  int unit;  // 1: the main diagonal is 1 and not stored
   int doff[kMaxDiag];
   long long dstride, dpad, n_pad;
 };
@@ -132,8 +133,11 @@ __device__ __forceinline__ void ldvals(const TV* p, TX (&o)[R]) {
   }
 }
 
-// ND > 0: that many stored diagonals, unrolled; ND = 0: d.nd at run time.
-template <typename TV, typename TX, int R, int ND, int MODE, int NDOT>
+// ND > 0: that many stored diagonals, unrolled, the main one first unless
+// UNIT; ND = 0: d.nd and d.unit at run time.  UNIT (the Jacobi-scaled matrix,
+// whose diagonal is 1 by construction) starts each row sum from x_i and
+// saves one multiply per row and one stored diagonal.
+template <typename TV, typename TX, int R, int ND, int MODE, int NDOT, bool UNIT = false>
 __global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* __restrict__ val, StepArgs<TX> a,
                                                           const Scalars* sc, double* partials,
                                                           unsigned int* counter) {
@@ -149,12 +153,21 @@ __global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* _
        i0 += (long long)gridDim.x * blockDim.x * R) {
     TX xs[R], acc[R], u[R];
     Vec<TX, R>::ld(a.x + i0, xs);
-    ldvals<TV, TX, R>(base + i0, u);
+    const bool unit = ND > 0 ? UNIT : (d.unit != 0);
+    if (unit) {
 #pragma unroll
-    for (int e = 0; e < R; ++e) acc[e] = u[e] * xs[e];
+      for (int e = 0; e < R; ++e) acc[e] = xs[e];
+    } else {
+      ldvals<TV, TX, R>(base + i0, u);
 #pragma unroll
-    for (int t = 1; t < (ND > 0 ? ND : kMaxDiag); ++t) {
-      if (ND == 0 && t >= nd) break;
+      for (int e = 0; e < R; ++e) acc[e] = u[e] * xs[e];
+    }
+#pragma unroll
+    for (int t = (ND > 0 ? (UNIT ? 0 : 1) : 0); t < (ND > 0 ? ND : kMaxDiag); ++t) {
+      if (ND == 0 && (t >= nd || (t == 0 && !unit))) {
+        if (t >= nd) break;
+        continue;
+      }
       const long long o = d.doff[t];
       const TV* vt = base + (long long)t * d.dstride;
       ldvals<TV, TX, R>(vt + i0, u);  // a(i, i + o); 0 past the last row
@@ -192,15 +205,15 @@ __global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* _
 // grid is taken per instantiation, capped by the caller's grid.
 constexpr int kWaves = 2;  // resident waves per launch (measured: 2 beats 1 and equals 3)
 
-template <typename TV, typename TX, int R, int ND, int MODE, int NDOT>
+template <typename TV, typename TX, int R, int ND, int MODE, int NDOT, bool UNIT = false>
 int wave_grid(int cap) {
   static int blocks = 0;  // one cache per kernel instantiation
   if (blocks == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dia_step_kernel<TV, TX, R, ND, MODE, NDOT>, kBlock,
-                                                      0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dia_step_kernel<TV, TX, R, ND, MODE, NDOT, UNIT>,
+                                                      kBlock, 0) != cudaSuccess ||
         per_sm <= 0)
       per_sm = 1;
     blocks = sms * per_sm * kWaves;
@@ -211,6 +224,7 @@ int wave_grid(int cap) {
 DiaArgs dia_args(const MatDesc& A) {
   DiaArgs d;
   d.nd = A.ndiag;
+  d.unit = A.dia_unit;
   for (int t = 0; t < kMaxDiag; ++t) d.doff[t] = t < A.ndiag ? A.doff[t] : 0;
   d.dstride = A.dstride;
   d.dpad = A.dpad;
@@ -226,7 +240,10 @@ cudaError_t go_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, dou
   } else {
     constexpr int R = std::is_same<TX, double>::value ? 4 : 2;
     const TV* v = static_cast<const TV*>(A.val);
-    if (A.ndiag == 4)
+    if (A.ndiag == 3 && A.dia_unit)  // Jacobi-scaled 7-point stencil
+      dia_step_kernel<TV, TX, R, 3, MODE, NDOT, true><<<wave_grid<TV, TX, R, 3, MODE, NDOT, true>(grid), kBlock, 0,
+                                                         s>>>(dia_args(A), v, make_args<TX>(p), sc, partials, cnt);
+    else if (A.ndiag == 4 && !A.dia_unit)
       dia_step_kernel<TV, TX, R, 4, MODE, NDOT><<<wave_grid<TV, TX, R, 4, MODE, NDOT>(grid), kBlock, 0, s>>>(
           dia_args(A), v, make_args<TX>(p), sc, partials, cnt);
     else
@@ -265,25 +282,17 @@ cudaError_t dia_mode(const MatDesc& A, const StepParams& p, const Scalars* sc, d
 
 cudaError_t launch_step_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, double* partials,
                             unsigned int* counter, int grid, cudaStream_t s) {
-  if (A.ndiag < 1 || A.ndiag > kMaxDiag) return cudaErrorInvalidValue;
+  if (A.ndiag < 0 || A.ndiag > kMaxDiag || (A.ndiag == 0 && !A.dia_unit)) return cudaErrorInvalidValue;
   if (A.prec == kF64) return dia_mode<double, double>(A, p, sc, partials, counter, grid, s);
   if (A.prec == kF32) return dia_mode<float, float>(A, p, sc, partials, counter, grid, s);
   return dia_mode<__nv_bfloat16, float>(A, p, sc, partials, counter, grid, s);
 }
 
+// DIA launches size their own grid per variant (wave_grid); the caller's grid
+// is only the cap, so no occupancy figure is needed here.
 int step_blocks_per_sm_dia(const MatDesc& A) {
-  int nb = 0;
-  cudaError_t e;
-  if (A.prec == kF32)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<float, float, 2, 4, kChebK, 0>, kBlock, 0);
-  else if (A.prec == kBF16)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<__nv_bfloat16, float, 2, 4, kChebK, 0>,
-                                                      kBlock, 0);
-  else if (A.ndiag == 4)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 4, 4, kChebK, 0>, kBlock, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dia_step_kernel<double, double, 4, 0, kChebK, 0>, kBlock, 0);
-  return (e == cudaSuccess && nb > 0) ? nb : 2;
+  (void)A;
+  return 16;
 }
 
 }  // namespace pp

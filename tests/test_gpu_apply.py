@@ -168,18 +168,23 @@ def test_dia_rejects_unsymmetric_and_missing_diagonal():
     E = np.diag([2.0, 2.0, 2.0])
     E[0, 1] = E[1, 0] = -1.0
     A = I.dense_to_csr(E)
-    A.val[0] = 2.0  # keep values; drop nothing: this one is fine
     S = P.Solver.from_host(A, k=2, format="dia", interval="given", alpha=0.5, beta=3.5)
-    assert S.info()["format"] == 3 and S.info()["ndiag"] == 2
+    assert S.info()["format"] == 3 and S.info()["ndiag"] == 1  # Jacobi: the unit diagonal is not stored
+    S = P.Solver.from_host(A, k=2, format="dia", interval="given", alpha=0.5, beta=3.5, seed_scaling=False)
+    assert S.info()["ndiag"] == 2
 
 
-def test_dia_uses_four_diagonals_for_the_7_point_stencil():
+def test_dia_diagonals_for_the_7_point_stencil():
+    """Jacobi-scaled: the diagonal is 1 by construction and only the upper
+    diagonals (1, N, N^2) are stored; unscaled: the main diagonal too."""
     A = I.diffusion3d(17, 2.0, seed=5)
-    S = P.Solver.from_host(A, k=5, format="dia")
-    info = S.info()
-    assert info["format"] == 3 and info["ndiag"] == 4
     x = I.rhs_normal(A.n, 6)
-    assert rel(to_np(S.operator(torch.as_tensor(x, device="cuda"))), A.matvec(x)) <= 1e-13
+    for scaling, nd in ((True, 3), (False, 4)):
+        S = P.Solver.from_host(A, k=5, format="dia", seed_scaling=scaling, interval="given", alpha=0.05,
+                               beta=14.0 if not scaling else 1.95)
+        info = S.info()
+        assert info["format"] == 3 and info["ndiag"] == nd
+        assert rel(to_np(S.operator(torch.as_tensor(x, device="cuda"))), A.matvec(x)) <= 1e-13
 
 
 @pytest.mark.parametrize("N", [16, 17, 18, 20])
