@@ -51,7 +51,8 @@ WORKLOADS = {
     "dfn200": dict(dfn=True, seed=2, k=3, lanczos=30, prec="f64"),
     # p_k(S_hat) with the FP32 copy of the trace blocks, outer FP64 FCG(1)
     "dfn200_f32": dict(dfn=True, seed=2, k=15, lanczos=30, prec="f32", flexible=1),
-    "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32"),
+    # per-instance symmetric DIA in the batch (the instances are 7-point stencils)
+    "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32", fmt="dia"),
 }
 METRIC = "PCG time-to-rtol-1e-8 (s) and polyprec_apply HBM GB/s vs plain FP64, 1 GB300"
 VAL_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
@@ -330,6 +331,7 @@ def run_batch(args, w, specs, k, dev, world, rank):
     mats = [I.batch_instance(s) for s in specs]
     rhs = [I.batch_rhs(s) for s in specs]
     S = P.BatchSolver(mats, [s.nrhs for s in specs], device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8,
+                      format=w.get("fmt", "auto"),
                       apply_prec=w["prec"], flexible=1, use_graphs=1, check_every=10, maxit=5000)
     bt = S.pack(rhs)
     mlp_used = 0
@@ -362,7 +364,8 @@ def run_batch(args, w, specs, k, dev, world, rank):
     err = 0.0
     its64 = []
     for i, (A, Bm) in enumerate(zip(mats, rhs)):
-        S64 = P.Solver.from_host(A, device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8, seed=i)
+        S64 = P.Solver.from_host(A, device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8, seed=i,
+                                 format=w.get("fmt", "auto"))
         for r in range(Bm.shape[1]):
             b = torch.as_tensor(np.ascontiguousarray(Bm[:, r]), device=dev)
             S64.solve(b)  # warm
@@ -386,7 +389,8 @@ def run_batch(args, w, specs, k, dev, world, rank):
                "config": {"workload": args.workload, "instances": len(specs), "rows": rows,
                           "columns": int(sum(s.nrhs for s in specs)), "k": k, "apply": w["prec"],
                           "outer": "f64 flexible CG", "graphs": 1, "interval": f"mlp ({mlp_used} instances)"
-                          if mlp_used else "lanczos"},
+                          if mlp_used else "lanczos", "layout": w.get("fmt", "auto"),
+                          "sequential_baseline": "each column alone, plain FP64 PCG, same layout, Lanczos interval"},
                "iterations_max": int(max(stats[-1]["iterations"], 0)),
                "sequential_f64_s": t_seq, "speedup_vs_sequential_f64": t_seq / (ms / 1e3),
                "max_rel_diff_vs_f64": err, "iterations_f64_max": int(max(its64)),

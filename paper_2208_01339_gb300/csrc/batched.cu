@@ -30,7 +30,8 @@
 
 namespace pp {
 
-constexpr int kBR = 8;  // maximum right-hand sides per instance
+constexpr int kBR = 8;     // maximum right-hand sides per instance
+constexpr int kBDiag = 8;  // DIA mode: stored upper diagonals per instance
 
 struct BatchDev {
   int nb = 0;             // instances
@@ -52,6 +53,19 @@ struct BatchDev {
   const int* ccol_inst = nullptr;   // instance of each global column
   const double* w = nullptr;        // Jacobi seed weights, per instance row (voff1 layout)
   const long long* woff = nullptr;  // weight offset per instance
+  // DIA mode (format = PP_FMT_DIA): every instance symmetric-banded; with the
+  // Jacobi seed its diagonal is 1 and only the upper diagonals are stored:
+  // entry (row, row + dia_off[i][t]) at dval[dia_base[i] + t * dia_stride[i]
+  // + dia_pad[i] + row], zero-padded in front (dia_pad >= largest offset) and
+  // over the padded rows of the instance's last slice.
+  int dia = 0;
+  const int* dia_nd = nullptr;
+  const int* dia_off = nullptr;  // [nb][kBDiag]
+  const long long* dia_base = nullptr;
+  const long long* dia_stride = nullptr;
+  const long long* dia_pad = nullptr;
+  const double* dval64 = nullptr;
+  const float* dval32 = nullptr;
   // per-column coefficients
   const double* theta_bar = nullptr;
   const double* delta = nullptr;
@@ -132,6 +146,43 @@ struct RowVec {
   }
 };
 
+// DIA mode: row sums of the instance's seed-scaled matrix for R right-hand
+// sides ([row][rhs] vectors; stride RS with R = 1 for the Lanczos view):
+// the unit diagonal, then each stored diagonal and its mirror.
+template <typename TV, typename TX, int R>
+__device__ __forceinline__ void b_dia_rowsum(const BatchDev& d, int i, long long row, const TV* __restrict__ dval,
+                                             const TX* __restrict__ xi, int RS, TX (&acc)[R]) {
+  if (R == 1 && RS != 1) {
+    acc[0] = xi[row * RS];
+  } else {
+    RowVec<TX, R> xs;
+    xs.load(xi + row * R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = xs.v[r];
+  }
+  const int nd = d.dia_nd[i];
+  const long long base = d.dia_base[i] + d.dia_pad[i];
+  const long long str = d.dia_stride[i];
+  const long long last = (d.sbase[i + 1] - d.sbase[i]) * 32 - 1;
+  for (int t = 0; t < nd; ++t) {
+    const long long o = d.dia_off[i * kBDiag + t];
+    const TV* U = dval + base + t * str;
+    const TX up = (TX)U[row];      // a(row, row + o); 0 past the instance's last row
+    const TX lo = (TX)U[row - o];  // a(row - o, row); 0 in the front pad
+    const long long ju = row + o < last ? row + o : last;
+    const long long jl = row - o > 0 ? row - o : 0;
+    if (R == 1 && RS != 1) {
+      acc[0] = fma(up, xi[ju * RS], fma(lo, xi[jl * RS], acc[0]));
+    } else {
+      RowVec<TX, R> xu, xl;
+      xu.load(xi + ju * R);
+      xl.load(xi + jl * R);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = fma(up, xu.v[r], fma(lo, xl.v[r], acc[r]));
+    }
+  }
+}
+
 __device__ __forceinline__ unsigned active_mask(const int* done, int g0, int R) {
   unsigned m = 0;
   for (int r = 0; r < R; ++r)
@@ -148,19 +199,23 @@ __device__ __forceinline__ void b_spmv_slice(const BatchDev& d, long long s, int
   const int lane = threadIdx.x & 31;
   const long long row = d.s_row0[s] + lane;
   const bool in = row < d.n[i];
-  const long long base = d.sptr[s];
-  const int w = (int)((d.sptr[s + 1] - base) / 32);
   const double* xi = x + d.voff[i];
   double acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = 0.0;
-  for (int j = 0; j < w; ++j) {
-    const double v = __ldcs(d.val64 + base + (long long)j * 32 + lane);
-    const long long c = __ldcs(d.col + base + (long long)j * 32 + lane);
-    RowVec<double, R> xv;
-    if (MODE == kLanczos) xv.v[0] = __ldg(xi + c * RS); else xv.load(xi + c * R);
+  if (d.dia) {
+    b_dia_rowsum<double, double, R>(d, i, row, d.dval64, xi, MODE == kLanczos ? RS : R, acc);
+  } else {
+    const long long base = d.sptr[s];
+    const int w = (int)((d.sptr[s + 1] - base) / 32);
+    for (int j = 0; j < w; ++j) {
+      const double v = __ldcs(d.val64 + base + (long long)j * 32 + lane);
+      const long long c = __ldcs(d.col + base + (long long)j * 32 + lane);
+      RowVec<double, R> xv;
+      if (MODE == kLanczos) xv.v[0] = __ldg(xi + c * RS); else xv.load(xi + c * R);
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = fma(v, xv.v[r], acc[r]);
+      for (int r = 0; r < R; ++r) acc[r] = fma(v, xv.v[r], acc[r]);
+    }
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -214,19 +269,23 @@ __device__ __forceinline__ void b_cheb_slice(const BatchDev& d, long long s, int
                                              const TX* xold, const TX* rin, TX* y, const double* coef, unsigned act) {
   const int lane = threadIdx.x & 31;
   const long long row = d.s_row0[s] + lane;
-  const long long base = d.sptr[s];
-  const int w = (int)((d.sptr[s + 1] - base) / 32);
   const TX* xi = x + d.voff[i];
   TX acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = (TX)0;
-  for (int jj = 0; jj < w; ++jj) {
-    const TX v = (TX)__ldcs(val + base + (long long)jj * 32 + lane);
-    const long long c = __ldcs(d.col + base + (long long)jj * 32 + lane);
-    RowVec<TX, R> xv;
-    xv.load(xi + c * R);
+  if (d.dia) {
+    b_dia_rowsum<TV, TX, R>(d, i, row, val, xi, R, acc);  // val: the DIA values in this precision
+  } else {
+    const long long base = d.sptr[s];
+    const int w = (int)((d.sptr[s + 1] - base) / 32);
+    for (int jj = 0; jj < w; ++jj) {
+      const TX v = (TX)__ldcs(val + base + (long long)jj * 32 + lane);
+      const long long c = __ldcs(d.col + base + (long long)jj * 32 + lane);
+      RowVec<TX, R> xv;
+      xv.load(xi + c * R);
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = fma(v, xv.v[r], acc[r]);
+      for (int r = 0; r < R; ++r) acc[r] = fma(v, xv.v[r], acc[r]);
+    }
   }
   const long long e0 = d.voff[i] + row * R;
   RowVec<TX, R> rs, xs, xo;
@@ -514,13 +573,22 @@ __global__ void __launch_bounds__(kBlock) b_feature_kernel(BatchDev d, const dou
     const int i = d.s_inst[s];
     const long long row = d.s_row0[s] + lane;
     const bool in = row < d.n[i];
-    const long long base = d.sptr[s];
-    const int w = (int)((d.sptr[s + 1] - base) / 32);
     double off = 0.0, dg = 0.0;
-    for (int j = 0; j < w; ++j) {
-      const double v = d.val64[base + (long long)j * 32 + lane];
-      const long long c = d.col[base + (long long)j * 32 + lane];
-      if (c == row) dg += v; else off += fabs(v);
+    if (d.dia) {
+      dg = 1.0;
+      const long long b0 = d.dia_base[i] + d.dia_pad[i];
+      for (int t = 0; t < d.dia_nd[i]; ++t) {
+        const double* U = d.dval64 + b0 + t * d.dia_stride[i];
+        off += fabs(U[row]) + fabs(U[row - d.dia_off[i * kBDiag + t]]);
+      }
+    } else {
+      const long long base = d.sptr[s];
+      const int w = (int)((d.sptr[s + 1] - base) / 32);
+      for (int j = 0; j < w; ++j) {
+        const double v = d.val64[base + (long long)j * 32 + lane];
+        const long long c = d.col[base + (long long)j * 32 + lane];
+        if (c == row) dg += v; else off += fabs(v);
+      }
     }
     const double dl = in ? diag_log[d.woff[i] + row] : 0.0;
     double a0 = warp_sum(dl), a1 = warp_sum(dl * dl);
@@ -565,21 +633,23 @@ __global__ void b_fill_kernel(BatchDev d, const int* const* rowptrs, const int* 
     const int i = d.s_inst[s];
     const long long row = d.s_row0[s] + lane;
     const bool in = row < d.n[i];
-    const long long base = d.sptr[s];
-    const int wd = (int)((d.sptr[s + 1] - base) / 32);
-    int j = 0;
-    if (in) {
-      const int* rp = rowptrs[i];
-      const int* ci = cols[i];
-      const double* va = vals[i];
-      for (int p = rp[row]; p < rp[row + 1]; ++p, ++j) {
-        ocol[base + (long long)j * 32 + lane] = ci[p];
-        oval[base + (long long)j * 32 + lane] = va[p];
+    if (ocol) {  // SELL mode
+      const long long base = d.sptr[s];
+      const int wd = (int)((d.sptr[s + 1] - base) / 32);
+      int j = 0;
+      if (in) {
+        const int* rp = rowptrs[i];
+        const int* ci = cols[i];
+        const double* va = vals[i];
+        for (int p = rp[row]; p < rp[row + 1]; ++p, ++j) {
+          ocol[base + (long long)j * 32 + lane] = ci[p];
+          oval[base + (long long)j * 32 + lane] = va[p];
+        }
       }
-    }
-    for (; j < wd; ++j) {
-      ocol[base + (long long)j * 32 + lane] = in ? (int)row : 0;
-      oval[base + (long long)j * 32 + lane] = 0.0;
+      for (; j < wd; ++j) {
+        ocol[base + (long long)j * 32 + lane] = in ? (int)row : 0;
+        oval[base + (long long)j * 32 + lane] = 0.0;
+      }
     }
     if (in) {
       double dg = 0.0;
@@ -589,6 +659,64 @@ __global__ void b_fill_kernel(BatchDev d, const int* const* rowptrs, const int* 
       if (!(dg > 0.0)) atomicExch(bad, 1);
       w[d.woff[i] + row] = dg > 0.0 ? 1.0 / sqrt(dg) : 1.0;
       diag_log[d.woff[i] + row] = dg > 0.0 ? log(dg) : 0.0;
+    }
+  }
+}
+
+// DIA mode: every entry of instance i lies on one of its offsets (or their
+// mirrors) and a(c, row) == a(row, c) exactly; otherwise bad[i] = 1.
+__global__ void b_dia_check_kernel(BatchDev d, const int* const* rowptrs, const int* const* cols,
+                                   const double* const* vals, int* __restrict__ bad) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const long long row = d.s_row0[s] + lane;
+    if (row >= d.n[i]) continue;
+    const int* rp = rowptrs[i];
+    const int* ci = cols[i];
+    const double* va = vals[i];
+    bool ok = true;
+    for (int p = rp[row]; p < rp[row + 1] && ok; ++p) {
+      const long long c = ci[p];
+      const long long o = c > row ? c - row : row - c;
+      if (o == 0) continue;
+      bool on = false;
+      for (int t = 0; t < d.dia_nd[i]; ++t) on = on || (d.dia_off[i * kBDiag + t] == o);
+      bool mirror = false;
+      for (int q = rp[c]; q < rp[c + 1]; ++q)
+        if (ci[q] == row) {
+          mirror = va[q] == va[p];
+          break;
+        }
+      ok = on && mirror;
+    }
+    if (!ok) atomicExch(bad + i, 1);
+  }
+}
+
+// DIA mode: the seed-scaled upper entries w_row a w_col into their diagonals.
+__global__ void b_dia_fill_kernel(BatchDev d, const int* const* rowptrs, const int* const* cols,
+                                  const double* const* vals, double* __restrict__ dval64, float* __restrict__ dval32) {
+  const int lane = threadIdx.x & 31;
+  for (long long s = bgw(); s < d.nslices; s += bnw()) {
+    const int i = d.s_inst[s];
+    const long long row = d.s_row0[s] + lane;
+    if (row >= d.n[i]) continue;
+    const int* rp = rowptrs[i];
+    const int* ci = cols[i];
+    const double* va = vals[i];
+    const double wr = d.w[d.woff[i] + row];
+    for (int p = rp[row]; p < rp[row + 1]; ++p) {
+      const long long c = ci[p];
+      if (c <= row) continue;
+      for (int t = 0; t < d.dia_nd[i]; ++t)
+        if (d.dia_off[i * kBDiag + t] == c - row) {
+          const long long e = d.dia_base[i] + t * d.dia_stride[i] + d.dia_pad[i] + row;
+          const double v = (wr * va[p]) * d.w[d.woff[i] + c];
+          dval64[e] = v;
+          if (dval32) dval32[e] = (float)v;
+          break;
+        }
     }
   }
 }
@@ -643,9 +771,45 @@ struct BPlan {
   long long nslices = 0, nnz_pad = 0, vec_elems = 0, rows_pad = 0;
   std::vector<int> s_inst, n, R, cbase, ccol_inst;
   std::vector<long long> s_row0, sptr, voff, woff, uoff, sbase;
+  // DIA mode
+  bool dia = false;
+  long long dia_total = 0;
+  std::vector<int> dia_nd, dia_off;
+  std::vector<long long> dia_base, dia_stride, dia_pad;
 };
 
-int plan_batch(const pp_batch_item* items, int count, BPlan& P, cudaStream_t s) {
+// DIA mode: the upper offsets of instance i are those of its first row
+// (for a Dirichlet stencil every offset occurs there); pp_batch_setup then
+// checks every entry against them on the device.
+int plan_dia_instance(const pp_batch_item& it, int i, long long ns, BPlan& P, cudaStream_t s) {
+  int r0[2];
+  cudaError_t e = cudaMemcpyAsync(r0, it.rowptr, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "pp_batch: reading rowptr");
+  const int len = r0[1] - r0[0];
+  std::vector<int> c0((size_t)std::max(len, 1));
+  if (len > 0) e = cudaMemcpyAsync(c0.data(), it.col + r0[0], sizeof(int) * len, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "pp_batch: reading row 0");
+  std::vector<int> offs;
+  for (int q = 0; q < len; ++q)
+    if (c0[q] > 0) offs.push_back(c0[q]);
+  std::sort(offs.begin(), offs.end());
+  offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
+  if ((int)offs.size() > kBDiag)
+    return fail(nullptr, PP_EUNSUPPORTED, "pp_batch DIA: more than 8 upper diagonals (item " + std::to_string(i) + ")");
+  const long long pad = offs.empty() ? 0 : ((long long)offs.back() + 31) / 32 * 32;
+  P.dia_nd.push_back((int)offs.size());
+  for (int t = 0; t < kBDiag; ++t) P.dia_off.push_back(t < (int)offs.size() ? offs[t] : 0);
+  P.dia_pad.push_back(pad);
+  P.dia_stride.push_back(pad + ns * 32);
+  P.dia_base.push_back(P.dia_total);
+  P.dia_total += (long long)offs.size() * (pad + ns * 32);
+  return PP_OK;
+}
+
+int plan_batch(const pp_batch_item* items, int count, BPlan& P, cudaStream_t s, bool dia) {
+  P.dia = dia;
   P.nb = count;
   P.sbase.assign(count + 1, 0);
   P.sptr.push_back(0);
@@ -667,6 +831,10 @@ int plan_batch(const pp_batch_item* items, int count, BPlan& P, cudaStream_t s) 
       P.sptr.push_back(P.sptr.back() + (long long)wmax * 32);
     }
     P.sbase[i + 1] = P.sbase[i] + ns;
+    if (dia) {
+      const int rc = plan_dia_instance(it, i, ns, P, s);
+      if (rc) return rc;
+    }
     P.n.push_back(it.n);
     P.R.push_back(it.nrhs);
     P.cbase.push_back(cb);
@@ -699,9 +867,23 @@ size_t layout_batch(pp_ctx* c, pp_batch_state* B, const BPlan& P, void* base) {
   d.s_inst = M.take<int>(P.nslices);
   d.s_row0 = M.take<long long>(P.nslices);
   d.sptr = M.take<long long>(P.nslices + 1);
-  d.col = M.take<int>(P.nnz_pad);
-  d.val64 = M.take<double>(P.nnz_pad);
-  d.val32 = B->apply_prec == PP_PREC_F32 ? M.take<float>(P.nnz_pad) : nullptr;
+  d.dia = P.dia ? 1 : 0;
+  if (P.dia) {
+    d.col = nullptr;
+    d.val64 = nullptr;
+    d.val32 = nullptr;
+    d.dia_nd = M.take<int>(P.nb);
+    d.dia_off = M.take<int>((long long)P.nb * kBDiag);
+    d.dia_base = M.take<long long>(P.nb);
+    d.dia_stride = M.take<long long>(P.nb);
+    d.dia_pad = M.take<long long>(P.nb);
+    d.dval64 = M.take<double>(P.dia_total);
+    d.dval32 = B->apply_prec == PP_PREC_F32 ? M.take<float>(P.dia_total) : nullptr;
+  } else {
+    d.col = M.take<int>(P.nnz_pad);
+    d.val64 = M.take<double>(P.nnz_pad);
+    d.val32 = B->apply_prec == PP_PREC_F32 ? M.take<float>(P.nnz_pad) : nullptr;
+  }
   d.n = M.take<int>(P.nb);
   d.R = M.take<int>(P.nb);
   d.voff = M.take<long long>(P.nb);
@@ -801,11 +983,11 @@ cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
     for (int j = 1; j <= k && e == cudaSuccess; ++j) {
       const double* cj = B->coefT + (size_t)j * d.ncols * 3;
       if (j == 1)
-        b_cheb_kernel<float, float, kCheb1><<<g, kBlock, 0, s>>>(d, d.val32, B->r32, nullptr, B->r32, Y(1), B->c.done, cj);
+        b_cheb_kernel<float, float, kCheb1><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval32 : d.val32, B->r32, nullptr, B->r32, Y(1), B->c.done, cj);
       else if (j == 2)
-        b_cheb_kernel<float, float, kCheb2><<<g, kBlock, 0, s>>>(d, d.val32, Y(1), nullptr, B->r32, Y(2), B->c.done, cj);
+        b_cheb_kernel<float, float, kCheb2><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval32 : d.val32, Y(1), nullptr, B->r32, Y(2), B->c.done, cj);
       else
-        b_cheb_kernel<float, float, kChebK><<<g, kBlock, 0, s>>>(d, d.val32, Y(j - 1), Y(j - 2), B->r32, Y(j), B->c.done,
+        b_cheb_kernel<float, float, kChebK><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval32 : d.val32, Y(j - 1), Y(j - 2), B->r32, Y(j), B->c.done,
                                                                cj);
       e = cudaGetLastError();
     }
@@ -817,11 +999,11 @@ cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
     for (int j = 1; j <= k && e == cudaSuccess; ++j) {
       const double* cj = B->coefT + (size_t)j * d.ncols * 3;
       if (j == 1)
-        b_cheb_kernel<double, double, kCheb1><<<g, kBlock, 0, s>>>(d, d.val64, B->r, nullptr, B->r, Y(1), B->c.done, cj);
+        b_cheb_kernel<double, double, kCheb1><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval64 : d.val64, B->r, nullptr, B->r, Y(1), B->c.done, cj);
       else if (j == 2)
-        b_cheb_kernel<double, double, kCheb2><<<g, kBlock, 0, s>>>(d, d.val64, Y(1), nullptr, B->r, Y(2), B->c.done, cj);
+        b_cheb_kernel<double, double, kCheb2><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval64 : d.val64, Y(1), nullptr, B->r, Y(2), B->c.done, cj);
       else
-        b_cheb_kernel<double, double, kChebK><<<g, kBlock, 0, s>>>(d, d.val64, Y(j - 1), Y(j - 2), B->r, Y(j),
+        b_cheb_kernel<double, double, kChebK><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval64 : d.val64, Y(j - 1), Y(j - 2), B->r, Y(j),
                                                                  B->c.done, cj);
       e = cudaGetLastError();
     }
@@ -981,7 +1163,7 @@ extern "C" int pp_batch_workspace_size(const pp_batch_item* items, int count, co
   if ((rc = check_batch_opts(opt))) return rc;
   if (!bytes) return fail(nullptr, PP_EINVAL, "bytes is NULL");
   BPlan P;
-  if ((rc = plan_batch(items, count, P, nullptr))) return rc;
+  if ((rc = plan_batch(items, count, P, nullptr, opt->format == PP_FMT_DIA))) return rc;
   pp_ctx tmp;
   tmp.opt = *opt;
   pp_batch_state B;
@@ -1018,7 +1200,7 @@ extern "C" int pp_batch_setup(pp_ctx** out, const pp_batch_item* items, int coun
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
   BPlan P;
-  if ((rc = plan_batch(items, count, P, s))) return bail(rc);
+  if ((rc = plan_batch(items, count, P, s, opt->format == PP_FMT_DIA))) return bail(rc);
   const size_t need = layout_batch(c, B, P, nullptr);
   if (ws_bytes < need) return bail(fail(c, PP_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes"));
   layout_batch(c, B, P, ws);
@@ -1065,6 +1247,11 @@ extern "C" int pp_batch_setup(pp_ctx** out, const pp_batch_item* items, int coun
              {d.sbase, P.sbase.data(), sizeof(long long) * P.sbase.size()},
              {d.ccol_inst, P.ccol_inst.data(), sizeof(int) * P.ccol_inst.size()},
              {d.woff, P.woff.data(), sizeof(long long) * P.woff.size()},
+             {d.dia_nd, P.dia_nd.data(), sizeof(int) * P.dia_nd.size()},
+             {d.dia_off, P.dia_off.data(), sizeof(int) * P.dia_off.size()},
+             {d.dia_base, P.dia_base.data(), sizeof(long long) * P.dia_base.size()},
+             {d.dia_stride, P.dia_stride.data(), sizeof(long long) * P.dia_stride.size()},
+             {d.dia_pad, P.dia_pad.data(), sizeof(long long) * P.dia_pad.size()},
              {d_rp, rps.data(), sizeof(void*) * count},
              {d_ci, cis.data(), sizeof(void*) * count},
              {d_va, vas.data(), sizeof(void*) * count}};
@@ -1079,7 +1266,27 @@ extern "C" int pp_batch_setup(pp_ctx** out, const pp_batch_item* items, int coun
                                                         const_cast<int*>(d.col), const_cast<double*>(d.val64), d_bad);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) {
+  int dia_bad = 0;
+  if (d.dia) {
+    // weights first (above), then the scaled upper entries; every entry is
+    // checked to lie on the planned diagonals with a symmetric partner
+    int* d_dbad = reinterpret_cast<int*>(B->t2);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_dbad, 0, sizeof(int) * count, s);
+    if (e == cudaSuccess && P.dia_total > 0)
+      e = cudaMemsetAsync(const_cast<double*>(d.dval64), 0, sizeof(double) * (size_t)P.dia_total, s);
+    if (e == cudaSuccess && d.dval32 && P.dia_total > 0)
+      e = cudaMemsetAsync(const_cast<float*>(d.dval32), 0, sizeof(float) * (size_t)P.dia_total, s);
+    if (e == cudaSuccess) {
+      b_dia_check_kernel<<<grid_b(d.nslices), kBlock, 0, s>>>(d, d_rp, d_ci, d_va, d_dbad);
+      b_dia_fill_kernel<<<grid_b(d.nslices), kBlock, 0, s>>>(d, d_rp, d_ci, d_va, const_cast<double*>(d.dval64),
+                                                              const_cast<float*>(d.dval32));
+      e = cudaGetLastError();
+    }
+    std::vector<int> hb(count, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), d_dbad, sizeof(int) * count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) dia_bad |= hb[i];
+  } else if (e == cudaSuccess) {
     b_scale_kernel<<<grid_b(d.nslices), kBlock, 0, s>>>(d, const_cast<double*>(d.val64), const_cast<float*>(d.val32));
     e = cudaGetLastError();
   }
@@ -1102,6 +1309,8 @@ extern "C" int pp_batch_setup(pp_ctx** out, const pp_batch_item* items, int coun
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "pp_batch setup"));
   if (bad) return bail(fail(c, PP_EINVAL, "pp_batch: non-positive diagonal"));
+  if (dia_bad)
+    return bail(fail(c, PP_EUNSUPPORTED, "pp_batch DIA: an instance is not symmetric-banded on its first row's offsets"));
   if (opt->interval == PP_INTERVAL_GIVEN) {
     B->abx.assign((size_t)P.ncols * 3, 0.0);
     for (int g = 0; g < P.ncols; ++g) {

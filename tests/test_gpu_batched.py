@@ -53,12 +53,16 @@ def oracle_cols(mats, rhs, k, seed, steps, abx=None, rtol=1e-10, flexible=False)
     return out
 
 
+FMTS = ["sell", "dia"]  # global SELL-32 slice list, or per-instance symmetric DIA
+
+
+@pytest.mark.parametrize("fmt", FMTS)
 @pytest.mark.parametrize("graphs", [0, 1])
 @pytest.mark.parametrize("k", [0, 1, 6])
-def test_batch_f64_matches_oracle_per_column(problem, graphs, k):
+def test_batch_f64_matches_oracle_per_column(problem, graphs, k, fmt):
     mats, rhs = problem
     S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=k, lanczos_steps=10, seed=3, rtol=1e-10, use_graphs=graphs,
-                      check_every=3)
+                      check_every=3, format=fmt)
     x, it, stv, st = S.solve(S.pack(rhs))
     xs = S.unpack(x)
     ref = oracle_cols(mats, rhs, k, 3, 10)
@@ -79,9 +83,10 @@ def test_batch_f64_matches_oracle_per_column(problem, graphs, k):
         assert abx[c0, 0] == pytest.approx(lo, rel=1e-9) and abx[c0, 1] == pytest.approx(hi, rel=1e-9)
 
 
-def test_batch_per_column_intervals(problem):
+@pytest.mark.parametrize("fmt", FMTS)
+def test_batch_per_column_intervals(problem, fmt):
     mats, rhs = problem
-    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=5, rtol=1e-10)
+    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=5, rtol=1e-10, format=fmt)
     abx = S.intervals()
     u = I.uniform(7, 9, 3 * S.ncols)
     abx[:, 0] *= 0.3 + u[0::3]        # different interval and xi in every column
@@ -100,9 +105,11 @@ def test_batch_per_column_intervals(problem):
             g += 1
 
 
-def test_batch_f32_apply_converges(problem):
+@pytest.mark.parametrize("fmt", FMTS)
+def test_batch_f32_apply_converges(problem, fmt):
     mats, rhs = problem
-    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=6, rtol=1e-9, apply_prec="f32", flexible=1, use_graphs=1)
+    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=6, rtol=1e-9, apply_prec="f32", flexible=1, use_graphs=1,
+                      format=fmt)
     x, it, stv, st = S.solve(S.pack(rhs))
     assert (stv == 0).all()
     xs = S.unpack(x)
@@ -115,11 +122,12 @@ def test_batch_f32_apply_converges(problem):
             g += 1
 
 
-def test_batch_zero_rhs_column_and_features(problem):
+@pytest.mark.parametrize("fmt", FMTS)
+def test_batch_zero_rhs_column_and_features(problem, fmt):
     mats, rhs = problem
     rhs = [b.copy() for b in rhs]
     rhs[1][:, 1] = 0.0
-    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=3, rtol=1e-9)
+    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=3, rtol=1e-9, format=fmt)
     x, it, stv, st = S.solve(S.pack(rhs))
     assert it[SPECS[0].nrhs + 1] == 0 and stv[SPECS[0].nrhs + 1] == 0
     assert not S.unpack(x)[1][:, 1].any()
@@ -134,3 +142,13 @@ def test_batch_zero_rhs_column_and_features(problem):
         off = np.abs(Ah).sum(axis=1) - np.diag(Ah)
         assert F[i, 3] == pytest.approx((np.diag(Ah) + off).max(), rel=1e-12)
         assert F[i, 4] == pytest.approx((np.diag(Ah) - off).min(), rel=1e-12, abs=1e-12)
+
+
+def test_batch_dia_rejects_unbanded_instance(problem):
+    """DIA takes each instance's offsets from its first row; an instance with
+    entries off those diagonals (here a dense SPD block) is refused."""
+    mats, _ = problem
+    D = I.dense_to_csr(I.random_spd(40, seed=2, cond=10.0))
+    with pytest.raises(P.PolyPrecError) as ei:
+        P.BatchSolver([mats[0], D], [1, 2], k=3, format="dia")
+    assert ei.value.status in (P.PP_EUNSUPPORTED,)
