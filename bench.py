@@ -51,6 +51,9 @@ WORKLOADS = {
     "dfn200": dict(dfn=True, seed=2, k=3, lanczos=30, prec="f64"),
     # p_k(S_hat) with the FP32 copy of the trace blocks, outer FP64 FCG(1)
     "dfn200_f32": dict(dfn=True, seed=2, k=15, lanczos=30, prec="f32", flexible=1),
+    # the same network with general fracture blocks (P1 stiffness on jittered triangulations,
+    # lognormal coefficients): A^{-1} from banded Cholesky factors built on the GPU
+    "dfn200_p1": dict(dfn=True, seed=2, k=3, lanczos=30, prec="f64", general="p1"),
     # per-instance symmetric DIA in the batch (the instances are 7-point stencils)
     "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32", fmt="dia"),
 }
@@ -63,7 +66,10 @@ def build_problem(w):
     from paper_2208_01339_gb300 import inputs as I
 
     if w.get("dfn"):
-        return I.fracture_network(seed=w["seed"]), None
+        net = I.fracture_network(seed=w["seed"])
+        if w.get("general") == "p1":
+            net = I.general_fracture_network(net, shuffle=False)
+        return net, None
     if w.get("batch"):
         specs = I.batch_specs(w["count"], seed=w["seed"], nmax=w.get("nmax", 160))
         return specs, None
@@ -311,6 +317,7 @@ def run_dfn_sweep(args, w, net, dopts, dev):
             ts.append(st["t_solve_ms"])
         info = S.info()
         print(json.dumps({"workload": args.workload, "k": k, "poly": dopts["poly"], "lowrank": dopts["lowrank"],
+                          "band_max": info["band_max"], "factor_ms": round(info["t_factor_ms"], 2),
                           "lanczos_steps": dopts["lanczos_steps"], "iterations": st["iterations"],
                           "time_s": statistics.median(ts) / 1e3, "mvp": st["mvp"], "dots": st["dots"],
                           "setup_ms": round(info["t_setup_ms"], 2), "alpha_hat": info["alpha_hat"],
@@ -426,7 +433,11 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
                "vs_baseline": None, "dtype": w["prec"], "data": "synthetic",
                "config": {"workload": args.workload, "n_f": net.n_f, "n_h": net.n_h, "n_u": net.n_u, "k": k,
                           "trace_block_entries": info["nnz"], "alpha_reg": net.alpha,
-                          "lanczos_steps": w["lanczos"], "lowrank": args.lowrank},
+                          "lanczos_steps": w["lanczos"], "lowrank": args.lowrank,
+                          "a_inverse": ("banded Cholesky per fracture" if info["band_max"] else
+                                        "closed form (uniform rectangles)"),
+                          "band_max": info["band_max"], "band_doubles": info["band_elems"]},
+               "factor_ms": round(info["t_factor_ms"], 2),
                "iterations": it, "setup_ms": round(info["t_setup_ms"], 2), "alpha_hat": info["alpha_hat"],
                "beta_hat": info["beta_hat"], "xi": info["xi"],
                "apply_ms": sum(s["t_apply_ms"] for s in stats) / max(1, sum(s["apply_launches"] for s in stats)),
@@ -463,6 +474,8 @@ def main():
                     help="force the step storage (skips pp_autotune)")
     ap.add_argument("--grid", type=int, default=0, help="override the grid size N of a diffusion workload "
                                                         "(smaller cases for profiler captures)")
+    ap.add_argument("--general", action="store_true",
+                    help="fracture networks: pass A and use the banded Cholesky factors even for rectangles")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip pp_autotune (layout from --sell-C/--sell-sigma/--sell-variant or the defaults)")
     args = ap.parse_args()
@@ -510,6 +523,7 @@ def main():
         dopts = dict(lanczos_steps=w["lanczos"], rtol=1e-8, check_every=args.check_every or 8,
                      use_graphs=max(args.graphs, 0), apply_prec=w["prec"], flexible=w.get("flexible", 0),
                      maxit=5000, lowrank=args.lowrank, poly=args.poly)
+        dopts["general"] = True if args.general else None
         if args.k_sweep:
             return run_dfn_sweep(args, w, net, dopts, dev)
         S = P.SchurSolver(net, device=dev, k=k, **dopts)

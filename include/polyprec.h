@@ -153,6 +153,11 @@ typedef struct {
   double ritz_resid;  /* max over them of ||A_hat v - theta v|| / theta,
                          theta = v^T A_hat v (0 for caller vectors)        */
   double theta_min;   /* smallest Rayleigh quotient theta of the vectors   */
+  int band_max;       /* Schur context with general blocks: largest
+                         half-bandwidth of the fracture factors; else 0   */
+  long long band_elems; /* doubles of band storage of those factors       */
+  double t_factor_ms; /* device time of the factorisation and the trace
+                         blocks built from it (part of t_setup_ms)         */
 } pp_info;
 
 /* Fill *opt with defaults: k=20, xi=-1 (auto), Lanczos with 10 steps, seed 0,
@@ -258,14 +263,28 @@ const char* pp_last_error(const pp_ctx* ctx);
 
 /* ---- fracture-network Schur complement (Section 4.2) ------------------- */
 
-/* Blocks of the saddle-point system Eq. sys.  A is block diagonal with
- * A_f = T[f] * (2-D 5-point Laplacian, Dirichlet on all four sides) on an
- * nx[f] x ny[f] grid of interior nodes (x fastest), unknowns
- * [offset[f], offset[f+1]); the fast exact solver used for A_f^{-1}
- * requires this uniform rectangular form.  C, B: n_h x n_u CSR; CT, BT:
- * their transposes (n_u x n_h); Gh: n_h x n_h; Gu: n_u x n_u.  nx, ny, T,
- * offset are host arrays; all CSR arrays are device arrays that must stay
- * valid until pp_destroy. */
+/* Blocks of the saddle-point system Eq. sys.  A is block diagonal, fracture
+ * f owning the unknowns [offset[f], offset[f+1]).  Two forms of A:
+ *  - rectangles (A_rowptr == NULL): A_f = T[f] * (2-D 5-point Laplacian,
+ *    Dirichlet on all four sides) on an nx[f] x ny[f] grid of interior
+ *    nodes (x fastest); A_f^{-1} restricted to the trace nodes is built in
+ *    closed form and full solves use fast diagonalisation;
+ *  - general blocks (A_rowptr != NULL): A is the caller's SPD matrix as
+ *    device CSR (n_h rows, global numbering, every entry inside its
+ *    fracture's rows, exactly symmetric, diagonal present, no repeated
+ *    entries); nx, ny, T are ignored and may be NULL.  As the paper does
+ *    (Section 4.2: the exact Cholesky factor of A), each block is factored
+ *    exactly: reordered on the host by reverse Cuthill-McKee (or kept in the
+ *    caller's numbering when that band is narrower) and factored on the GPU
+ *    as a band matrix.  PP_EUNSUPPORTED if a block's half-bandwidth after
+ *    reordering exceeds 768; PP_EBREAKDOWN if a block is not positive
+ *    definite; PP_EINVAL if A is not block diagonal or not symmetric.
+ *    Workspace: the band factors (sum over fractures of n_f (w_f + 1)
+ *    doubles) plus 2 x (SM count) x max n_f x 32 doubles of solve scratch.
+ * C, B: n_h x n_u CSR; CT, BT: their transposes (n_u x n_h); Gh: n_h x n_h;
+ * Gu: n_u x n_u.  nx, ny, T, offset are host arrays; all CSR arrays are
+ * device arrays; C..Gu must stay valid until pp_destroy, A only during
+ * schur_setup. */
 typedef struct {
   int n_f, n_h, n_u;
   const int* nx;            /* host, n_f */
@@ -279,6 +298,7 @@ typedef struct {
   const int *Gh_rowptr, *Gh_col; const double* Gh_val;
   const int *Gu_rowptr, *Gu_col; const double* Gu_val;
   double alpha_reg;         /* regularisation parameter alpha of Eq. func_psi */
+  const int *A_rowptr, *A_col; const double* A_val;  /* general blocks, or NULL */
 } pp_dfn;
 
 int pp_schur_workspace_size(const pp_dfn* d, const pp_options* opt, size_t* bytes);

@@ -562,6 +562,9 @@ extern "C" int pp_get_info(const pp_ctx* c, pp_info* info) {
   info->ritz_resid = c->lr_ritz_resid;
   info->lowrank_steps_done = c->lr_steps_done;
   info->theta_min = c->lr_theta.empty() ? 0.0 : *std::min_element(c->lr_theta.begin(), c->lr_theta.end());
+  info->band_max = c->band_max;
+  info->band_elems = c->band_elems;
+  info->t_factor_ms = c->t_band_ms;
   return PP_OK;
 }
 

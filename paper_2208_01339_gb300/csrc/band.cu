@@ -1,0 +1,535 @@
+// Banded Cholesky factors of general fracture blocks and the solves built on
+// them (declarations and storage in band.cuh).
+//
+// Factorisation: one block per fracture, columns in order.  Column j is
+// scaled by the pivot, then the (w x w) lower triangle below it takes the
+// rank-one update.  The live part of the band -- rows j..j+w, columns j..i
+// of row i -- is kept in a window indexed by (row mod W, column mod W),
+// W = w + 1.  Of the two mirrored slots (a, b) and (b, a) only one is live at
+// any time, so the window folds into a packed triangle of W (W + 1) / 2
+// doubles.  For w <= 238 that fits in shared memory; wider bands keep the
+// same window in global memory (L1/L2 resident).  Every band entry is read
+// from HBM once and the factor written once.
+//
+// Trace blocks: work item = one fracture and up to 32 of its trace columns
+// (sorted by position, so the forward solve starts at the first one: the
+// unit vectors are zero above it).  Lanes are columns, warps split the band.
+// Forward L y = e in dot form over row i of L; backward L^T x = y in axpy form
+// over the same row (x_i is final once rows i+1..i+w have been applied), so
+// both sweeps read L by rows.  Rows of x that are trace nodes are written
+// into M_f.  Items are handed out largest first from a device counter.
+//
+// Full solves: one warp per fracture, the same two sweeps on one vector.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "../../include/polyprec.h"
+#include "band.cuh"
+#include "common.cuh"
+
+namespace pp {
+namespace {
+
+__host__ __device__ __forceinline__ int tri(int a) { return (a * (a + 1)) >> 1; }
+
+// packed window slot of the live entry (i, j), i >= j
+__device__ __forceinline__ int wslot(int i, int j, int W) {
+  const int a = i % W, b = j % W;
+  return a >= b ? tri(a) + b : tri(b) + a;
+}
+
+__device__ __forceinline__ int fracture_of(const long long* off, int nf, long long e) {
+  int lo = 0, hi = nf;  // off[lo] <= e < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void band_fill_kernel(BandDev D, int n_h, const int* __restrict__ rp, const int* __restrict__ col,
+                                 const double* __restrict__ val) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n_h;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int f = fracture_of(D.off, D.n_f, r);
+    const int w = D.w[f], W = w + 1;
+    const int pi = D.pos[r];
+    double* row = D.L + D.boff[f] + (long long)pi * W + w - pi;  // row[pj] = (pi, pj)
+    for (int p = rp[r]; p < rp[r + 1]; ++p) {
+      const int pj = D.pos[col[p]];
+      if (pj <= pi) row[pj] = val[p];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) band_factor_kernel(BandDev D) {
+  extern __shared__ double band_sm[];
+  const int f = D.order[blockIdx.x];
+  const long long o = D.off[f];
+  const int n = (int)(D.off[f + 1] - o), w = D.w[f], W = w + 1;
+  double* L = D.L + D.boff[f];
+  double* win = D.gwoff[f] >= 0 ? D.gwin + D.gwoff[f] : band_sm;
+  double* lcol = win + tri(W);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // rows 0..w are all live at column 0
+  const int r0 = min(w, n - 1);
+  for (int i = 0; i <= r0; ++i)
+    for (int j = tid; j <= i; j += nt) win[wslot(i, j, W)] = L[(long long)i * W + w - i + j];
+  __syncthreads();
+  bool bad = false;
+  for (int j = 0; j < n; ++j) {
+    const double ajj = win[wslot(j, j, W)];
+    const bool ok = ajj > 0.0;  // false for NaN too
+    bad |= !ok;
+    const double d = ok ? sqrt(ajj) : 1.0;
+    const double rd = 1.0 / d;
+    const int m = min(w, n - 1 - j);
+    for (int r = 1 + tid; r <= m; r += nt) {
+      const double l = win[wslot(j + r, j, W)] * rd;
+      lcol[r] = l;
+      L[(long long)(j + r) * W + w - r] = l;
+    }
+    if (tid == 0) L[(long long)j * W + w] = d;
+    __syncthreads();
+    // rank-one update of rows j+r, columns j+s, 1 <= s <= r <= m; thread p
+    // takes rows p+1 and m-p, m+1 updates in all
+    const int half = (m + 1) >> 1;
+    for (int p = tid; p < half; p += nt) {
+      for (int h = 0; h < 2; ++h) {
+        const int r = h == 0 ? p + 1 : m - p;
+        if (h == 1 && r == p + 1) break;
+        const int a = (j + r) % W, ta = tri(a);
+        int b = (j + 1) % W, tb = tri(b);
+        const double lr = lcol[r];
+        for (int s = 1; s <= r; ++s) {
+          const int idx = a >= b ? ta + b : tb + a;
+          win[idx] = fma(-lr, lcol[s], win[idx]);
+          if (++b == W) {
+            b = 0;
+            tb = 0;
+          } else {
+            tb += b;
+          }
+        }
+      }
+    }
+    // row j + W enters in the slots that column j has just left
+    const int inew = j + W;
+    if (inew < n)
+      for (int q = tid; q < W; q += nt) {
+        const int c = j + 1 + q;
+        win[wslot(inew, c, W)] = L[(long long)inew * W + w - inew + c];
+      }
+    __syncthreads();
+  }
+  if (tid == 0 && bad) atomicCAS(D.flags, 0, f + 1);
+}
+
+__global__ void __launch_bounds__(kBandWarps * 32) band_trace_kernel(BandDev D, const long long* toff,
+                                                                     const long long* moff, double* M) {
+  extern __shared__ double band_sm[];
+  __shared__ int item_s;
+  constexpr int NC = kBandCols, NW = kBandWarps;
+  double* part = band_sm;       // NW x NC partial row sums
+  double* xs = part + NW * NC;  // NC
+  double* ring = xs + NC;       // W x NC: the last W rows of the sweep
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  double* Z = D.Z + (long long)blockIdx.x * D.max_n * NC;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(D.flags + 1, 1);
+    __syncthreads();
+    const int it = item_s;
+    if (it >= D.n_items) break;
+    const int4 I = D.items[it];
+    const int f = I.x, cnt = I.z, p0 = I.w;
+    const long long o = D.off[f], t0 = toff[f];
+    const int n = (int)(D.off[f + 1] - o), w = D.w[f], W = w + 1;
+    const long long tf = toff[f + 1] - t0;
+    const double* L = D.L + D.boff[f];
+    const int col_b = lane < cnt ? D.tcol[t0 + I.y + lane] : -1;
+    const int col_p = lane < cnt ? D.tpos[t0 + I.y + lane] : -1;
+    for (int e = threadIdx.x; e < W * NC; e += blockDim.x) ring[e] = 0.0;
+    __syncthreads();
+    // forward: L y = e_b from row p0 on
+    for (int i = p0; i < n; ++i) {
+      const double* Li = L + (long long)i * W + w;  // Li[-k] = L(i, i-k)
+      const int kmax = min(w, i - p0);
+      double acc = 0.0;
+      if (1 + g <= kmax) {
+        int sl = (i - 1 - g) % W;
+        for (int k = 1 + g; k <= kmax; k += NW) {
+          acc = fma(Li[-k], ring[sl * NC + lane], acc);
+          sl -= NW;
+          while (sl < 0) sl += W;
+        }
+      }
+      part[g * NC + lane] = acc;
+      __syncthreads();
+      if (g == 0) {
+        double s = 0.0;
+        for (int q = 0; q < NW; ++q) s += part[q * NC + lane];
+        const double y = ((i == col_p ? 1.0 : 0.0) - s) / Li[0];
+        ring[(i % W) * NC + lane] = y;
+        Z[(long long)i * NC + lane] = y;
+      }
+      __syncthreads();
+    }
+    // backward: L^T x = y; slot of row t holds y_t minus the rows applied so far
+    for (int e = threadIdx.x; e < W * NC; e += blockDim.x) {
+      const int rr = n - 1 - e / NC, ln = e % NC;
+      if (rr >= 0) ring[(rr % W) * NC + ln] = rr >= p0 ? Z[(long long)rr * NC + ln] : 0.0;
+    }
+    __syncthreads();
+    const int* tat = D.trace_at + o;
+    double* Mf = M + moff[f];
+    for (int t = n - 1; t >= 0; --t) {
+      const double* Lt = L + (long long)t * W + w;
+      if (g == 0) {
+        const int st = (t % W) * NC + lane;
+        const double x = ring[st] / Lt[0];
+        xs[lane] = x;
+        const int a = tat[t];
+        if (a >= 0 && col_b >= 0) Mf[(long long)a * tf + col_b] = x;
+        const int rn = t - W;  // the row that takes this slot next
+        ring[st] = rn >= p0 ? Z[(long long)rn * NC + lane] : 0.0;
+      }
+      __syncthreads();
+      const double x = xs[lane];
+      const int kmax = min(w, t);
+      if (1 + g <= kmax) {
+        int sl = (t - 1 - g) % W;
+        for (int k = 1 + g; k <= kmax; k += NW) {
+          double* q = ring + sl * NC + lane;
+          *q = fma(-Lt[-k], x, *q);
+          sl -= NW;
+          while (sl < 0) sl += W;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// M_f <- (M_f + M_f^T) / 2: the two solves of a pair round differently
+__global__ void band_symmetrize_kernel(int nf, const long long* toff, const long long* moff, double* M) {
+  const long long total = moff[nf];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int f = fracture_of(moff, nf, e);
+    const long long t = toff[f + 1] - toff[f], loc = e - moff[f];
+    const long long a = loc / t, b = loc % t;
+    if (a >= b) continue;
+    double* Mf = M + moff[f];
+    const double v = 0.5 * (Mf[a * t + b] + Mf[b * t + a]);
+    Mf[a * t + b] = v;
+    Mf[b * t + a] = v;
+  }
+}
+
+__global__ void band_solve_kernel(BandDev D, const double* v, double* y, double* z) {
+  extern __shared__ double band_sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (gw >= D.n_f) return;  // whole warps only: no block barrier below
+  const int f = D.order[gw];
+  const long long o = D.off[f];
+  const int n = (int)(D.off[f + 1] - o), w = D.w[f], W = w + 1;
+  const double* L = D.L + D.boff[f];
+  const int* perm = D.perm + o;
+  double* ring = band_sm + (long long)wib * (D.max_w + 1);
+  double* zf = z + o;
+  for (int i = 0; i < n; ++i) {
+    const double* Li = L + (long long)i * W + w;
+    const int kmax = min(w, i);
+    double acc = 0.0;
+    for (int k = 1 + lane; k <= kmax; k += 32) acc = fma(Li[-k], ring[(i - k) % W], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const double yi = (v[o + perm[i]] - acc) / Li[0];
+      ring[i % W] = yi;
+      zf[i] = yi;
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < W; e += 32) {
+    const int rr = n - 1 - e;
+    if (rr >= 0) ring[rr % W] = zf[rr];
+  }
+  __syncwarp();
+  for (int t = n - 1; t >= 0; --t) {
+    const double* Lt = L + (long long)t * W + w;
+    const double x = ring[t % W] / Lt[0];
+    __syncwarp();
+    if (lane == 0) {
+      y[o + perm[t]] = x;
+      ring[t % W] = t - W >= 0 ? zf[t - W] : 0.0;
+    }
+    const int kmax = min(w, t);
+    for (int k = 1 + lane; k <= kmax; k += 32) {
+      const int sl = (t - k) % W;
+      ring[sl] = fma(-Lt[-k], x, ring[sl]);
+    }
+    __syncwarp();
+  }
+}
+
+int grid_for(long long work, int block) {
+  const long long g = (work + block - 1) / block;
+  return (int)std::max(1LL, std::min<long long>(g, 152LL * 16));
+}
+
+cudaError_t allow_smem(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Reverse Cuthill-McKee (Cuthill & McKee 1969; reversed as in George 1971)
+// from pseudo-peripheral roots (George & Liu 1979), one connected component
+// at a time; neighbours are visited by increasing degree, ties by index.
+// Returns order[position] = local node.
+std::vector<int> rcm_order(int n, const std::vector<int>& aptr, const std::vector<int>& adj) {
+  std::vector<int> order, queue(n), dist(n, 0), stamp(n, -1), nbr;
+  std::vector<char> placed(n, 0);
+  order.reserve(n);
+  auto deg = [&](int v) { return aptr[v + 1] - aptr[v]; };
+  int round = 0;
+  auto bfs = [&](int root) {  // over unplaced nodes; returns the visit count
+    ++round;
+    int head = 0, tail = 0;
+    queue[tail++] = root;
+    stamp[root] = round;
+    dist[root] = 0;
+    while (head < tail) {
+      const int v = queue[head++];
+      for (int p = aptr[v]; p < aptr[v + 1]; ++p) {
+        const int u = adj[p];
+        if (placed[u] || stamp[u] == round) continue;
+        stamp[u] = round;
+        dist[u] = dist[v] + 1;
+        queue[tail++] = u;
+      }
+    }
+    return tail;
+  };
+  for (int s = 0; s < n; ++s) {
+    if (placed[s]) continue;
+    int root = s, depth = -1;
+    for (int it = 0; it < 16; ++it) {
+      const int cnt = bfs(root);
+      const int d = dist[queue[cnt - 1]];
+      if (d <= depth) break;
+      depth = d;
+      int best = queue[cnt - 1];
+      for (int q = cnt - 1; q >= 0 && dist[queue[q]] == d; --q)
+        if (deg(queue[q]) < deg(best) || (deg(queue[q]) == deg(best) && queue[q] < best)) best = queue[q];
+      root = best;
+    }
+    size_t head = order.size();
+    order.push_back(root);
+    placed[root] = 1;
+    while (head < order.size()) {
+      const int v = order[head++];
+      nbr.clear();
+      for (int p = aptr[v]; p < aptr[v + 1]; ++p) {
+        const int u = adj[p];
+        if (!placed[u]) {
+          placed[u] = 1;
+          nbr.push_back(u);
+        }
+      }
+      std::sort(nbr.begin(), nbr.end(), [&](int x, int y) { return deg(x) != deg(y) ? deg(x) < deg(y) : x < y; });
+      order.insert(order.end(), nbr.begin(), nbr.end());
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
+
+}  // namespace
+
+size_t band_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    v = 227 * 1024;
+  }
+  return (size_t)v;
+}
+
+int band_plan(int n_f, int n_h, const long long* offset, const std::vector<int>& rp, const std::vector<int>& col,
+              const std::vector<double>& val, const std::vector<long long>& toff, const std::vector<int>& tnode,
+              BandHost& H, std::string& err) {
+  H = BandHost();
+  H.n_f = n_f;
+  H.w.assign(n_f, 0);
+  H.boff.assign(n_f + 1, 0);
+  H.gwoff.assign(n_f, -1);
+  H.pos.assign(n_h, 0);
+  H.perm.assign(n_h, 0);
+  H.trace_at.assign(n_h, -1);
+  const size_t optin = band_smem_optin();
+  std::vector<int> aptr, adj, seen(n_h, -1);
+  std::vector<double> work(n_f, 0.0);
+  for (int f = 0; f < n_f; ++f) {
+    const long long o = offset[f];
+    const int n = (int)(offset[f + 1] - o);
+    aptr.assign(n + 1, 0);
+    adj.clear();
+    for (int i = 0; i < n; ++i) {
+      const long long r = o + i;
+      bool diag = false;
+      for (int p = rp[r]; p < rp[r + 1]; ++p) {
+        const long long c = col[p];
+        if (c < o || c >= o + n) {
+          err = "A is not block diagonal: row " + std::to_string(r) + " of fracture " + std::to_string(f) +
+                " has column " + std::to_string(c);
+          return PP_EINVAL;
+        }
+        if (seen[c] == (int)r) {
+          err = "A has a repeated entry (" + std::to_string(r) + ", " + std::to_string(c) + ")";
+          return PP_EINVAL;
+        }
+        seen[c] = (int)r;
+        if (c == r) {
+          if (!(val[p] > 0.0)) {
+            err = "A is not positive definite: diagonal " + std::to_string(r) + " is not positive";
+            return PP_EBREAKDOWN;
+          }
+          diag = true;
+          continue;
+        }
+        // the mirrored entry must exist with the same value
+        bool sym = false;
+        for (int q = rp[c]; q < rp[c + 1]; ++q)
+          if (col[q] == r) {
+            sym = val[q] == val[p];
+            break;
+          }
+        if (!sym) {
+          err = "A is not symmetric at (" + std::to_string(r) + ", " + std::to_string(c) + ")";
+          return PP_EINVAL;
+        }
+        adj.push_back((int)(c - o));
+      }
+      if (!diag) {
+        err = "A has no diagonal entry in row " + std::to_string(r);
+        return PP_EINVAL;
+      }
+      aptr[i + 1] = (int)adj.size();
+    }
+    int w_nat = 0;
+    for (int i = 0; i < n; ++i)
+      for (int p = aptr[i]; p < aptr[i + 1]; ++p) w_nat = std::max(w_nat, std::abs(adj[p] - i));
+    std::vector<int> ord = rcm_order(n, aptr, adj), inv(n);
+    for (int p = 0; p < n; ++p) inv[ord[p]] = p;
+    int w_rcm = 0;
+    for (int i = 0; i < n; ++i)
+      for (int p = aptr[i]; p < aptr[i + 1]; ++p) w_rcm = std::max(w_rcm, std::abs(inv[adj[p]] - inv[i]));
+    const bool use_rcm = w_rcm < w_nat;
+    H.rcm_used += use_rcm ? 1 : 0;
+    const int w = use_rcm ? w_rcm : w_nat;
+    if (w > kBandMaxW) {
+      err = "fracture " + std::to_string(f) + ": half-bandwidth " + std::to_string(w) +
+            " after reordering is above " + std::to_string(kBandMaxW);
+      return PP_EUNSUPPORTED;
+    }
+    for (int p = 0; p < n; ++p) {
+      const int node = use_rcm ? ord[p] : p;
+      H.perm[o + p] = node;
+      H.pos[o + node] = p;
+    }
+    const int W = w + 1;
+    H.w[f] = w;
+    H.boff[f + 1] = H.boff[f] + (long long)n * W;
+    const size_t win_bytes = (size_t)(tri(W) + W) * sizeof(double);
+    if (win_bytes > optin) {
+      H.gwoff[f] = H.gwin_elems;
+      H.gwin_elems += tri(W) + W;
+    } else {
+      H.factor_smem = std::max(H.factor_smem, win_bytes);
+    }
+    H.max_w = std::max(H.max_w, w);
+    H.max_n = std::max(H.max_n, n);
+    work[f] = (double)n * W * W;
+  }
+  H.elems = H.boff[n_f];
+  H.order.resize(n_f);
+  std::iota(H.order.begin(), H.order.end(), 0);
+  std::stable_sort(H.order.begin(), H.order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  // trace columns of each fracture by position, in items of kBandCols
+  const int n_T = (int)tnode.size();
+  H.tcol.assign(std::max(n_T, 1), 0);
+  H.tpos.assign(std::max(n_T, 1), 0);
+  std::vector<std::pair<int, int>> slots;
+  std::vector<double> cost;
+  for (int f = 0; f < n_f; ++f) {
+    const long long t0 = toff[f], t1 = toff[f + 1], o = offset[f];
+    const int n = (int)(offset[f + 1] - o);
+    slots.clear();
+    for (long long a = 0; a < t1 - t0; ++a) {
+      const int node = tnode[t0 + a];
+      const int p = H.pos[node];
+      H.trace_at[o + p] = (int)a;
+      slots.push_back({p, (int)a});
+    }
+    std::sort(slots.begin(), slots.end());
+    for (size_t s = 0; s < slots.size(); ++s) {
+      H.tpos[t0 + s] = slots[s].first;
+      H.tcol[t0 + s] = slots[s].second;
+    }
+    for (size_t s0 = 0; s0 < slots.size(); s0 += kBandCols) {
+      const int cnt = (int)std::min<size_t>(kBandCols, slots.size() - s0);
+      H.items.push_back(make_int4(f, (int)s0, cnt, slots[s0].first));
+      cost.push_back((double)(2 * n - slots[s0].first) * (H.w[f] + 1));
+    }
+  }
+  std::vector<int> idx(H.items.size());
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int4> sorted(H.items.size());
+  for (size_t i = 0; i < idx.size(); ++i) sorted[i] = H.items[idx[i]];
+  H.items.swap(sorted);
+  H.n_items = (int)H.items.size();
+  return PP_OK;
+}
+
+cudaError_t band_fill(const BandDev& D, int n_h, const int* rp, const int* col, const double* val, cudaStream_t s) {
+  band_fill_kernel<<<grid_for(n_h, 256), 256, 0, s>>>(D, n_h, rp, col, val);
+  return cudaGetLastError();
+}
+
+cudaError_t band_factor(const BandDev& D, cudaStream_t s) {
+  cudaError_t e = allow_smem((const void*)band_factor_kernel, D.factor_smem);
+  if (e != cudaSuccess) return e;
+  band_factor_kernel<<<D.n_f, 256, D.factor_smem, s>>>(D);
+  return cudaGetLastError();
+}
+
+cudaError_t band_trace_blocks(const BandDev& D, const long long* toff, const long long* moff, double* M,
+                              cudaStream_t s) {
+  if (D.n_items > 0) {
+    const size_t sm = sizeof(double) * ((size_t)kBandWarps * kBandCols + kBandCols + (size_t)(D.max_w + 1) * kBandCols);
+    cudaError_t e = allow_smem((const void*)band_trace_kernel, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.flags + 1, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    band_trace_kernel<<<D.grid_trace, kBandWarps * 32, sm, s>>>(D, toff, moff, M);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  band_symmetrize_kernel<<<152 * 8, 256, 0, s>>>(D.n_f, toff, moff, M);
+  return cudaGetLastError();
+}
+
+cudaError_t band_solve(const BandDev& D, const double* v, double* y, double* z, cudaStream_t s) {
+  constexpr int kWarps = 4;
+  const size_t sm = sizeof(double) * kWarps * (size_t)(D.max_w + 1);
+  cudaError_t e = allow_smem((const void*)band_solve_kernel, sm);
+  if (e != cudaSuccess) return e;
+  band_solve_kernel<<<(D.n_f + kWarps - 1) / kWarps, kWarps * 32, sm, s>>>(D, v, y, z);
+  return cudaGetLastError();
+}
+
+}  // namespace pp

@@ -102,6 +102,10 @@ struct pp_ctx {
   std::vector<double> rho;
   int lanczos_steps_done = 0;
   double t_setup_ms = 0;
+  // Schur context with general blocks: banded Cholesky factors
+  int band_max = 0;
+  long long band_elems = 0;
+  double t_band_ms = 0;
   std::string err;
   std::vector<cudaEvent_t> events;
   cudaStream_t cap_stream = nullptr;

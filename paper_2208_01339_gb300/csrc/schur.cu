@@ -20,6 +20,11 @@
 // Algorithm 4 (D_S) uses the same M.  Full-vector solves with A (right-hand
 // side, recovery of h and p) use fast diagonalisation: sine transform along
 // x, a Thomas solve along y per mode, inverse transform.
+//
+// Fractures of any other shape or coefficients are given as the caller's
+// block-diagonal CSR A; M and the full solves then come from a banded
+// Cholesky factor of each block (band.cu), and everything downstream of M
+// is shared.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -28,6 +33,7 @@
 #include <string>
 #include <vector>
 
+#include "band.cuh"
 #include "driver.cuh"
 #include "step_impl.cuh"
 
@@ -46,6 +52,10 @@ struct SchurImpl {
   int n_f = 0, n_h = 0, n_u = 0, n_T = 0, max_t = 0, max_nx = 0;
   long long m_elems = 0, s_elems = 0, u_elems = 0, rows_y = 0;
   double alpha = 0.0;
+  // general blocks: banded Cholesky factors instead of the closed form
+  bool general = false;
+  long long band_elems = 0;
+  BandDev band;
   // fracture metadata (device)
   int *nx = nullptr, *ny = nullptr;
   double* T = nullptr;
@@ -415,6 +425,8 @@ struct HCsr {
 
 struct TracePlan {
   int n_T = 0, max_t = 0, max_nx = 0;
+  bool general = false;
+  BandHost band;  // general blocks only
   std::vector<int> tnode;             // global node of trace index
   std::vector<int> tfrac, tloc;       // fracture, local grid index
   std::vector<long long> toff, moff, soff, loff, uoff, yoff;
@@ -444,7 +456,10 @@ int download(const int* rp, const int* ci, const double* va, int nrows, HCsr& h,
 int check_dfn(const pp_dfn* d) {
   if (!d) return fail(nullptr, PP_EINVAL, "pp_dfn is NULL");
   if (d->n_f <= 0 || d->n_h <= 0 || d->n_u <= 0) return fail(nullptr, PP_EINVAL, "n_f, n_h, n_u must be positive");
-  if (!d->nx || !d->ny || !d->T || !d->offset) return fail(nullptr, PP_EINVAL, "fracture metadata is NULL");
+  const bool general = d->A_rowptr != nullptr;
+  if (!d->offset) return fail(nullptr, PP_EINVAL, "fracture offsets are NULL");
+  if (general && (!d->A_col || !d->A_val)) return fail(nullptr, PP_EINVAL, "A_col or A_val is NULL");
+  if (!general && (!d->nx || !d->ny || !d->T)) return fail(nullptr, PP_EINVAL, "fracture metadata is NULL");
   const void* ptrs[] = {d->C_rowptr, d->C_col, d->C_val, d->B_rowptr, d->B_col, d->B_val, d->CT_rowptr,
                         d->CT_col, d->CT_val, d->BT_rowptr, d->BT_col, d->BT_val, d->Gh_rowptr, d->Gh_col,
                         d->Gh_val, d->Gu_rowptr, d->Gu_col, d->Gu_val};
@@ -452,6 +467,9 @@ int check_dfn(const pp_dfn* d) {
     if (!p) return fail(nullptr, PP_EINVAL, "a fracture-network CSR array is NULL");
   if (d->offset[0] != 0 || d->offset[d->n_f] != d->n_h) return fail(nullptr, PP_EINVAL, "offset must span [0, n_h]");
   for (int f = 0; f < d->n_f; ++f) {
+    if (d->offset[f + 1] <= d->offset[f])
+      return fail(nullptr, PP_EINVAL, "fracture " + std::to_string(f) + " has no nodes");
+    if (general) continue;
     if (d->nx[f] <= 0 || d->ny[f] <= 0 || !(d->T[f] > 0.0))
       return fail(nullptr, PP_EINVAL, "fracture " + std::to_string(f) + ": nx, ny, T must be positive");
     if (d->offset[f + 1] - d->offset[f] != (long long)d->nx[f] * d->ny[f])
@@ -506,11 +524,13 @@ int plan_traces(const pp_dfn* d, TracePlan& P, cudaStream_t s) {
   P.loff.assign(nf + 1, 0);
   P.uoff.assign(nf + 1, 0);
   P.yoff.assign(nf + 1, 0);
+  P.general = d->A_rowptr != nullptr;
   for (int g = 0; g < nf; ++g) {
     const long long t = P.toff[g + 1] - P.toff[g];
     P.max_t = std::max<long long>(P.max_t, t);
-    P.max_nx = std::max(P.max_nx, d->nx[g]);
     P.moff[g + 1] = P.moff[g] + t * t;
+    if (P.general) continue;  // no closed-form tables
+    P.max_nx = std::max(P.max_nx, d->nx[g]);
     P.soff[g + 1] = P.soff[g] + (long long)d->nx[g] * d->nx[g];
     P.loff[g + 1] = P.loff[g] + d->nx[g];
     P.uoff[g + 1] = P.uoff[g] + (long long)d->nx[g] * (d->ny[g] + 1);
@@ -548,6 +568,15 @@ int plan_traces(const pp_dfn* d, TracePlan& P, cudaStream_t s) {
   for (const HCsr* X : {&P.C_T, &P.B_T})
     for (int p = 0; p < X->rp[X->nrows]; ++p)
       if (X->col[p] < 0 || X->col[p] >= d->n_u) return fail(nullptr, PP_EINVAL, "C/B column out of range");
+  if (P.general) {
+    HCsr A;
+    if ((rc = download(d->A_rowptr, d->A_col, d->A_val, d->n_h, A, s))) return rc;
+    for (int p = 0; p < A.rp[nh]; ++p)
+      if (A.col[p] < 0 || A.col[p] >= nh) return fail(nullptr, PP_EINVAL, "A column out of range");
+    std::string err;
+    if ((rc = band_plan(nf, nh, d->offset, A.rp, A.col, A.val, P.toff, P.tnode, P.band, err)))
+      return fail(nullptr, rc, err);
+  }
   return PP_OK;
 }
 
@@ -615,6 +644,33 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
   S->CT_T = put_csr(B, P.CT_T, up);
   S->BT_T = put_csr(B, P.BT_T, up);
   S->M = B.take<double>(P.m_elems);
+  S->general = P.general;
+  if (P.general) {
+    const BandHost& H = P.band;
+    BandDev& D = S->band;
+    D.n_f = d->n_f;
+    D.max_w = H.max_w;
+    D.max_n = H.max_n;
+    D.n_items = H.n_items;
+    D.factor_smem = H.factor_smem;
+    D.off = S->off;
+    D.w = put(B, H.w, up);
+    D.boff = put(B, H.boff, up);
+    D.gwoff = put(B, H.gwoff, up);
+    D.pos = put(B, H.pos, up);
+    D.perm = put(B, H.perm, up);
+    D.trace_at = put(B, H.trace_at, up);
+    D.order = put(B, H.order, up);
+    D.tcol = put(B, H.tcol, up);
+    D.tpos = put(B, H.tpos, up);
+    D.items = put(B, H.items, up);
+    D.L = B.take<double>(H.elems);
+    D.gwin = B.take<double>(H.gwin_elems);
+    D.grid_trace = std::max(1, std::min(H.n_items, 2 * num_sms()));
+    D.Z = B.take<double>((long long)D.grid_trace * H.max_n * kBandCols);
+    D.flags = B.take<int>(2);
+    S->band_elems = H.elems;
+  }
   S->S = B.take<double>(P.soff.back());
   S->lam = B.take<double>(P.loff.back());
   S->U = B.take<double>(P.uoff.back());
@@ -672,8 +728,10 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
   return B.off + 256;
 }
 
-// Full solve y = A^{-1} v by fast diagonalisation.
+// Full solve y = A^{-1} v: banded Cholesky factors for general blocks, else
+// fast diagonalisation.
 cudaError_t ainv_full(const SchurImpl* S, const double* v, double* y, cudaStream_t s) {
+  if (S->general) return band_solve(S->band, v, y, S->fd, s);
   const size_t sm = (size_t)(kBlock / 32) * S->max_nx * sizeof(double);
   const int g_rows = grid_of(S->rows_y * 32);
   fd_transform_kernel<<<g_rows, kBlock, sm, s>>>(S->n_f, S->yoff, S->off, S->nx, S->soff, S->S, v, S->fc,
@@ -799,8 +857,14 @@ namespace {
 int prepare(pp_ctx* c, SchurImpl* S, const pp_dfn* d, TracePlan& P, void* base, bool upload, cudaStream_t s,
             size_t* bytes) {
   std::vector<long long> offh(d->offset, d->offset + d->n_f + 1);
-  std::vector<int> nxh(d->nx, d->nx + d->n_f), nyh(d->ny, d->ny + d->n_f);
-  std::vector<double> Th(d->T, d->T + d->n_f);
+  // general blocks carry no grid metadata (nx, ny, T may be NULL)
+  std::vector<int> nxh(d->n_f, 0), nyh(d->n_f, 0);
+  std::vector<double> Th(d->n_f, 0.0);
+  if (!P.general) {
+    nxh.assign(d->nx, d->nx + d->n_f);
+    nyh.assign(d->ny, d->ny + d->n_f);
+    Th.assign(d->T, d->T + d->n_f);
+  }
   std::vector<std::pair<void*, std::pair<const void*, size_t>>> up;
   *bytes = layout_schur(c, S, d, P, base, upload ? &up : nullptr, &offh, &nxh, &nyh, &Th);
   if (!upload) return PP_OK;
@@ -900,11 +964,49 @@ extern "C" int schur_setup(pp_ctx** out, const pp_dfn* d, const pp_options* opt,
   cudaError_t e = cudaMemsetAsync(c->vec_begin, 0, (char*)c->vec_end - (char*)c->vec_begin, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->sc, 0, sizeof(Scalars), s);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "clearing workspace"));
-  // sine tables, eigenvalues, U tables, the trace blocks M, then D_S (Algorithm 4)
-  sine_tables_kernel<<<grid_of(S->s_elems), kBlock, 0, s>>>(S->n_f, S->nx, S->soff, S->loff, S->S, S->lam);
-  cheb_u_kernel<<<grid_of(S->u_elems), kBlock, 0, s>>>(S->n_f, S->nx, S->ny, S->loff, S->uoff, S->lam, S->U);
-  m_blocks_kernel<<<grid_of(S->m_elems), kBlock, 0, s>>>(S->n_f, S->toff, S->moff, S->nx, S->ny, S->T, S->soff,
-                                                         S->uoff, S->tloc, S->S, S->U, S->M);
+  if (S->general) {
+    // banded Cholesky of every block, then M from band solves
+    cudaEvent_t b0 = nullptr, b1 = nullptr;
+    cudaEventCreate(&b0);
+    cudaEventCreate(&b1);
+    cudaEventRecord(b0, s);
+    e = cudaMemsetAsync(S->band.L, 0, sizeof(double) * (size_t)S->band_elems, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->band.flags, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = band_fill(S->band, d->n_h, d->A_rowptr, d->A_col, d->A_val, s);
+    if (e == cudaSuccess) e = band_factor(S->band, s);
+    int bad_f = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_f, S->band.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(b0);
+      cudaEventDestroy(b1);
+      return bail(cuda_fail(c, e, "banded Cholesky of the fracture blocks"));
+    }
+    if (bad_f) {
+      cudaEventDestroy(b0);
+      cudaEventDestroy(b1);
+      return bail(fail(c, PP_EBREAKDOWN,
+                       "A_f of fracture " + std::to_string(bad_f - 1) + " is not positive definite"));
+    }
+    e = band_trace_blocks(S->band, S->toff, S->moff, S->M, s);
+    cudaEventRecord(b1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b1);
+    float bms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&bms, b0, b1);
+    cudaEventDestroy(b0);
+    cudaEventDestroy(b1);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "trace blocks from the band factors"));
+    c->band_max = P.band.max_w;
+    c->band_elems = S->band_elems;
+    c->t_band_ms = bms;
+  } else {
+    // sine tables, eigenvalues, U tables, the trace blocks M
+    sine_tables_kernel<<<grid_of(S->s_elems), kBlock, 0, s>>>(S->n_f, S->nx, S->soff, S->loff, S->S, S->lam);
+    cheb_u_kernel<<<grid_of(S->u_elems), kBlock, 0, s>>>(S->n_f, S->nx, S->ny, S->loff, S->uoff, S->lam, S->U);
+    m_blocks_kernel<<<grid_of(S->m_elems), kBlock, 0, s>>>(S->n_f, S->toff, S->moff, S->nx, S->ny, S->T, S->soff,
+                                                           S->uoff, S->tloc, S->S, S->U, S->M);
+  }
+  // then D_S (Algorithm 4)
   if (c->mixed) e = sell_convert_values(S->m_elems, S->M, S->M32, kF32, s);  // M rounded to FP32
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "FP32 copy of M"));
   int* d_bad = reinterpret_cast<int*>(c->t1);

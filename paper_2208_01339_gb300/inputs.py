@@ -45,6 +45,7 @@ STREAM_LANCZOS = 3
 STREAM_FRACTURE = 4
 STREAM_TRACE = 5
 STREAM_BATCH = 6
+STREAM_GENERAL = 8  # general fracture blocks (mesh jitter, diagonals, coefficients, numbering)
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -456,6 +457,166 @@ def fracture_network(n_f: int = 200, side_min: float = 5.0, side_max: float = 50
                            C=Cm, B=Bm, CT=CT, BT=BT, Gh=Gh, Gu=Gu, q=q, alpha=float(alpha),
                            own_node=own_node, partner_node=partner_node, pair=pair_arr,
                            meta={"n_traces": n_traces, "seed": seed, "h": h})
+
+
+def _coo_sum_to_csr(nrows: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray) -> tuple:
+    """CSR with repeated (row, col) entries summed in their input order."""
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    first = np.ones(rows.size, dtype=bool)
+    first[1:] = (rows[1:] != rows[:-1]) | (cols[1:] != cols[:-1])
+    starts = np.nonzero(first)[0]
+    sums = np.add.reduceat(vals, starts) if vals.size else vals
+    return _coo_to_csr(nrows, rows[starts], cols[starts], sums)
+
+
+def _p1_blocks(nx, ny, T, offset, jitter: float, k_sigma: float, seed: int) -> CSR:
+    """P1 finite-element stiffness of -div(k grad h) on each fracture.
+
+    The fracture's node grid, with a boundary ring of Dirichlet nodes around
+    the nx x ny interior nodes (eliminated), is moved by jitter * U(-1,1)
+    per interior coordinate (grid units; jitter < 1/2 keeps every triangle
+    positively oriented) and every cell is split along a random diagonal.
+    Each triangle has k = T_f exp(k_sigma N(0,1)).  Element matrices
+    k (b_a b_b + c_a c_b) / (4 area) (b, c the edge-normal components).
+    Interior node (ix, iy) keeps the index iy*nx + ix of the rectangle, so
+    trace nodes are unchanged.  The lower triangle is assembled and mirrored,
+    so the matrix is exactly symmetric.
+    """
+    rows_l, cols_l, vals_l = [], [], []
+    ofs = 0
+    for f in range(len(nx)):
+        mx, my, o = int(nx[f]), int(ny[f]), int(offset[f])
+        ex, ey = mx + 2, my + 2
+        ncell = (mx + 1) * (my + 1)
+        gx = np.tile(np.arange(ex, dtype=np.float64), ey)
+        gy = np.repeat(np.arange(ey, dtype=np.float64), ex)
+        ix = np.tile(np.arange(ex), ey)
+        iy = np.repeat(np.arange(ey), ex)
+        inner = (ix >= 1) & (ix <= mx) & (iy >= 1) & (iy <= my)
+        ni = int(inner.sum())
+        jx = (2.0 * uniform(seed, STREAM_GENERAL, ni, ofs) - 1.0) * jitter
+        jy = (2.0 * uniform(seed, STREAM_GENERAL, ni, ofs + ni) - 1.0) * jitter
+        ofs += 2 * ni
+        gx[inner] += jx
+        gy[inner] += jy
+        lidx = np.where(inner, (iy - 1) * mx + (ix - 1), -1)
+        diag = uniform(seed, STREAM_GENERAL, ncell, ofs) < 0.5
+        ofs += ncell
+        u = uniform(seed, STREAM_GENERAL, 4 * ncell, ofs)
+        ofs += 4 * ncell
+        z = np.sqrt(-2.0 * np.log(1.0 - u[0::2])) * np.cos(2.0 * np.pi * u[1::2])  # 2 ncell normals
+        cx = np.tile(np.arange(mx + 1), my + 1)
+        cy = np.repeat(np.arange(my + 1), mx + 1)
+        n00 = cy * ex + cx
+        n10 = n00 + 1
+        n01 = n00 + ex
+        n11 = n01 + 1
+        t1 = np.where(diag[:, None], np.stack([n00, n10, n11], 1), np.stack([n00, n10, n01], 1))
+        t2 = np.where(diag[:, None], np.stack([n00, n11, n01], 1), np.stack([n10, n11, n01], 1))
+        tri = np.concatenate([t1, t2])
+        kt = float(T[f]) * np.exp(k_sigma * z)
+        x = gx[tri]
+        y = gy[tri]
+        b = np.stack([y[:, 1] - y[:, 2], y[:, 2] - y[:, 0], y[:, 0] - y[:, 1]], 1)
+        c = np.stack([x[:, 2] - x[:, 1], x[:, 0] - x[:, 2], x[:, 1] - x[:, 0]], 1)
+        area = 0.5 * np.abs((x[:, 1] - x[:, 0]) * (y[:, 2] - y[:, 0]) - (x[:, 2] - x[:, 0]) * (y[:, 1] - y[:, 0]))
+        for aa in range(3):
+            for bb in range(aa, 3):
+                ka = kt * (b[:, aa] * b[:, bb] + c[:, aa] * c[:, bb]) / (4.0 * area)
+                ga, gb = lidx[tri[:, aa]], lidx[tri[:, bb]]
+                ok = (ga >= 0) & (gb >= 0)
+                rows_l.append(o + np.maximum(ga[ok], gb[ok]))
+                cols_l.append(o + np.minimum(ga[ok], gb[ok]))
+                vals_l.append(ka[ok])
+    n = int(offset[-1])
+    rp, cc, vv = _coo_sum_to_csr(n, np.concatenate(rows_l), np.concatenate(cols_l), np.concatenate(vals_l))
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    strict = rows != cc
+    rowptr, col, val = _coo_to_csr(n, np.concatenate([rows, cc[strict]]), np.concatenate([cc, rows[strict]]),
+                                   np.concatenate([vv, vv[strict]]))
+    return CSR(n, rowptr, col, val, {"kind": "dfn_A_p1"})
+
+
+def _relabel_network(net: FractureNetwork, new: np.ndarray) -> FractureNetwork:
+    """The same network with node i renamed new[i] (a permutation that maps
+    every fracture's range onto itself): A, G^h rows and columns, the rows of
+    C, B, the columns of C^T, B^T, q and the trace node lists."""
+    n = net.n_h
+
+    def rows_of(X):
+        r = np.repeat(np.arange(X.nrows if hasattr(X, "nrows") else X.n), np.diff(X.rowptr))
+        return r
+
+    def sq(X, kind):
+        r = rows_of(X)
+        rp, cc, vv = _coo_to_csr(n, new[r], new[X.col], X.val)
+        return CSR(n, rp, cc, vv, {"kind": kind})
+
+    def rect_rows(X):
+        r = rows_of(X)
+        rp, cc, vv = _coo_to_csr(X.nrows, new[r], X.col.astype(np.int64), X.val)
+        return RectCSR(X.nrows, X.ncols, rp, cc, vv)
+
+    def rect_cols(X):
+        r = rows_of(X)
+        rp, cc, vv = _coo_to_csr(X.nrows, r, new[X.col], X.val)
+        return RectCSR(X.nrows, X.ncols, rp, cc, vv)
+
+    q = np.empty_like(net.q)
+    q[new] = net.q
+    return FractureNetwork(nx=net.nx, ny=net.ny, T=net.T, offset=net.offset, A=sq(net.A, net.A.meta.get("kind")),
+                           C=rect_rows(net.C), B=rect_rows(net.B), CT=rect_cols(net.CT), BT=rect_cols(net.BT),
+                           Gh=sq(net.Gh, "dfn_Gh"), Gu=net.Gu, q=q, alpha=net.alpha, own_node=new[net.own_node],
+                           partner_node=new[net.partner_node], pair=net.pair, meta=dict(net.meta))
+
+
+def general_fracture_network(net: FractureNetwork, jitter: float = 0.25, k_sigma: float = 1.0, seed: int = 11,
+                             shuffle: bool = True) -> FractureNetwork:
+    """The network `net` with fracture blocks of general form: A_f is the P1
+    stiffness of a jittered, randomly split triangulation with lognormal
+    coefficients (see _p1_blocks), and with shuffle the nodes of every
+    fracture are renumbered by a seeded random permutation (so that the
+    given numbering has no band structure).  Traces, C, B, G^h, G^u and q
+    are those of `net`, carried along by the renumbering.  The rectangle
+    metadata (nx, ny, T) no longer describes A; meta["general"] is set.
+    """
+    A = _p1_blocks(net.nx, net.ny, net.T, net.offset, jitter, k_sigma, seed)
+    out = FractureNetwork(nx=net.nx, ny=net.ny, T=net.T, offset=net.offset, A=A, C=net.C, B=net.B, CT=net.CT,
+                          BT=net.BT, Gh=net.Gh, Gu=net.Gu, q=net.q, alpha=net.alpha, own_node=net.own_node,
+                          partner_node=net.partner_node, pair=net.pair, meta=dict(net.meta))
+    if shuffle:
+        u = uniform(seed, STREAM_GENERAL + 1, net.n_h)
+        new = np.empty(net.n_h, dtype=np.int64)
+        for f in range(net.n_f):
+            o, e = int(net.offset[f]), int(net.offset[f + 1])
+            new[o:e] = o + np.argsort(np.argsort(u[o:e], kind="stable"), kind="stable")
+        out = _relabel_network(out, new)
+    out.meta.update({"general": True, "jitter": jitter, "k_sigma": k_sigma, "general_seed": seed,
+                     "shuffled": shuffle})
+    return out
+
+
+def with_dense_block(net: FractureNetwork, f: int, seed: int = 13) -> FractureNetwork:
+    """The network with A_f replaced by the dense SPD block A_f + g g^T / n_f
+    (g ~ N(0,1), seeded): a block whose band cannot be narrowed by any
+    reordering.  meta["general"] is set."""
+    o, e = int(net.offset[f]), int(net.offset[f + 1])
+    nf = e - o
+    D = net.A.to_dense()
+    g = normal(seed, STREAM_GENERAL + 2, nf)
+    blk = D[o:e, o:e] + np.outer(g, g) / nf
+    D[o:e, o:e] = 0.5 * (blk + blk.T)
+    mask = D != 0.0
+    mask[o:e, o:e] = True
+    rows, cols = np.nonzero(mask)
+    rp, cc, vv = _coo_to_csr(net.n_h, rows, cols, D[rows, cols])
+    A = CSR(net.n_h, rp, cc, vv, {"kind": "dfn_A_dense_block"})
+    out = FractureNetwork(nx=net.nx, ny=net.ny, T=net.T, offset=net.offset, A=A, C=net.C, B=net.B, CT=net.CT,
+                          BT=net.BT, Gh=net.Gh, Gu=net.Gu, q=net.q, alpha=net.alpha, own_node=net.own_node,
+                          partner_node=net.partner_node, pair=net.pair, meta=dict(net.meta))
+    out.meta.update({"general": True, "dense_block": f})
+    return out
 
 
 def tiny_fracture_network(seed: int = 7) -> FractureNetwork:

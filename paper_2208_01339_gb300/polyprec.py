@@ -69,7 +69,8 @@ class Info(ctypes.Structure):
                 ("delta", ctypes.c_double), ("sigma_bar", ctypes.c_double), ("k", ctypes.c_int),
                 ("apply_prec", ctypes.c_int), ("lanczos_steps_done", ctypes.c_int), ("t_setup_ms", ctypes.c_double),
                 ("grid_blocks", ctypes.c_int), ("ndiag", ctypes.c_int), ("lowrank", ctypes.c_int),
-                ("lowrank_steps_done", ctypes.c_int), ("ritz_resid", ctypes.c_double), ("theta_min", ctypes.c_double)]
+                ("lowrank_steps_done", ctypes.c_int), ("ritz_resid", ctypes.c_double), ("theta_min", ctypes.c_double),
+                ("band_max", ctypes.c_int), ("band_elems", ctypes.c_longlong), ("t_factor_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -96,7 +97,8 @@ _DFN_MATS = ("C", "B", "CT", "BT", "Gh", "Gu")
 class Dfn(ctypes.Structure):
     _fields_ = [("n_f", ctypes.c_int), ("n_h", ctypes.c_int), ("n_u", ctypes.c_int), ("nx", _vp), ("ny", _vp),
                 ("T", _vp), ("offset", _vp)] + [
-        (f"{m}_{p}", _vp) for m in _DFN_MATS for p in ("rowptr", "col", "val")] + [("alpha_reg", ctypes.c_double)]
+        (f"{m}_{p}", _vp) for m in _DFN_MATS for p in ("rowptr", "col", "val")] + [("alpha_reg", ctypes.c_double)] + [
+        (f"A_{p}", _vp) for p in ("rowptr", "col", "val")]
 
 
 _lib = None
@@ -348,9 +350,14 @@ class Solver:
 
 
 class SchurSolver(Solver):
-    """PCG on the D_S-scaled Schur complement S_u of a fracture network."""
+    """PCG on the D_S-scaled Schur complement S_u of a fracture network.
 
-    def __init__(self, net, device="cuda", stream=None, **options):  # noqa: D401
+    general=True hands the network's block-diagonal A to the library
+    (banded Cholesky factors of the fracture blocks) instead of the
+    rectangle metadata (closed-form inverse blocks); the default follows
+    net.meta["general"]."""
+
+    def __init__(self, net, device="cuda", stream=None, general=None, **options):  # noqa: D401
         torch = _torch()
         self.n = int(net.n_u)
         self.opts = make_options(**options)
@@ -378,6 +385,12 @@ class SchurSolver(Solver):
             setattr(d, f"{m}_col", dev(M.col, np.int32))
             setattr(d, f"{m}_val", dev(M.val, np.float64))
         d.alpha_reg = float(net.alpha)
+        if general is None:
+            general = bool(net.meta.get("general", False))
+        if general:
+            d.A_rowptr = dev(net.A.rowptr, np.int32)
+            d.A_col = dev(net.A.col, np.int32)
+            d.A_val = dev(net.A.val, np.float64)
         self._keep = keep
         self._dfn = d
         nbytes = ctypes.c_size_t()

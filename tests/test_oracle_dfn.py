@@ -33,9 +33,21 @@ def dense_schur(net):
     return Gu - a * B.T @ Ai @ C - a * C.T @ Ai @ B + C.T @ Ai @ Gh @ Ai @ C
 
 
-@pytest.fixture(scope="module", params=[None, 5, 9])
+NETS = {
+    "tiny": lambda: I.tiny_fracture_network(),
+    "small5": lambda: small_net(5),
+    "small9": lambda: small_net(9),
+    # general fracture blocks: P1 stiffness on jittered triangulations with
+    # lognormal coefficients, nodes renumbered at random; and one dense block
+    "p1_tiny": lambda: I.general_fracture_network(I.tiny_fracture_network(), seed=3),
+    "p1_small5": lambda: I.general_fracture_network(small_net(5)),
+    "dense_small9": lambda: I.with_dense_block(small_net(9), 2),
+}
+
+
+@pytest.fixture(scope="module", params=list(NETS))
 def net(request):
-    return I.tiny_fracture_network() if request.param is None else small_net(request.param)
+    return NETS[request.param]()
 
 
 def test_block_properties(net):
@@ -115,3 +127,21 @@ def test_schur_solve_and_recovery_match_K0(net):
     h, p = S.recover(net.q, u)
     for got, ref in ((u, u_ref), (h, h_ref), (p, p_ref)):
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
+
+
+def test_general_blocks_are_general():
+    """The general blocks leave the rectangle form: obtuse triangles give
+    positive off-diagonal entries, rows have up to 9 entries, and the random
+    numbering spreads each block over its whole index range."""
+    base = small_net(5)
+    g = I.general_fracture_network(base)
+    A = g.A.to_dense()
+    assert np.array_equal(A, A.T)
+    assert np.linalg.eigvalsh(A).min() > 0
+    off = ~np.eye(g.n_h, dtype=bool)
+    assert (A[off] > 0).any() and np.diff(g.A.rowptr).max() > 5
+    rows = np.repeat(np.arange(g.n_h), np.diff(g.A.rowptr))
+    assert np.abs(rows - g.A.col).max() > 4 * int(np.minimum(base.nx, base.ny).max())
+    # the numbering is a relabelling: S_u is unchanged by it
+    unshuffled = I.general_fracture_network(base, shuffle=False)
+    np.testing.assert_allclose(dense_schur(g), dense_schur(unshuffled), rtol=0, atol=1e-12 * np.abs(dense_schur(g)).max())
