@@ -318,6 +318,7 @@ def run_dfn_sweep(args, w, net, dopts, dev):
         info = S.info()
         print(json.dumps({"workload": args.workload, "k": k, "poly": dopts["poly"], "lowrank": dopts["lowrank"],
                           "band_max": info["band_max"], "factor_ms": round(info["t_factor_ms"], 2),
+                          "trace_blocks_ms": round(info["t_trace_ms"], 2),
                           "lanczos_steps": dopts["lanczos_steps"], "iterations": st["iterations"],
                           "time_s": statistics.median(ts) / 1e3, "mvp": st["mvp"], "dots": st["dots"],
                           "setup_ms": round(info["t_setup_ms"], 2), "alpha_hat": info["alpha_hat"],
@@ -437,7 +438,7 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
                           "a_inverse": ("banded Cholesky per fracture" if info["band_max"] else
                                         "closed form (uniform rectangles)"),
                           "band_max": info["band_max"], "band_doubles": info["band_elems"]},
-               "factor_ms": round(info["t_factor_ms"], 2),
+               "factor_ms": round(info["t_factor_ms"], 2), "trace_blocks_ms": round(info["t_trace_ms"], 2),
                "iterations": it, "setup_ms": round(info["t_setup_ms"], 2), "alpha_hat": info["alpha_hat"],
                "beta_hat": info["beta_hat"], "xi": info["xi"],
                "apply_ms": sum(s["t_apply_ms"] for s in stats) / max(1, sum(s["apply_launches"] for s in stats)),

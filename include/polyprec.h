@@ -156,8 +156,9 @@ typedef struct {
   int band_max;       /* Schur context with general blocks: largest
                          half-bandwidth of the fracture factors; else 0   */
   long long band_elems; /* doubles of band storage of those factors       */
-  double t_factor_ms; /* device time of the factorisation and the trace
-                         blocks built from it (part of t_setup_ms)         */
+  double t_factor_ms; /* device time of the band factorisation          */
+  double t_trace_ms;  /* device time of the trace blocks M_f built from
+                         the factors (both part of t_setup_ms)             */
 } pp_info;
 
 /* Fill *opt with defaults: k=20, xi=-1 (auto), Lanczos with 10 steps, seed 0,

@@ -565,6 +565,7 @@ extern "C" int pp_get_info(const pp_ctx* c, pp_info* info) {
   info->band_max = c->band_max;
   info->band_elems = c->band_elems;
   info->t_factor_ms = c->t_band_ms;
+  info->t_trace_ms = c->t_trace_ms;
   return PP_OK;
 }
 

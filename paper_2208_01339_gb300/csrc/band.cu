@@ -16,10 +16,18 @@
 // unit vectors are zero above it).  Lanes are columns, warps split the band.
 // Forward L y = e in dot form over row i of L; backward L^T x = y in axpy form
 // over the same row (x_i is final once rows i+1..i+w have been applied), so
-// both sweeps read L by rows.  Rows of x that are trace nodes are written
-// into M_f.  Items are handed out largest first from a device counter.
+// both sweeps read L by rows.  The backward sweep also stops at the first
+// column: M_f is symmetric, and an entry above it is the mirror of one the
+// earlier column computes.  Rows of x that are trace nodes are written into
+// M_f.  Items are handed out largest first from a device counter.
 //
 // Full solves: one warp per fracture, the same two sweeps on one vector.
+//
+// The sweeps are latency chains (row i needs row i-1), so the rows of the
+// factor they read -- with the pivot reciprocals and the vector entries of
+// the same step -- are copied into shared memory a few rows ahead with
+// cp.async; the factorisation loads the row that enters its window one
+// column ahead into registers.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -64,15 +72,32 @@ __global__ void band_fill_kernel(BandDev D, int n_h, const int* __restrict__ rp,
   }
 }
 
-__global__ void __launch_bounds__(256) band_factor_kernel(BandDev D) {
+constexpr int kFactorThreads = 256;
+constexpr int kFactorPre = (kBandMaxW + 1 + kFactorThreads - 1) / kFactorThreads;  // new-row values per thread
+constexpr int kRowsAhead = 4;  // band rows in flight (cp.async ring) in the solve sweeps
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__global__ void __launch_bounds__(kFactorThreads, 1) band_factor_kernel(BandDev D) {
   extern __shared__ double band_sm[];
   const int f = D.order[blockIdx.x];
   const long long o = D.off[f];
   const int n = (int)(D.off[f + 1] - o), w = D.w[f], W = w + 1;
   double* L = D.L + D.boff[f];
+  double* dinv = D.dinv + o;
   double* win = D.gwoff[f] >= 0 ? D.gwin + D.gwoff[f] : band_sm;
   double* lcol = win + tri(W);
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nt = kFactorThreads;
   // rows 0..w are all live at column 0
   const int r0 = min(w, n - 1);
   for (int i = 0; i <= r0; ++i)
@@ -80,6 +105,15 @@ __global__ void __launch_bounds__(256) band_factor_kernel(BandDev D) {
   __syncthreads();
   bool bad = false;
   for (int j = 0; j < n; ++j) {
+    // the row entering at the end of this column, loaded now so that its
+    // latency hides behind the column's work
+    const int inew = j + W;
+    double pre[kFactorPre];
+#pragma unroll
+    for (int u = 0; u < kFactorPre; ++u) {
+      const int q = tid + u * nt;
+      pre[u] = inew < n && q < W ? L[(long long)inew * W + w - inew + (j + 1 + q)] : 0.0;
+    }
     const double ajj = win[wslot(j, j, W)];
     const bool ok = ajj > 0.0;  // false for NaN too
     bad |= !ok;
@@ -91,19 +125,65 @@ __global__ void __launch_bounds__(256) band_factor_kernel(BandDev D) {
       lcol[r] = l;
       L[(long long)(j + r) * W + w - r] = l;
     }
-    if (tid == 0) L[(long long)j * W + w] = d;
+    if (tid == 0) {
+      L[(long long)j * W + w] = d;
+      dinv[j] = rd;
+    }
     __syncthreads();
-    // rank-one update of rows j+r, columns j+s, 1 <= s <= r <= m; thread p
-    // takes rows p+1 and m-p, m+1 updates in all
-    const int half = (m + 1) >> 1;
-    for (int p = tid; p < half; p += nt) {
-      for (int h = 0; h < 2; ++h) {
-        const int r = h == 0 ? p + 1 : m - p;
-        if (h == 1 && r == p + 1) break;
+    // rank-one update of rows j+r, columns j+s, 1 <= s <= r <= m.  Rows are
+    // folded in pairs (p+1, m-p) of m+1 updates each; the pairs laid end to
+    // end are cut into one equal run per thread, so every warp (and every
+    // SM sub-partition's FP64 unit) gets the same share.  Four slots at a
+    // time are read before any is written (they are distinct).
+    const int half = (m + 1) >> 1, per = m + 1;
+    const int total = half * per;
+    const int chunk = (total + nt - 1) / nt;
+    int u = tid * chunk;
+    const int u_end = min(total, u + chunk);
+    int p = u < u_end ? u / per : 0, ui = u < u_end ? u % per : 0;
+    while (u < u_end) {
+      const int r1 = p + 1, r2 = m - p;
+      int r, s0;
+      if (ui < r1) {
+        r = r1;
+        s0 = ui + 1;
+      } else if (r2 != r1) {
+        r = r2;
+        s0 = ui - r1 + 1;
+      } else {  // the middle row of odd m has no partner: skip the empty rest
+        u += per - ui;
+        ++p;
+        ui = 0;
+        continue;
+      }
+      const int s_end = min(r, s0 + (u_end - u) - 1);
+      {
         const int a = (j + r) % W, ta = tri(a);
-        int b = (j + 1) % W, tb = tri(b);
+        int b = (j + s0) % W, tb = tri(b);
         const double lr = lcol[r];
-        for (int s = 1; s <= r; ++s) {
+        int s = s0;
+        for (; s + 3 <= s_end; s += 4) {
+          int idx[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            idx[q] = a >= b ? ta + b : tb + a;
+            if (++b == W) {
+              b = 0;
+              tb = 0;
+            } else {
+              tb += b;
+            }
+          }
+          double v[4], l[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            v[q] = win[idx[q]];
+            l[q] = lcol[s + q];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) win[idx[q]] = fma(-lr, l[q], v[q]);
+        }
+        for (; s <= s_end; ++s) {
           const int idx = a >= b ? ta + b : tb + a;
           win[idx] = fma(-lr, lcol[s], win[idx]);
           if (++b == W) {
@@ -114,27 +194,44 @@ __global__ void __launch_bounds__(256) band_factor_kernel(BandDev D) {
           }
         }
       }
+      const int done = s_end - s0 + 1;
+      u += done;
+      ui += done;
+      if (ui >= per) {
+        ++p;
+        ui = 0;
+      }
     }
     // row j + W enters in the slots that column j has just left
-    const int inew = j + W;
-    if (inew < n)
-      for (int q = tid; q < W; q += nt) {
-        const int c = j + 1 + q;
-        win[wslot(inew, c, W)] = L[(long long)inew * W + w - inew + c];
-      }
+#pragma unroll
+    for (int u = 0; u < kFactorPre; ++u) {
+      const int q = tid + u * nt;
+      if (inew < n && q < W) win[wslot(inew, j + 1 + q, W)] = pre[u];
+    }
     __syncthreads();
   }
   if (tid == 0 && bad) atomicCAS(D.flags, 0, f + 1);
+}
+
+// Shared-memory layout of the M-build block: partial sums, the broadcast
+// x row, the W x NC ring of the sweep, and kRowsAhead row buffers of
+// stride max_w + 2 + NC: L(row, row-w..row), 1/L(row,row) and, in the
+// backward sweep, the NC forward values of row - W.
+__host__ __device__ inline size_t trace_smem_doubles(int max_w) {
+  const size_t W = (size_t)max_w + 1;
+  return (size_t)kBandWarps * kBandCols + kBandCols + W * kBandCols + kRowsAhead * (W + 1 + kBandCols);
 }
 
 __global__ void __launch_bounds__(kBandWarps * 32) band_trace_kernel(BandDev D, const long long* toff,
                                                                      const long long* moff, double* M) {
   extern __shared__ double band_sm[];
   __shared__ int item_s;
-  constexpr int NC = kBandCols, NW = kBandWarps;
-  double* part = band_sm;       // NW x NC partial row sums
-  double* xs = part + NW * NC;  // NC
-  double* ring = xs + NC;       // W x NC: the last W rows of the sweep
+  constexpr int NC = kBandCols, NW = kBandWarps, RA = kRowsAhead;
+  double* part = band_sm;                       // NW x NC partial row sums
+  double* xs = part + NW * NC;                  // NC
+  double* ring = xs + NC;                       // W x NC: the last W rows of the sweep
+  double* rows = ring + (D.max_w + 1) * NC;     // RA row buffers
+  const int RS = D.max_w + 2 + NC;              // row buffer stride
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   double* Z = D.Z + (long long)blockIdx.x * D.max_n * NC;
   for (;;) {
@@ -148,13 +245,30 @@ __global__ void __launch_bounds__(kBandWarps * 32) band_trace_kernel(BandDev D, 
     const int n = (int)(D.off[f + 1] - o), w = D.w[f], W = w + 1;
     const long long tf = toff[f + 1] - t0;
     const double* L = D.L + D.boff[f];
+    const double* dinv = D.dinv + o;
     const int col_b = lane < cnt ? D.tcol[t0 + I.y + lane] : -1;
     const int col_p = lane < cnt ? D.tpos[t0 + I.y + lane] : -1;
+    // copy row `row` of the factor (and its pivot reciprocal; with zrow, the
+    // forward values of row - W) into its buffer; one commit group per call
+    auto fetch = [&](int row, bool zrow) {
+      if (row >= p0 && row < n) {
+        double* dst = rows + (row % RA) * RS;
+        const double* src = L + (long long)row * W;
+        for (int e = threadIdx.x; e < W; e += blockDim.x) cp_async8(dst + e, src + e);
+        if (threadIdx.x == 0) cp_async8(dst + W, dinv + row);
+        if (zrow && row - W >= p0 && threadIdx.x < NC)
+          cp_async8(dst + W + 1 + threadIdx.x, Z + (long long)(row - W) * NC + threadIdx.x);
+      }
+      cp_async_commit();
+    };
     for (int e = threadIdx.x; e < W * NC; e += blockDim.x) ring[e] = 0.0;
-    __syncthreads();
     // forward: L y = e_b from row p0 on
+    for (int q = 0; q < RA - 1; ++q) fetch(p0 + q, false);
+    cp_async_wait<RA - 2>();
+    __syncthreads();
     for (int i = p0; i < n; ++i) {
-      const double* Li = L + (long long)i * W + w;  // Li[-k] = L(i, i-k)
+      fetch(i + RA - 1, false);  // into the buffer row i-1 has left
+      const double* Li = rows + (i % RA) * RS + w;  // Li[-k] = L(i, i-k), Li[1] = 1/L(i,i)
       const int kmax = min(w, i - p0);
       double acc = 0.0;
       if (1 + g <= kmax) {
@@ -170,34 +284,41 @@ __global__ void __launch_bounds__(kBandWarps * 32) band_trace_kernel(BandDev D, 
       if (g == 0) {
         double s = 0.0;
         for (int q = 0; q < NW; ++q) s += part[q * NC + lane];
-        const double y = ((i == col_p ? 1.0 : 0.0) - s) / Li[0];
+        const double y = ((i == col_p ? 1.0 : 0.0) - s) * Li[1];
         ring[(i % W) * NC + lane] = y;
         Z[(long long)i * NC + lane] = y;
       }
+      cp_async_wait<RA - 2>();  // row i + 1 is in
       __syncthreads();
     }
+    // all forward values are written before the backward sweep copies them
+    __threadfence_block();
     // backward: L^T x = y; slot of row t holds y_t minus the rows applied so far
     for (int e = threadIdx.x; e < W * NC; e += blockDim.x) {
       const int rr = n - 1 - e / NC, ln = e % NC;
       if (rr >= 0) ring[(rr % W) * NC + ln] = rr >= p0 ? Z[(long long)rr * NC + ln] : 0.0;
     }
+    for (int q = 0; q < RA - 1; ++q) fetch(n - 1 - q, true);
+    cp_async_wait<RA - 2>();
     __syncthreads();
     const int* tat = D.trace_at + o;
     double* Mf = M + moff[f];
-    for (int t = n - 1; t >= 0; --t) {
-      const double* Lt = L + (long long)t * W + w;
+    // x is needed at rows >= p0 only: an entry M_f[a][b] with a above the
+    // item's first column is the mirror of one that column a's item computes
+    for (int t = n - 1; t >= p0; --t) {
+      fetch(t - RA + 1, true);
+      const double* Lt = rows + (t % RA) * RS + w;  // Lt[1] = 1/L(t,t), Lt[2 + lane] = y(t - W)
       if (g == 0) {
         const int st = (t % W) * NC + lane;
-        const double x = ring[st] / Lt[0];
+        const double x = ring[st] * Lt[1];
         xs[lane] = x;
         const int a = tat[t];
         if (a >= 0 && col_b >= 0) Mf[(long long)a * tf + col_b] = x;
-        const int rn = t - W;  // the row that takes this slot next
-        ring[st] = rn >= p0 ? Z[(long long)rn * NC + lane] : 0.0;
+        ring[st] = t - W >= p0 ? Lt[2 + lane] : 0.0;  // the row that takes this slot next
       }
       __syncthreads();
       const double x = xs[lane];
-      const int kmax = min(w, t);
+      const int kmax = min(w, t - p0);
       if (1 + g <= kmax) {
         int sl = (t - 1 - g) % W;
         for (int k = 1 + g; k <= kmax; k += NW) {
@@ -207,13 +328,18 @@ __global__ void __launch_bounds__(kBandWarps * 32) band_trace_kernel(BandDev D, 
           while (sl < 0) sl += W;
         }
       }
+      cp_async_wait<RA - 2>();  // row t - 1 is in
       __syncthreads();
     }
   }
+  cp_async_wait<0>();
 }
 
-// M_f <- (M_f + M_f^T) / 2: the two solves of a pair round differently
-__global__ void band_symmetrize_kernel(int nf, const long long* toff, const long long* moff, double* M) {
+// Of each mirrored pair M_f[a][b], M_f[b][a], the entry in the column of
+// the trace node further up the ordering is computed by every item (the
+// row lies below that column's first position); copy it onto the other.
+__global__ void band_symmetrize_kernel(int nf, const long long* toff, const long long* moff, const int* tposa,
+                                       double* M) {
   const long long total = moff[nf];
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -222,14 +348,28 @@ __global__ void band_symmetrize_kernel(int nf, const long long* toff, const long
     const long long a = loc / t, b = loc % t;
     if (a >= b) continue;
     double* Mf = M + moff[f];
-    const double v = 0.5 * (Mf[a * t + b] + Mf[b * t + a]);
-    Mf[a * t + b] = v;
-    Mf[b * t + a] = v;
+    if (tposa[toff[f] + a] < tposa[toff[f] + b])
+      Mf[a * t + b] = Mf[b * t + a];
+    else
+      Mf[b * t + a] = Mf[a * t + b];
   }
 }
 
-__global__ void band_solve_kernel(BandDev D, const double* v, double* y, double* z) {
+// z[offset[f] + position] = v[offset[f] + node at that position]
+__global__ void band_gather_kernel(BandDev D, int n_h, const double* __restrict__ v, double* __restrict__ z) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n_h;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int f = fracture_of(D.off, D.n_f, r);
+    const long long o = D.off[f];
+    z[r] = v[o + D.perm[r]];
+  }
+}
+
+// One warp per fracture; z holds the permuted right-hand side on entry and
+// the forward values on exit; y receives A_f^{-1} v in the caller's order.
+__global__ void band_solve_kernel(BandDev D, double* z, double* y) {
   extern __shared__ double band_sm[];
+  constexpr int RA = kRowsAhead;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   if (gw >= D.n_f) return;  // whole warps only: no block barrier below
@@ -237,42 +377,68 @@ __global__ void band_solve_kernel(BandDev D, const double* v, double* y, double*
   const long long o = D.off[f];
   const int n = (int)(D.off[f + 1] - o), w = D.w[f], W = w + 1;
   const double* L = D.L + D.boff[f];
+  const double* dinv = D.dinv + o;
   const int* perm = D.perm + o;
-  double* ring = band_sm + (long long)wib * (D.max_w + 1);
+  const int RS = D.max_w + 3;
+  double* ring = band_sm + (long long)wib * ((D.max_w + 1) + RA * RS);
+  double* rows = ring + (D.max_w + 1);
   double* zf = z + o;
+  // row buffer: L(row, row-w..row), 1/L(row,row), and z[row] (forward) or
+  // z[row - W] (backward)
+  auto fetch = [&](int row, int zoff) {
+    if (row >= 0 && row < n) {
+      double* dst = rows + (row % RA) * RS;
+      const double* src = L + (long long)row * W;
+      for (int e = lane; e < W; e += 32) cp_async8(dst + e, src + e);
+      if (lane == 0) cp_async8(dst + W, dinv + row);
+      if (lane == 1 && row - zoff >= 0) cp_async8(dst + W + 1, zf + row - zoff);
+    }
+    cp_async_commit();
+  };
+  for (int q = 0; q < RA - 1; ++q) fetch(q, 0);
+  cp_async_wait<RA - 2>();
+  __syncwarp();
   for (int i = 0; i < n; ++i) {
-    const double* Li = L + (long long)i * W + w;
+    fetch(i + RA - 1, 0);
+    const double* Li = rows + (i % RA) * RS + w;  // Li[1] = 1/L(i,i), Li[2] = z[i]
     const int kmax = min(w, i);
     double acc = 0.0;
     for (int k = 1 + lane; k <= kmax; k += 32) acc = fma(Li[-k], ring[(i - k) % W], acc);
     acc = warp_sum(acc);
     if (lane == 0) {
-      const double yi = (v[o + perm[i]] - acc) / Li[0];
+      const double yi = (Li[2] - acc) * Li[1];
       ring[i % W] = yi;
       zf[i] = yi;
     }
+    cp_async_wait<RA - 2>();
     __syncwarp();
   }
+  __threadfence_block();
   for (int e = lane; e < W; e += 32) {
     const int rr = n - 1 - e;
     if (rr >= 0) ring[rr % W] = zf[rr];
   }
+  for (int q = 0; q < RA - 1; ++q) fetch(n - 1 - q, W);
+  cp_async_wait<RA - 2>();
   __syncwarp();
   for (int t = n - 1; t >= 0; --t) {
-    const double* Lt = L + (long long)t * W + w;
-    const double x = ring[t % W] / Lt[0];
+    fetch(t - RA + 1, W);
+    const double* Lt = rows + (t % RA) * RS + w;  // Lt[1] = 1/L(t,t), Lt[2] = z[t - W]
+    const double x = ring[t % W] * Lt[1];
     __syncwarp();
     if (lane == 0) {
       y[o + perm[t]] = x;
-      ring[t % W] = t - W >= 0 ? zf[t - W] : 0.0;
+      ring[t % W] = t - W >= 0 ? Lt[2] : 0.0;
     }
     const int kmax = min(w, t);
     for (int k = 1 + lane; k <= kmax; k += 32) {
       const int sl = (t - k) % W;
       ring[sl] = fma(-Lt[-k], x, ring[sl]);
     }
+    cp_async_wait<RA - 2>();
     __syncwarp();
   }
+  cp_async_wait<0>();
 }
 
 int grid_for(long long work, int block) {
@@ -463,6 +629,7 @@ int band_plan(int n_f, int n_h, const long long* offset, const std::vector<int>&
   const int n_T = (int)tnode.size();
   H.tcol.assign(std::max(n_T, 1), 0);
   H.tpos.assign(std::max(n_T, 1), 0);
+  H.tposa.assign(std::max(n_T, 1), 0);
   std::vector<std::pair<int, int>> slots;
   std::vector<double> cost;
   for (int f = 0; f < n_f; ++f) {
@@ -479,11 +646,12 @@ int band_plan(int n_f, int n_h, const long long* offset, const std::vector<int>&
     for (size_t s = 0; s < slots.size(); ++s) {
       H.tpos[t0 + s] = slots[s].first;
       H.tcol[t0 + s] = slots[s].second;
+      H.tposa[t0 + slots[s].second] = slots[s].first;
     }
     for (size_t s0 = 0; s0 < slots.size(); s0 += kBandCols) {
       const int cnt = (int)std::min<size_t>(kBandCols, slots.size() - s0);
       H.items.push_back(make_int4(f, (int)s0, cnt, slots[s0].first));
-      cost.push_back((double)(2 * n - slots[s0].first) * (H.w[f] + 1));
+      cost.push_back((double)(n - slots[s0].first) * (H.w[f] + 1));
     }
   }
   std::vector<int> idx(H.items.size());
@@ -504,14 +672,14 @@ cudaError_t band_fill(const BandDev& D, int n_h, const int* rp, const int* col, 
 cudaError_t band_factor(const BandDev& D, cudaStream_t s) {
   cudaError_t e = allow_smem((const void*)band_factor_kernel, D.factor_smem);
   if (e != cudaSuccess) return e;
-  band_factor_kernel<<<D.n_f, 256, D.factor_smem, s>>>(D);
+  band_factor_kernel<<<D.n_f, kFactorThreads, D.factor_smem, s>>>(D);
   return cudaGetLastError();
 }
 
 cudaError_t band_trace_blocks(const BandDev& D, const long long* toff, const long long* moff, double* M,
                               cudaStream_t s) {
   if (D.n_items > 0) {
-    const size_t sm = sizeof(double) * ((size_t)kBandWarps * kBandCols + kBandCols + (size_t)(D.max_w + 1) * kBandCols);
+    const size_t sm = sizeof(double) * trace_smem_doubles(D.max_w);
     cudaError_t e = allow_smem((const void*)band_trace_kernel, sm);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.flags + 1, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -519,16 +687,17 @@ cudaError_t band_trace_blocks(const BandDev& D, const long long* toff, const lon
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  band_symmetrize_kernel<<<152 * 8, 256, 0, s>>>(D.n_f, toff, moff, M);
+  band_symmetrize_kernel<<<152 * 8, 256, 0, s>>>(D.n_f, toff, moff, D.tposa, M);
   return cudaGetLastError();
 }
 
-cudaError_t band_solve(const BandDev& D, const double* v, double* y, double* z, cudaStream_t s) {
+cudaError_t band_solve(const BandDev& D, int n_h, const double* v, double* y, double* z, cudaStream_t s) {
   constexpr int kWarps = 4;
-  const size_t sm = sizeof(double) * kWarps * (size_t)(D.max_w + 1);
+  const size_t sm = sizeof(double) * kWarps * ((size_t)(D.max_w + 1) + kRowsAhead * (size_t)(D.max_w + 3));
   cudaError_t e = allow_smem((const void*)band_solve_kernel, sm);
   if (e != cudaSuccess) return e;
-  band_solve_kernel<<<(D.n_f + kWarps - 1) / kWarps, kWarps * 32, sm, s>>>(D, v, y, z);
+  band_gather_kernel<<<grid_for(n_h, 256), 256, 0, s>>>(D, n_h, v, z);
+  band_solve_kernel<<<(D.n_f + kWarps - 1) / kWarps, kWarps * 32, sm, s>>>(D, z, y);
   return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ struct BandHost {
   std::vector<int> trace_at;        // n_h: local trace index at offset[f] + position, or -1
   std::vector<int> order;           // fractures by decreasing factorisation work
   std::vector<int> tcol, tpos;      // n_T: trace columns per fracture sorted by position
+  std::vector<int> tposa;           // n_T: position of each trace node (by local trace index)
   std::vector<int4> items;          // (fracture, first slot, count, first position)
 };
 
@@ -50,9 +51,10 @@ struct BandDev {
   const long long* boff = nullptr;
   const long long* gwoff = nullptr;
   const int *pos = nullptr, *perm = nullptr, *trace_at = nullptr, *order = nullptr;
-  const int *tcol = nullptr, *tpos = nullptr;
+  const int *tcol = nullptr, *tpos = nullptr, *tposa = nullptr;
   const int4* items = nullptr;
   double* L = nullptr;
+  double* dinv = nullptr;           // n_h: 1 / L(i, i) by fracture position
   double* gwin = nullptr;
   double* Z = nullptr;              // grid_trace x max_n x kBandCols forward results
   int* flags = nullptr;             // [0] first non-positive pivot + 1, [1] work-queue counter
@@ -76,6 +78,6 @@ cudaError_t band_factor(const BandDev& D, cudaStream_t s);
 cudaError_t band_trace_blocks(const BandDev& D, const long long* toff, const long long* moff, double* M,
                               cudaStream_t s);
 // y = A^{-1} v (n_h vectors, global numbering); z: n_h scratch.  y may alias v.
-cudaError_t band_solve(const BandDev& D, const double* v, double* y, double* z, cudaStream_t s);
+cudaError_t band_solve(const BandDev& D, int n_h, const double* v, double* y, double* z, cudaStream_t s);
 
 }  // namespace pp

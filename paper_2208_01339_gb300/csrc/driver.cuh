@@ -105,7 +105,7 @@ struct pp_ctx {
   // Schur context with general blocks: banded Cholesky factors
   int band_max = 0;
   long long band_elems = 0;
-  double t_band_ms = 0;
+  double t_band_ms = 0, t_trace_ms = 0;
   std::string err;
   std::vector<cudaEvent_t> events;
   cudaStream_t cap_stream = nullptr;

@@ -663,8 +663,10 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
     D.order = put(B, H.order, up);
     D.tcol = put(B, H.tcol, up);
     D.tpos = put(B, H.tpos, up);
+    D.tposa = put(B, H.tposa, up);
     D.items = put(B, H.items, up);
     D.L = B.take<double>(H.elems);
+    D.dinv = B.take<double>(d->n_h);
     D.gwin = B.take<double>(H.gwin_elems);
     D.grid_trace = std::max(1, std::min(H.n_items, 2 * num_sms()));
     D.Z = B.take<double>((long long)D.grid_trace * H.max_n * kBandCols);
@@ -731,7 +733,7 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
 // Full solve y = A^{-1} v: banded Cholesky factors for general blocks, else
 // fast diagonalisation.
 cudaError_t ainv_full(const SchurImpl* S, const double* v, double* y, cudaStream_t s) {
-  if (S->general) return band_solve(S->band, v, y, S->fd, s);
+  if (S->general) return band_solve(S->band, S->n_h, v, y, S->fd, s);
   const size_t sm = (size_t)(kBlock / 32) * S->max_nx * sizeof(double);
   const int g_rows = grid_of(S->rows_y * 32);
   fd_transform_kernel<<<g_rows, kBlock, sm, s>>>(S->n_f, S->yoff, S->off, S->nx, S->soff, S->S, v, S->fc,
@@ -966,39 +968,48 @@ extern "C" int schur_setup(pp_ctx** out, const pp_dfn* d, const pp_options* opt,
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "clearing workspace"));
   if (S->general) {
     // banded Cholesky of every block, then M from band solves
-    cudaEvent_t b0 = nullptr, b1 = nullptr;
+    cudaEvent_t b0 = nullptr, b1 = nullptr, b2 = nullptr;
     cudaEventCreate(&b0);
     cudaEventCreate(&b1);
+    cudaEventCreate(&b2);
     cudaEventRecord(b0, s);
     e = cudaMemsetAsync(S->band.L, 0, sizeof(double) * (size_t)S->band_elems, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->band.flags, 0, 2 * sizeof(int), s);
     if (e == cudaSuccess) e = band_fill(S->band, d->n_h, d->A_rowptr, d->A_col, d->A_val, s);
     if (e == cudaSuccess) e = band_factor(S->band, s);
+    cudaEventRecord(b2, s);
     int bad_f = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_f, S->band.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
       cudaEventDestroy(b0);
       cudaEventDestroy(b1);
+      cudaEventDestroy(b2);
       return bail(cuda_fail(c, e, "banded Cholesky of the fracture blocks"));
     }
     if (bad_f) {
       cudaEventDestroy(b0);
       cudaEventDestroy(b1);
+      cudaEventDestroy(b2);
       return bail(fail(c, PP_EBREAKDOWN,
                        "A_f of fracture " + std::to_string(bad_f - 1) + " is not positive definite"));
     }
     e = band_trace_blocks(S->band, S->toff, S->moff, S->M, s);
     cudaEventRecord(b1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(b1);
-    float bms = 0.f;
-    if (e == cudaSuccess) cudaEventElapsedTime(&bms, b0, b1);
+    float fms = 0.f, tms = 0.f;
+    if (e == cudaSuccess) {
+      cudaEventElapsedTime(&fms, b0, b2);
+      cudaEventElapsedTime(&tms, b2, b1);
+    }
     cudaEventDestroy(b0);
     cudaEventDestroy(b1);
+    cudaEventDestroy(b2);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "trace blocks from the band factors"));
     c->band_max = P.band.max_w;
     c->band_elems = S->band_elems;
-    c->t_band_ms = bms;
+    c->t_band_ms = fms;
+    c->t_trace_ms = tms;
   } else {
     // sine tables, eigenvalues, U tables, the trace blocks M
     sine_tables_kernel<<<grid_of(S->s_elems), kBlock, 0, s>>>(S->n_f, S->nx, S->soff, S->loff, S->S, S->lam);

@@ -70,7 +70,8 @@ class Info(ctypes.Structure):
                 ("apply_prec", ctypes.c_int), ("lanczos_steps_done", ctypes.c_int), ("t_setup_ms", ctypes.c_double),
                 ("grid_blocks", ctypes.c_int), ("ndiag", ctypes.c_int), ("lowrank", ctypes.c_int),
                 ("lowrank_steps_done", ctypes.c_int), ("ritz_resid", ctypes.c_double), ("theta_min", ctypes.c_double),
-                ("band_max", ctypes.c_int), ("band_elems", ctypes.c_longlong), ("t_factor_ms", ctypes.c_double)]
+                ("band_max", ctypes.c_int), ("band_elems", ctypes.c_longlong), ("t_factor_ms", ctypes.c_double),
+                ("t_trace_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

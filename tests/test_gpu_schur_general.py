@@ -77,7 +77,7 @@ def test_ainv(pair):
     assert rel(y, ref.ainv(v)) <= TOL
     assert rel(net.A.matvec(y), v) <= TOL
     info = S.info()
-    assert info["band_max"] > 0 and info["band_elems"] > 0 and info["t_factor_ms"] > 0
+    assert info["band_max"] > 0 and info["band_elems"] > 0 and info["t_factor_ms"] > 0 and info["t_trace_ms"] > 0
 
 
 def test_schur_apply_and_diag(pair):
@@ -111,12 +111,15 @@ def test_pcg_on_scaled_schur(pair, k):
     xo, so = ref.pcg(ref.diag(), r, v0=I.lanczos_start(net.n_u, 0), **opts)
     assert so["status"] == 0 and st["status"] == 0
     assert st["alpha_hat"] == pytest.approx(so["alpha_hat"], rel=1e-9)
+    # the two sides factor in different orders (reordered band with pivot
+    # reciprocals vs the given numbering), so M differs in the last bits; the
+    # iteration at which the residual crosses rtol may move by one
+    d_it = abs(st["iterations"] - so["iterations"])
     if so["iterations"] <= 100:
-        assert st["iterations"] == so["iterations"]
-        assert rel(to_np(x), xo) <= 1e-9
+        assert d_it <= 1
+        assert rel(to_np(x), xo) <= (1e-9 if d_it == 0 else 1e-7)
     else:
-        # long diagonal-seed runs: the stopping step depends on rounding order
-        assert abs(st["iterations"] - so["iterations"]) <= 0.03 * so["iterations"]
+        assert d_it <= 0.03 * so["iterations"]
         assert rel(to_np(x), xo) <= 1e-7
 
 
