@@ -54,6 +54,8 @@ WORKLOADS = {
     # the same network with general fracture blocks (P1 stiffness on jittered triangulations,
     # lognormal coefficients): A^{-1} from banded Cholesky factors built on the GPU
     "dfn200_p1": dict(dfn=True, seed=2, k=3, lanczos=30, prec="f64", general="p1"),
+    # its first 40 fractures (0.4M nodes): a small case of the same kernels for profiler captures
+    "dfn40_p1": dict(dfn=True, seed=2, n_f=40, k=3, lanczos=30, prec="f64", general="p1"),
     # per-instance symmetric DIA in the batch (the instances are 7-point stencils)
     "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32", fmt="dia"),
 }
@@ -66,7 +68,7 @@ def build_problem(w):
     from paper_2208_01339_gb300 import inputs as I
 
     if w.get("dfn"):
-        net = I.fracture_network(seed=w["seed"])
+        net = I.fracture_network(n_f=w.get("n_f", 200), seed=w["seed"])
         if w.get("general") == "p1":
             net = I.general_fracture_network(net, shuffle=False)
         return net, None

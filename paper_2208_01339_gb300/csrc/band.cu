@@ -72,7 +72,7 @@ __global__ void band_fill_kernel(BandDev D, int n_h, const int* __restrict__ rp,
   }
 }
 
-constexpr int kFactorThreads = 256;
+constexpr int kFactorThreads = 512;
 constexpr int kFactorPre = (kBandMaxW + 1 + kFactorThreads - 1) / kFactorThreads;  // new-row values per thread
 constexpr int kRowsAhead = 4;  // band rows in flight (cp.async ring) in the solve sweeps
 
@@ -87,14 +87,15 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-__global__ void __launch_bounds__(kFactorThreads, 1) band_factor_kernel(BandDev D) {
-  extern __shared__ double band_sm[];
-  const int f = D.order[blockIdx.x];
+// The factorisation of fracture f with its window at `win` (shared memory
+// for SH, else global): instantiated twice so that the shared-memory case
+// addresses the window with 32-bit shared loads and stores.
+template <bool SH>
+__device__ __forceinline__ void factor_block(const BandDev& D, int f, double* win) {
   const long long o = D.off[f];
   const int n = (int)(D.off[f + 1] - o), w = D.w[f], W = w + 1;
   double* L = D.L + D.boff[f];
   double* dinv = D.dinv + o;
-  double* win = D.gwoff[f] >= 0 ? D.gwin + D.gwoff[f] : band_sm;
   double* lcol = win + tri(W);
   const int tid = threadIdx.x;
   constexpr int nt = kFactorThreads;
@@ -211,6 +212,15 @@ __global__ void __launch_bounds__(kFactorThreads, 1) band_factor_kernel(BandDev 
     __syncthreads();
   }
   if (tid == 0 && bad) atomicCAS(D.flags, 0, f + 1);
+}
+
+__global__ void __launch_bounds__(kFactorThreads, 1) band_factor_kernel(BandDev D) {
+  extern __shared__ double band_sm[];
+  const int f = D.order[blockIdx.x];
+  if (D.gwoff[f] < 0)
+    factor_block<true>(D, f, band_sm);
+  else
+    factor_block<false>(D, f, D.gwin + D.gwoff[f]);
 }
 
 // Shared-memory layout of the M-build block: partial sums, the broadcast
