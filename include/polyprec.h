@@ -331,6 +331,17 @@ int schur_recover(pp_ctx* ctx, const double* q, const double* u, double* h, doub
 /* y = A^{-1} v for the block-diagonal fracture matrix (device, n_h). */
 int schur_ainv(pp_ctx* ctx, const double* v, double* y, void* stream);
 
+/* Band layout that schur_setup would use for general fracture blocks
+ * (Section 4.2, the exact Cholesky factor of A), computed on the host
+ * without a GPU: A as HOST CSR (offset[n_f] rows, global numbering) with
+ * the same requirements as pp_dfn.A_*.  w_out[f] (host, n_f) receives the
+ * half-bandwidth of block f after reordering, rcm_out[f] (host, n_f, may be
+ * NULL) 1 where reverse Cuthill-McKee beat the given numbering.  Returns the
+ * status schur_setup's planning would return (PP_EINVAL, PP_EBREAKDOWN for a
+ * non-positive diagonal, PP_EUNSUPPORTED for a band wider than 768). */
+int pp_fracture_bands(int n_f, const long long* offset, const int* rowptr, const int* col,
+                      const double* val, int* w_out, int* rcm_out);
+
 /* ---- batched solves (many instances, many right-hand sides) ------------- */
 
 /* One SPD instance of a batch: CSR on the device (kept valid during

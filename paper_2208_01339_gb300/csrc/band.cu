@@ -33,9 +33,12 @@
 #include <cstring>
 #include <numeric>
 
+#include <climits>
+
 #include "../../include/polyprec.h"
 #include "band.cuh"
 #include "common.cuh"
+#include "driver.cuh"
 
 namespace pp {
 namespace {
@@ -541,6 +544,7 @@ int band_plan(int n_f, int n_h, const long long* offset, const std::vector<int>&
   H = BandHost();
   H.n_f = n_f;
   H.w.assign(n_f, 0);
+  H.rcm.assign(n_f, 0);
   H.boff.assign(n_f + 1, 0);
   H.gwoff.assign(n_f, -1);
   H.pos.assign(n_h, 0);
@@ -606,6 +610,7 @@ int band_plan(int n_f, int n_h, const long long* offset, const std::vector<int>&
       for (int p = aptr[i]; p < aptr[i + 1]; ++p) w_rcm = std::max(w_rcm, std::abs(inv[adj[p]] - inv[i]));
     const bool use_rcm = w_rcm < w_nat;
     H.rcm_used += use_rcm ? 1 : 0;
+    H.rcm[f] = use_rcm ? 1 : 0;
     const int w = use_rcm ? w_rcm : w_nat;
     if (w > kBandMaxW) {
       err = "fracture " + std::to_string(f) + ": half-bandwidth " + std::to_string(w) +
@@ -712,3 +717,33 @@ cudaError_t band_solve(const BandDev& D, int n_h, const double* v, double* y, do
 }
 
 }  // namespace pp
+
+extern "C" int pp_fracture_bands(int n_f, const long long* offset, const int* rowptr, const int* col,
+                                 const double* val, int* w_out, int* rcm_out) {
+  using namespace pp;
+  if (n_f <= 0 || !offset || !rowptr || !w_out) return fail(nullptr, PP_EINVAL, "NULL argument or n_f <= 0");
+  if (offset[0] != 0) return fail(nullptr, PP_EINVAL, "offset[0] must be 0");
+  for (int f = 0; f < n_f; ++f)
+    if (offset[f + 1] <= offset[f]) return fail(nullptr, PP_EINVAL, "fracture " + std::to_string(f) + " has no nodes");
+  const long long n_h = offset[n_f];
+  if (n_h > INT_MAX) return fail(nullptr, PP_EINVAL, "too many nodes");
+  const long long nnz = rowptr[n_h];
+  if (rowptr[0] != 0 || nnz < 0 || (nnz > 0 && (!col || !val))) return fail(nullptr, PP_EINVAL, "bad CSR arrays");
+  std::vector<int> rp(rowptr, rowptr + n_h + 1), cc(col, col + nnz);
+  std::vector<double> vv(val, val + nnz);
+  for (long long r = 0; r < n_h; ++r)
+    if (rp[r + 1] < rp[r]) return fail(nullptr, PP_EINVAL, "rowptr is not monotone");
+  for (long long p = 0; p < nnz; ++p)
+    if (cc[p] < 0 || cc[p] >= n_h) return fail(nullptr, PP_EINVAL, "A column out of range");
+  BandHost H;
+  std::string err;
+  const std::vector<long long> toff(n_f + 1, 0);
+  const std::vector<int> tnode;
+  const int rc = band_plan(n_f, (int)n_h, offset, rp, cc, vv, toff, tnode, H, err);
+  if (rc) return fail(nullptr, rc, err);
+  for (int f = 0; f < n_f; ++f) {
+    w_out[f] = H.w[f];
+    if (rcm_out) rcm_out[f] = H.rcm[f];
+  }
+  return PP_OK;
+}

@@ -32,6 +32,7 @@ struct BandHost {
   long long elems = 0, gwin_elems = 0;
   size_t factor_smem = 0;           // dynamic shared memory of the factor launch
   std::vector<int> w;               // half-bandwidth per fracture
+  std::vector<int> rcm;             // 1 where reverse Cuthill-McKee beat the given numbering
   std::vector<long long> boff;      // band storage offsets (n_f + 1)
   std::vector<long long> gwoff;     // factor window in global memory (-1: shared memory)
   std::vector<int> pos;             // n_h: position of each node in its fracture's order

@@ -133,6 +133,7 @@ SIGNATURES = [
     ("schur_rhs", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("schur_recover", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("schur_ainv", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("pp_fracture_bands", ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("pp_batch_workspace_size", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(Options),
                                                ctypes.POINTER(ctypes.c_size_t)]),
     ("pp_batch_setup", ctypes.c_int, [ctypes.POINTER(_vp), _vp, ctypes.c_int, ctypes.POINTER(Options), _vp,
@@ -186,6 +187,23 @@ def polyprec_coeffs(alpha: float, beta: float, xi: float, k: int):
                                rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     _check(rc)
     return tb.value, d.value, sb.value, rho
+
+
+def fracture_bands(offset, A):
+    """(w, rcm): per fracture, the half-bandwidth of the banded Cholesky
+    factor that schur_setup would build for the general blocks A (host CSR
+    with rowptr/col/val) and whether reverse Cuthill-McKee was chosen.
+    Host only (pp_fracture_bands)."""
+    off = np.ascontiguousarray(offset, dtype=np.int64)
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.col, dtype=np.int32)
+    va = np.ascontiguousarray(A.val, dtype=np.float64)
+    n_f = off.size - 1
+    w = np.zeros(n_f, dtype=np.int32)
+    rcm = np.zeros(n_f, dtype=np.int32)
+    _check(lib().pp_fracture_bands(n_f, _vp(off.ctypes.data), _vp(rp.ctypes.data), _vp(ci.ctypes.data),
+                                   _vp(va.ctypes.data), _vp(w.ctypes.data), _vp(rcm.ctypes.data)))
+    return w, rcm.astype(bool)
 
 
 def make_options(**kw) -> Options:
