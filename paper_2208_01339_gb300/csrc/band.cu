@@ -1,15 +1,17 @@
 // Banded Cholesky factors of general fracture blocks and the solves built on
 // them (declarations and storage in band.cuh).
 //
-// Factorisation: one block per fracture, columns in order.  Column j is
-// scaled by the pivot, then the (w x w) lower triangle below it takes the
-// rank-one update.  The live part of the band -- rows j..j+w, columns j..i
-// of row i -- is kept in a window indexed by (row mod W, column mod W),
-// W = w + 1.  Of the two mirrored slots (a, b) and (b, a) only one is live at
-// any time, so the window folds into a packed triangle of W (W + 1) / 2
-// doubles.  For w <= 238 that fits in shared memory; wider bands keep the
-// same window in global memory (L1/L2 resident).  Every band entry is read
-// from HBM once and the factor written once.
+// Factorisation: one block per fracture, in panels of kPanel columns.  The
+// panel's columns are scaled by their pivots and update the panel's later
+// columns one by one; then the triangle below the panel takes one rank-kPanel
+// update, each entry read and written once for kPanel FMAs.  The live part of
+// the band -- rows jp..jp+w+kPanel-1 for the panel starting at column jp,
+// columns jp..i of row i -- is kept in a window indexed by (row mod WP,
+// column mod WP), WP = w + kPanel.  Of the two mirrored slots (a, b) and
+// (b, a) only one is live at any time, so the window folds into a packed
+// triangle of WP (WP + 1) / 2 doubles.  For w <= 225 it fits in shared
+// memory; wider bands keep the same window in global memory.  Every band
+// entry is read from HBM once and the factor written once.
 //
 // Trace blocks: work item = one fracture and up to 32 of its trace columns
 // (sorted by position, so the forward solve starts at the first one: the
@@ -76,7 +78,6 @@ __global__ void band_fill_kernel(BandDev D, int n_h, const int* __restrict__ rp,
 }
 
 constexpr int kFactorThreads = 512;
-constexpr int kFactorPre = (kBandMaxW + 1 + kFactorThreads - 1) / kFactorThreads;  // new-row values per thread
 constexpr int kRowsAhead = 4;  // band rows in flight (cp.async ring) in the solve sweeps
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
@@ -97,120 +98,87 @@ template <bool SH>
 __device__ __forceinline__ void factor_block(const BandDev& D, int f, double* win) {
   const long long o = D.off[f];
   const int n = (int)(D.off[f + 1] - o), w = D.w[f], W = w + 1;
+  const int WP = W + kPanel - 1;  // live rows: a panel's columns reach w rows below its last one
   double* L = D.L + D.boff[f];
   double* dinv = D.dinv + o;
-  double* lcol = win + tri(W);
-  const int tid = threadIdx.x;
-  constexpr int nt = kFactorThreads;
-  // rows 0..w are all live at column 0
-  const int r0 = min(w, n - 1);
+  double* P = win + tri(WP);  // P[(i - jp) kPanelStride + c] = L(i, jp + c) for the current panel
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nt = kFactorThreads, nw = kFactorThreads / 32;
+  // rows 0..WP-1 are all live at the first panel
+  const int r0 = min(WP - 1, n - 1);
   for (int i = 0; i <= r0; ++i)
-    for (int j = tid; j <= i; j += nt) win[wslot(i, j, W)] = L[(long long)i * W + w - i + j];
+    for (int k = max(0, i - w) + tid; k <= i; k += nt) win[wslot(i, k, WP)] = L[(long long)i * W + w - i + k];
   __syncthreads();
   bool bad = false;
-  for (int j = 0; j < n; ++j) {
-    // the row entering at the end of this column, loaded now so that its
-    // latency hides behind the column's work
-    const int inew = j + W;
-    double pre[kFactorPre];
-#pragma unroll
-    for (int u = 0; u < kFactorPre; ++u) {
-      const int q = tid + u * nt;
-      pre[u] = inew < n && q < W ? L[(long long)inew * W + w - inew + (j + 1 + q)] : 0.0;
-    }
-    const double ajj = win[wslot(j, j, W)];
-    const bool ok = ajj > 0.0;  // false for NaN too
-    bad |= !ok;
-    const double d = ok ? sqrt(ajj) : 1.0;
-    const double rd = 1.0 / d;
-    const int m = min(w, n - 1 - j);
-    for (int r = 1 + tid; r <= m; r += nt) {
-      const double l = win[wslot(j + r, j, W)] * rd;
-      lcol[r] = l;
-      L[(long long)(j + r) * W + w - r] = l;
-    }
-    if (tid == 0) {
-      L[(long long)j * W + w] = d;
-      dinv[j] = rd;
-    }
+  for (int jp = 0; jp < n; jp += kPanel) {
+    const int nbb = min(kPanel, n - jp);
+    for (int e = tid; e < WP * kPanelStride; e += nt) P[e] = 0.0;
     __syncthreads();
-    // rank-one update of rows j+r, columns j+s, 1 <= s <= r <= m.  Rows are
-    // folded in pairs (p+1, m-p) of m+1 updates each; the pairs laid end to
-    // end are cut into one equal run per thread, so every warp (and every
-    // SM sub-partition's FP64 unit) gets the same share.  Four slots at a
-    // time are read before any is written (they are distinct).
-    const int half = (m + 1) >> 1, per = m + 1;
-    const int total = half * per;
-    const int chunk = (total + nt - 1) / nt;
-    int u = tid * chunk;
-    const int u_end = min(total, u + chunk);
-    int p = u < u_end ? u / per : 0, ui = u < u_end ? u % per : 0;
-    while (u < u_end) {
-      const int r1 = p + 1, r2 = m - p;
-      int r, s0;
-      if (ui < r1) {
-        r = r1;
-        s0 = ui + 1;
-      } else if (r2 != r1) {
-        r = r2;
-        s0 = ui - r1 + 1;
-      } else {  // the middle row of odd m has no partner: skip the empty rest
-        u += per - ui;
-        ++p;
-        ui = 0;
-        continue;
+    // the panel, column by column: scale, then update the panel's later columns
+    for (int cc = 0; cc < nbb; ++cc) {
+      const int c = jp + cc;
+      const double acc = win[wslot(c, c, WP)];
+      const bool ok = acc > 0.0;  // false for NaN too
+      bad |= !ok;
+      const double d = ok ? sqrt(acc) : 1.0;
+      const double rd = 1.0 / d;
+      const int m = min(w, n - 1 - c);
+      for (int r = 1 + tid; r <= m; r += nt) {
+        const double l = win[wslot(c + r, c, WP)] * rd;
+        P[(c + r - jp) * kPanelStride + cc] = l;
+        L[(long long)(c + r) * W + w - r] = l;
       }
-      const int s_end = min(r, s0 + (u_end - u) - 1);
-      {
-        const int a = (j + r) % W, ta = tri(a);
-        int b = (j + s0) % W, tb = tri(b);
-        const double lr = lcol[r];
-        int s = s0;
-        for (; s + 3 <= s_end; s += 4) {
-          int idx[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            idx[q] = a >= b ? ta + b : tb + a;
-            if (++b == W) {
-              b = 0;
-              tb = 0;
-            } else {
-              tb += b;
-            }
-          }
-          double v[4], l[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            v[q] = win[idx[q]];
-            l[q] = lcol[s + q];
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) win[idx[q]] = fma(-lr, l[q], v[q]);
-        }
-        for (; s <= s_end; ++s) {
-          const int idx = a >= b ? ta + b : tb + a;
-          win[idx] = fma(-lr, lcol[s], win[idx]);
-          if (++b == W) {
-            b = 0;
-            tb = 0;
-          } else {
-            tb += b;
-          }
+      if (tid == 0) {
+        L[(long long)c * W + w] = d;
+        dinv[c] = rd;
+      }
+      __syncthreads();
+      const int rem = min(nbb - 1 - cc, m);  // later panel columns c + s, s <= rem, inside the band
+      if (rem > 0) {
+        for (int e = tid; e < rem * m; e += nt) {
+          const int s = 1 + e % rem, r = 1 + e / rem;
+          if (s > r) continue;
+          const int idx = wslot(c + r, c + s, WP);
+          win[idx] = fma(-P[(c + r - jp) * kPanelStride + cc], P[(c + s - jp) * kPanelStride + cc], win[idx]);
         }
       }
-      const int done = s_end - s0 + 1;
-      u += done;
-      ui += done;
-      if (ui >= per) {
-        ++p;
-        ui = 0;
+      __syncthreads();
+    }
+    // rank-nbb update of the trailing triangle: rows and columns K0..R1.
+    // Work item = 32 columns (one per lane) x 8 rows; each lane keeps its
+    // column's panel values in registers, the row's are a broadcast load.
+    const int K0 = jp + nbb, R1 = min(jp + nbb - 1 + w, n - 1);
+    const int mt = R1 - K0 + 1;
+    if (mt > 0) {
+      const int strips = (mt + 31) >> 5;
+      int s = 0, base = 0;  // items of the strips before s
+      for (int it = warp;; it += nw) {
+        while (s < strips && it >= base + ((mt - 32 * s + 7) >> 3)) {
+          base += (mt - 32 * s + 7) >> 3;
+          ++s;
+        }
+        if (s >= strips) break;
+        const int k = K0 + 32 * s + lane;
+        const int i0 = K0 + 32 * s + 8 * (it - base), i1 = min(i0 + 8, R1 + 1);
+        if (k <= R1) {
+          double pk[kPanel];
+#pragma unroll
+          for (int q = 0; q < kPanel; ++q) pk[q] = P[(k - jp) * kPanelStride + q];
+          for (int i = max(i0, k); i < i1; ++i) {
+            const double* pi = P + (i - jp) * kPanelStride;
+            const int idx = wslot(i, k, WP);
+            double v = win[idx];
+#pragma unroll
+            for (int q = 0; q < kPanel; ++q) v = fma(-pi[q], pk[q], v);
+            win[idx] = v;
+          }
+        }
       }
     }
-    // row j + W enters in the slots that column j has just left
-#pragma unroll
-    for (int u = 0; u < kFactorPre; ++u) {
-      const int q = tid + u * nt;
-      if (inew < n && q < W) win[wslot(inew, j + 1 + q, W)] = pre[u];
+    // rows jp+WP.. enter in the slots the panel's columns have left
+    for (int q = tid; q < nbb * W; q += nt) {
+      const int inew = jp + WP + q / W, cq = q % W;
+      if (inew < n) win[wslot(inew, inew - w + cq, WP)] = L[(long long)inew * W + cq];
     }
     __syncthreads();
   }
@@ -625,10 +593,10 @@ int band_plan(int n_f, int n_h, const long long* offset, const std::vector<int>&
     const int W = w + 1;
     H.w[f] = w;
     H.boff[f + 1] = H.boff[f] + (long long)n * W;
-    const size_t win_bytes = (size_t)(tri(W) + W) * sizeof(double);
+    const size_t win_bytes = (size_t)factor_window_doubles(W) * sizeof(double);
     if (win_bytes > optin) {
       H.gwoff[f] = H.gwin_elems;
-      H.gwin_elems += tri(W) + W;
+      H.gwin_elems += factor_window_doubles(W);
     } else {
       H.factor_smem = std::max(H.factor_smem, win_bytes);
     }

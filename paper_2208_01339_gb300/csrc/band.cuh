@@ -26,6 +26,16 @@ namespace pp {
 constexpr int kBandMaxW = 768;   // largest half-bandwidth accepted after reordering
 constexpr int kBandCols = 32;    // trace columns per work item of the M build
 constexpr int kBandWarps = 8;    // warps of the M-build block (split the band)
+constexpr int kPanel = 8;        // columns per panel of the factorisation
+constexpr int kPanelStride = 9;  // doubles per row of the panel buffer (padded against bank conflicts)
+
+// Doubles of the factorisation window of a block with W = w + 1: the live
+// rows of the band (W + kPanel - 1 of them) folded into a packed triangle,
+// then the panel buffer.
+__host__ __device__ inline long long factor_window_doubles(int W) {
+  const long long WP = (long long)W + kPanel - 1;
+  return WP * (WP + 1) / 2 + WP * kPanelStride;
+}
 
 struct BandHost {
   int n_f = 0, max_w = 0, max_n = 0, n_items = 0, rcm_used = 0;
