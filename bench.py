@@ -428,6 +428,24 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1) / args.steps
     it = int(statistics.median(s["iterations"] for s in stats))
+    # the right-hand side (one full A^{-1} solve) and the recovery of h and p
+    # (two), timed separately: they sit outside the iteration
+    qd = torch.as_tensor(net.q, device=dev)
+    u, _ = S.solve(bt)
+    reps = 3
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(reps):
+        S.rhs(qd)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    rhs_ms = ev0.elapsed_time(ev1) / reps
+    ev0.record(stream)
+    for _ in range(reps):
+        S.recover(qd, u)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    recover_ms = ev0.elapsed_time(ev1) / reps
     # one S_hat product: M streamed twice (2-RHS and 1-RHS products), 3 FMAs per entry
     m_bytes = info["nnz"] * 8
     if rank == 0:
@@ -441,6 +459,7 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
                                         "closed form (uniform rectangles)"),
                           "band_max": info["band_max"], "band_doubles": info["band_elems"]},
                "factor_ms": round(info["t_factor_ms"], 2), "trace_blocks_ms": round(info["t_trace_ms"], 2),
+               "rhs_ms": round(rhs_ms, 3), "recover_ms": round(recover_ms, 3),
                "iterations": it, "setup_ms": round(info["t_setup_ms"], 2), "alpha_hat": info["alpha_hat"],
                "beta_hat": info["beta_hat"], "xi": info["xi"],
                "apply_ms": sum(s["t_apply_ms"] for s in stats) / max(1, sum(s["apply_launches"] for s in stats)),

@@ -28,14 +28,12 @@
 // The sweeps are latency chains (row i needs row i-1), so the rows of the
 // factor they read -- with the pivot reciprocals and the vector entries of
 // the same step -- are copied into shared memory a few rows ahead with
-// cp.async; the factorisation loads the row that enters its window one
-// column ahead into registers.
+// cp.async.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
-
-#include <climits>
 
 #include "../../include/polyprec.h"
 #include "band.cuh"
