@@ -281,7 +281,8 @@ const char* pp_last_error(const pp_ctx* ctx);
  *    reordering exceeds 768; PP_EBREAKDOWN if a block is not positive
  *    definite; PP_EINVAL if A is not block diagonal or not symmetric.
  *    Workspace: the band factors (sum over fractures of n_f (w_f + 1)
- *    doubles) plus 2 x (SM count) x max n_f x 32 doubles of solve scratch.
+ *    doubles) plus min(2 x SM count, 8 GiB / (max n_f x 256 B)) x max n_f x
+ *    32 doubles of solve scratch.
  * C, B: n_h x n_u CSR; CT, BT: their transposes (n_u x n_h); Gh: n_h x n_h;
  * Gu: n_u x n_u.  nx, ny, T, offset are host arrays; all CSR arrays are
  * device arrays; C..Gu must stay valid until pp_destroy, A only during

@@ -668,7 +668,11 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
     D.L = B.take<double>(H.elems);
     D.dinv = B.take<double>(d->n_h);
     D.gwin = B.take<double>(H.gwin_elems);
-    D.grid_trace = std::max(1, std::min(H.n_items, 2 * num_sms()));
+    // forward-sweep scratch: max_n x 32 doubles per block of the M build,
+    // at most 8 GiB in all (fewer blocks for very large fractures)
+    const long long per_block = std::max(1LL, (long long)H.max_n * kBandCols * (long long)sizeof(double));
+    const long long cap_blocks = std::max(1LL, (8LL << 30) / per_block);
+    D.grid_trace = (int)std::max(1LL, std::min<long long>({(long long)H.n_items, 2LL * num_sms(), cap_blocks}));
     D.Z = B.take<double>((long long)D.grid_trace * H.max_n * kBandCols);
     D.flags = B.take<int>(2);
     S->band_elems = H.elems;
