@@ -112,4 +112,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.pp_autotune(ctypes.byref(csr), ctypes.byref(o), ctypes.c_void_p(8), 1 << 20, None, 0, None,
                            None) == P.PP_EINVAL  # unaligned workspace
     assert lib.pp_set_lowrank(None, None, 0, 0, None) == P.PP_EINVAL
+    assert lib.pp_fracture_bands(0, None, None, None, None, None, None) == P.PP_EINVAL
+    off = np.array([0, 2], dtype=np.int64)
+    assert lib.pp_fracture_bands(1, ctypes.c_void_p(off.ctypes.data), None, None, None, None, None) == P.PP_EINVAL
     assert b"NULL" in lib.pp_last_error(None)
