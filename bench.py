@@ -104,14 +104,18 @@ def bytes_per_step_launch(nnz: int, n: int, k: int, prec: str, ndiag: int = 0) -
     return (k * mat + n * sv * vec_passes) / k
 
 
-def flops_per_step_launch(nnz: int, n: int, k: int) -> float:
-    """Arithmetic of one fused degree step, averaged over the k steps: one
-    fused multiply-add per stored nonzero, then per row 3 flops in the first
-    step (y = ca r + cb A r) and 6 in the others (y = ca x + cb x_old +
-    cc (r - A x))."""
+def flops_per_step_launch(nnz: int, n: int, k: int, ndiag: int = 0) -> float:
+    """Algorithmic arithmetic of one fused degree step, averaged over the k
+    steps: one multiply-add (2 flops) per nonzero of A x -- with the unit
+    diagonal of the Jacobi-scaled DIA storage the diagonal term is the
+    vector entry itself, so 2 (nnz - n) + n -- then per row 3 flops in the
+    first step (y = ca r + cb A r) and 6 in the others (y = ca x + cb x_old
+    + cc (r - A x)).  The count is the method's, independent of how a kernel
+    folds the coefficients."""
     if k <= 0:
         return 0.0
-    return 2.0 * nnz + n * (3.0 + 6.0 * (k - 1)) / k
+    mat = 2.0 * nnz if not ndiag else 2.0 * (nnz - n) + n
+    return mat + n * (3.0 + 6.0 * (k - 1)) / k
 
 
 def fp64_peak_tflops() -> float:
@@ -219,55 +223,60 @@ def oracle_iterations(workload: str, k: int, lanczos_steps: int):
     return table.get(f"{workload}/{key}", table.get(f"{base}/{key}"))
 
 
-def cpu_sample(A, b, w, k, alpha, beta, xi):
-    """Oracle seconds per PCG iteration on the full workload: one p_k apply
-    (Algorithm 2, k products) plus one product by A_hat, single thread."""
+def cpu_solve(A, b, k, lanczos_steps, maxit=10000):
+    """The oracle's solve on all host cores (the oracle's loops with OpenMP
+    over rows, liboracle_omp.so): Jacobi seed, Lanczos interval from the
+    shared start vector, xi = clip(10 alpha/beta, 1e-6, 1e-2), PCG from x = 0
+    to rtol 1e-8 with p_k by Algorithm 2.  Returns (x, stats, setup s, PCG s,
+    threads)."""
     import oracle as O
 
-    vh, wgt = O.jacobi_scale(A)
-    from paper_2208_01339_gb300.inputs import CSR
+    from paper_2208_01339_gb300 import inputs as I
 
-    Ah = CSR(A.n, A.rowptr, A.col, vh)
-    r = wgt * b
-    t0 = time.perf_counter()
-    z = O.cheb_apply(Ah, alpha, beta, xi, k, r)
-    O.spmv(Ah, z)
-    return time.perf_counter() - t0
+    x, st, t_setup, t_pcg = O.omp_solve(A, b, I.lanczos_start(A.n, 0), k, lanczos_steps, rtol=1e-8, maxit=maxit)
+    return x, st, t_setup, t_pcg, O.omp_threads()
+
+
+# reference arm: PCG iterations per timed step (a bounded sample of the solve)
+REF_ITERS = 12
 
 
 def run_reference(args, w, rank):
+    """The oracle on the host cores, on the same workload and metric: each
+    step runs the oracle's all-core solve for REF_ITERS PCG iterations (setup
+    -- scaling, Lanczos, coefficients -- excluded like the GPU's), and the
+    time to rtol is the median time per iteration times the oracle's own
+    iteration count for this workload."""
     if rank != 0:
         return
     import oracle as O
 
     O.build()
-    from paper_2208_01339_gb300 import inputs as I
-
     A, b = build_problem(w)
     k = args.k if args.k is not None else w["k"]
-    vh, _ = O.jacobi_scale(A)
-    a, bb = O.lanczos(A, I.lanczos_start(A.n, 0), w["lanczos"], val=vh)
-    alpha, beta = O.tridiag_extremes(a, bb)
-    xi = min(max(10 * alpha / beta, 1e-6), 1e-2)
     iters = oracle_iterations(args.workload, k, w["lanczos"])
-    src = "oracle's own count (tests/golden/oracle_iterations.json)"
-    if iters is None:
-        iters, src = None, "unknown"
-    for _ in range(args.warmup):
-        cpu_sample(A, b, w, k, alpha, beta, xi)
+    src = "the oracle's own count, tests/golden/oracle_iterations.json"
     per_it = []
-    for _ in range(args.steps):
-        per_it.append(cpu_sample(A, b, w, k, alpha, beta, xi))
+    threads = O.omp_threads()
+    for i in range(args.warmup + args.steps):
+        _, st, _, t_pcg, _ = cpu_solve(A, b, k, w["lanczos"], maxit=REF_ITERS)
+        if i >= args.warmup:
+            per_it.append(t_pcg / max(1, st["iterations"]))
     t_it = statistics.median(per_it)
-    value = t_it * iters if iters else None
-    sample = (f"1 PCG iteration's operator work (p_{k} apply + 1 product by A_hat) on the full {A.n}-row matrix, "
-              f"single thread, x {iters} iterations ({src})")
+    if iters is None:  # no stored count: run the full solve once for it
+        _, st, _, _, _ = cpu_solve(A, b, k, w["lanczos"])
+        iters, src = st["iterations"], "a full oracle solve in this run"
+    value = t_it * iters
+    sample = (f"{REF_ITERS} PCG iterations per step of the oracle's all-core solve (OpenMP over rows, "
+              f"{threads} threads) on the full {A.n}-row workload, k = {k}; time to rtol = median seconds per "
+              f"iteration x {iters} iterations ({src})")
     out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": value * 1e3 if value else None, "higher_is_better": False,
+           "warmup": args.warmup, "ms_per_step": t_it * REF_ITERS * 1e3, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "oracle_ms_per_iteration": t_it * 1e3,
-           "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "k": k},
-           "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "k": k, "lanczos_steps": w["lanczos"]},
+           "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample,
+                            "extrapolation": f"x {iters / REF_ITERS:.1f} (iterations {iters} / {REF_ITERS} timed)"},
            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -413,6 +422,8 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
     """Fracture-network Schur complement: PCG on S_hat to rtol 1e-8."""
     import torch
 
+    from paper_2208_01339_gb300 import polyprec as P_
+
     info = S.info()
     for _ in range(max(3, args.warmup)):
         S.solve(bt)
@@ -446,8 +457,34 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     recover_ms = ev0.elapsed_time(ev1) / reps
-    # one S_hat product: M streamed twice (2-RHS and 1-RHS products), 3 FMAs per entry
+    # one S_u product timed alone: the trace blocks M are streamed twice (t = M v,
+    # then M (G^h t - alpha z)), one FMA per entry each time
     m_bytes = info["nnz"] * 8
+    xr = torch.as_tensor(np.random.default_rng(0).standard_normal(net.n_u), device=dev)
+    yr = torch.empty_like(xr)
+    for _ in range(3):
+        S.schur_apply(xr, yr)
+    reps = 20
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(reps):
+        S.schur_apply(xr, yr)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    prod_s = ev0.elapsed_time(ev1) / reps / 1e3
+    fp64_peak = P_.fp64_fma_rate(reps=3) if w["prec"] == "f64" else None
+    peak_bw, peak_src = measured_peak()
+    prod_bytes = 2.0 * m_bytes
+    prod_flops = 4.0 * info["nnz"]
+    roof = {"bound": "alu", "kernel": "S_u product: 2 x m_apply_kernel (FP64 trace blocks) + 3 sparse trace kernels",
+            "achieved": round(prod_flops / prod_s / 1e12, 4), "unit": "TFLOP/s",
+            "peak": round(fp64_peak, 4) if fp64_peak else None,
+            "frac": round(prod_flops / prod_s / 1e12 / fp64_peak, 4) if fp64_peak else None,
+            "peak_source": "measured in this run: pp_fp64_fma_rate", "traffic": None,
+            "algorithmic_flops_per_product": int(prod_flops), "avg_product_us": round(prod_s * 1e6, 2),
+            "hbm": {"achieved": round(prod_bytes / prod_s / 1e9, 1), "peak": peak_bw, "unit": "GB/s",
+                    "frac": round(prod_bytes / prod_s / 1e9 / peak_bw, 4), "peak_source": peak_src,
+                    "algorithmic_bytes_per_product": int(prod_bytes)}}
     if rank == 0:
         out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -463,7 +500,8 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
                "iterations": it, "setup_ms": round(info["t_setup_ms"], 2), "alpha_hat": info["alpha_hat"],
                "beta_hat": info["beta_hat"], "xi": info["xi"],
                "apply_ms": sum(s["t_apply_ms"] for s in stats) / max(1, sum(s["apply_launches"] for s in stats)),
-               "trace_block_bytes": m_bytes, "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
+               "trace_block_bytes": m_bytes, "roofline": roof,
+               "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
         print(json.dumps(out), flush=True)
 
 
@@ -482,6 +520,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=0, help="PCG iterations per host check (default: per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP32/BF16 and k = 80 comparison solves of the default workload")
     ap.add_argument("--k-sweep", default="", help="comma-separated degrees: time one solve per degree instead")
     ap.add_argument("--batch-count", type=int, default=0, help="override the batched workload's instance count")
     ap.add_argument("--batch-nmax", type=int, default=0, help="override the batched workload's largest grid")
@@ -620,50 +660,43 @@ def main():
         return
 
     it = [s["iterations"] for s in stats]
-    t_apply = sum(s["t_apply_ms"] for s in stats)
-    n_launch = sum(s["apply_launches"] for s in stats)
-    bpl = bytes_per_step_launch(A.nnz, A.n, k, w["prec"], info["ndiag"] if info["format"] == 3 else 0)
-    roof = None
     fmt_name = {1: "CSR", 2: "SELL", 3: "DIA"}[info["format"]]
-    layout = (f"SELL C={info['sell_C']} sigma={info['sell_sigma']} {'direct' if variant == 1 else 'tma'}"
-              if info["format"] == 2 else (f"DIA ndiag={info['ndiag']}" if info["format"] == 3 else "CSR"))
-    if n_launch > 0 and t_apply > 0:
-        avg_s = t_apply / 1e3 / n_launch
-        peak, peak_src = measured_peak()
-        ach = bpl / avg_s / 1e9
-        kname = {2: f"sell_step_{'tma_' if variant != 1 else ''}kernel ({w['prec']}, C={info['sell_C']})",
-                 3: f"dia_step_kernel ({w['prec']}, {info['ndiag']} stored diagonals)",
-                 1: f"csr_step_kernel ({w['prec']})"}[info["format"]]
-        tr = traffic_from_profile(args.workload, k, w["prec"], layout)
-        hbm = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-               "traffic": tr["bytes"] if tr else None, "traffic_of": tr, "peak_source": peak_src,
-               "kernel": kname, "algorithmic_bytes_per_launch": int(bpl), "avg_launch_us": round(avg_s * 1e6, 2)}
-        if w["prec"] == "f64":
-            # FP64 arithmetic is scarce on GB300: the step kernel is bound by the
-            # FP64 pipe before HBM (ncu: FP64 pipe ~77% busy, DRAM ~50%).
-            fl = flops_per_step_launch(A.nnz, A.n, k)
-            tf = fl / avg_s / 1e12
-            pk = fp64_peak_tflops()
-            roof = {"bound": "alu", "achieved": round(tf, 4), "peak": round(pk, 4), "unit": "TFLOP/s",
-                    "frac": round(tf / pk, 4), "traffic": hbm["traffic"], "traffic_of": hbm["traffic_of"],
-                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                    "kernel": kname, "algorithmic_flops_per_launch": int(fl), "avg_launch_us": hbm["avg_launch_us"],
-                    "hbm": {k2: hbm[k2] for k2 in ("achieved", "peak", "unit", "frac", "peak_source",
-                                                  "algorithmic_bytes_per_launch")}}
-        else:
-            roof = hbm
-    cpu = None
+    layout = layout_name(info, variant)
+    fp64_peak = None
+    if w["prec"] == "f64" or not args.no_variants:
+        fp64_peak = P.fp64_fma_rate(reps=5)
+    roof = step_roofline(info, stats, A, k, w["prec"], args.workload, variant, fp64_peak)
+
+    # one-shot time to solution: setup (layout, seed scaling, Lanczos,
+    # coefficients) plus one solve, wall clock, on a fresh context
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    S1 = P.Solver(rp, ci, va, A.n, **opts)
+    x1, _ = S1.solve(bt)
+    torch.cuda.synchronize(dev)
+    one_shot = time.perf_counter() - t0
+    S1.close()
+    del S1, x1
+
+    cpu, err, x_oracle = None, None, None
+    xg = x.cpu().numpy()
     if not args.no_cpu_baseline and world == 1:
         import oracle as O
 
         O.build()
-        t_it = cpu_sample(A, b, w, k, info["alpha_hat"], info["beta_hat"], info["xi"])
-        oi = oracle_iterations(args.workload, k, w["lanczos"])
-        its = oi if oi else statistics.median(it)
-        src = "oracle's own iteration count" if oi else "the GPU iteration count"
-        cpu = {"value": t_it * its, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"1 PCG iteration's operator work (p_{k} apply + 1 product) on the full {A.n}-row matrix, "
-                         f"single thread, extrapolated x {its} iterations ({src})"}
+        x_oracle, st_o, t_setup_o, t_pcg_o, threads = cpu_solve(A, b, k, w["lanczos"])
+        cpu = {"value": t_pcg_o, "unit": "s", "cores": threads, "kind": "oracle",
+               "sample": f"the whole workload: one full solve to rtol 1e-8 ({st_o['iterations']} iterations) by the "
+                         f"oracle's loops with OpenMP over rows on {threads} host threads; setup (scaling, "
+                         f"{w['lanczos']} Lanczos steps, coefficients: {t_setup_o:.2f} s) excluded like the GPU's; "
+                         f"no extrapolation",
+               "iterations": st_o["iterations"], "setup_s": round(t_setup_o, 3)}
+        err = solution_error(xg, x_oracle, int(statistics.median(it)), st_o["iterations"])
+
+    variants = None
+    if not args.no_variants and args.workload == "diffusion192":
+        variants = run_variants(args, A, rp, ci, va, bt, opts, x_oracle, fp64_peak, ms / 1e3, dev)
+
     out = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -679,13 +712,129 @@ def main():
                    "lowrank": args.lowrank,
                    "parallelism": f"replicas x{world}"},
         "iterations": int(statistics.median(it)), "setup_ms": round(info["t_setup_ms"], 2),
+        "one_shot_s": round(one_shot, 4),
         "alpha_hat": info["alpha_hat"], "beta_hat": info["beta_hat"], "xi": info["xi"],
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "err_vs_oracle": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "north_star": variants,
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def layout_name(info, variant) -> str:
+    if info["format"] == 2:
+        return f"SELL C={info['sell_C']} sigma={info['sell_sigma']} {'direct' if variant == 1 else 'tma'}"
+    return f"DIA ndiag={info['ndiag']}" if info["format"] == 3 else "CSR"
+
+
+def solution_error(xg, xo, it_gpu, it_oracle):
+    """Relative 2-norm and per-element (scaled by max |x|) difference of the
+    GPU solution from the oracle's, both solved to rtol 1e-8."""
+    d = np.asarray(xg) - np.asarray(xo)
+    return {"rel_2norm": float(np.linalg.norm(d) / np.linalg.norm(xo)),
+            "rel_max_elem": float(np.max(np.abs(d)) / np.max(np.abs(xo))),
+            "iterations_gpu": int(it_gpu), "iterations_oracle": int(it_oracle),
+            "oracle": "the oracle's all-core FP64 solve of the same system to the same rtol"}
+
+
+def step_roofline(info, stats, A, k, prec, workload, variant, fp64_peak):
+    """Roofline of the dominant kernel, the fused degree step: algorithmic
+    bytes (or flops) per launch over its average launch time, both from the
+    solves' own CUDA-event records of the step launches."""
+    t_apply = sum(s["t_apply_ms"] for s in stats)
+    n_launch = sum(s["apply_launches"] for s in stats)
+    if n_launch <= 0 or t_apply <= 0:
+        return None
+    bpl = bytes_per_step_launch(A.nnz, A.n, k, prec, info["ndiag"] if info["format"] == 3 else 0)
+    avg_s = t_apply / 1e3 / n_launch
+    peak, peak_src = measured_peak()
+    ach = bpl / avg_s / 1e9
+    layout = layout_name(info, variant)
+    kname = {2: f"sell_step_{'tma_' if variant != 1 else ''}kernel ({prec}, C={info['sell_C']})",
+             3: f"dia_step_kernel ({prec}, {info['ndiag']} stored diagonals)",
+             1: f"csr_step_kernel ({prec})"}[info["format"]]
+    tr = traffic_from_profile(workload, k, prec, layout)
+    hbm = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+           "traffic": tr["bytes"] if tr else None, "traffic_of": tr, "peak_source": peak_src,
+           "kernel": kname, "algorithmic_bytes_per_launch": int(bpl), "avg_launch_us": round(avg_s * 1e6, 2)}
+    if prec != "f64":
+        return hbm
+    # FP64 arithmetic is scarce on GB300: the FP64 step is bound by the FP64
+    # pipe before HBM (ncu: FP64 pipe ~90% busy, DRAM ~45%)
+    fl = flops_per_step_launch(A.nnz, A.n, k, info["ndiag"] if info["format"] == 3 else 0)
+    tf = fl / avg_s / 1e12
+    pk = fp64_peak if fp64_peak else fp64_peak_tflops()
+    return {"bound": "alu", "achieved": round(tf, 4), "peak": round(pk, 4), "unit": "TFLOP/s",
+            "frac": round(tf / pk, 4), "traffic": hbm["traffic"], "traffic_of": hbm["traffic_of"],
+            "peak_source": ("measured in this run: pp_fp64_fma_rate (independent DFMA chains on every SM, CUDA "
+                            "events)" if fp64_peak else "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz"),
+            "peak_derived": round(fp64_peak_tflops(), 4), "frac_of_derived": round(tf / fp64_peak_tflops(), 4),
+            "kernel": kname, "algorithmic_flops_per_launch": int(fl), "avg_launch_us": hbm["avg_launch_us"],
+            "hbm": {k2: hbm[k2] for k2 in ("achieved", "peak", "unit", "frac", "peak_source",
+                                          "algorithmic_bytes_per_launch")}}
+
+
+# The precision variant and the paper's degree range on the same system:
+# (name, apply precision, degree, outer iteration: 0 PCG, 1 FCG(1))
+VARIANTS = [("f32_k20", "f32", 20, 1), ("bf16_k20", "bf16", 20, 1), ("f64_k80", "f64", 80, 0),
+            ("f32_k80", "f32", 80, 1), ("bf16_k80", "bf16", 80, 1)]
+
+
+def run_variants(args, A, rp, ci, va, bt, opts, x_oracle, fp64_peak, fp64_s, dev):
+    """Time to rtol 1e-8 of the FP32/BF16 applications of p_k inside FP64
+    flexible CG, and of FP64 at k = 80, on the same matrix, right-hand side
+    and layout as the FP64 line: the comparison the method's precision
+    variant is judged by (faster than plain FP64 on the same GPU)."""
+    import torch
+
+    from paper_2208_01339_gb300 import polyprec as P
+
+    stream = torch.cuda.current_stream(dev)
+    out = []
+    reps = max(3, min(args.steps, 10))
+    for name, prec, kk, flex in VARIANTS:
+        o = dict(opts, apply_prec=prec, k=kk, flexible=flex)
+        S = P.Solver(rp, ci, va, A.n, **o)
+        info = S.info()
+        x = torch.zeros_like(bt)
+        for _ in range(3):
+            S.solve(bt, x)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record(stream)
+        for _ in range(reps):
+            _, st = S.solve(bt, x)
+            stats.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / reps / 1e3
+        roof = step_roofline(info, stats, A, kk, prec, f"diffusion192{'' if prec == 'f64' else '_' + prec}",
+                             o.get("sell_variant", 0), fp64_peak)
+        ent = {"name": name, "apply": prec, "k": kk, "outer": "FCG(1)" if flex else "PCG", "time_s": round(t, 5),
+               "iterations": int(stats[-1]["iterations"]), "rel_res": stats[-1]["rel_res"],
+               "speedup_vs_fp64_k5": round(fp64_s / t, 3), "steps_timed": reps,
+               "step_roofline": {kk2: roof[kk2] for kk2 in ("bound", "achieved", "peak", "unit", "frac",
+                                                           "avg_launch_us")} if roof else None}
+        if x_oracle is not None:
+            xv = x.cpu().numpy()
+            d = xv - x_oracle
+            ent["err_vs_oracle"] = {"rel_2norm": float(np.linalg.norm(d) / np.linalg.norm(x_oracle)),
+                                    "rel_max_elem": float(np.max(np.abs(d)) / np.max(np.abs(x_oracle)))}
+        out.append(ent)
+        S.close()
+        del S
+    t64_80 = next(e["time_s"] for e in out if e["name"] == "f64_k80")
+    for e in out:
+        if e["k"] == 80 and e["apply"] != "f64":
+            e["speedup_vs_fp64_k80"] = round(t64_80 / e["time_s"], 3)
+    best = min(out, key=lambda e: e["time_s"])
+    return {"fp64_k5_s": round(fp64_s, 5), "variants": out, "fastest": best["name"],
+            "fastest_speedup_vs_fp64": round(fp64_s / best["time_s"], 3),
+            "note": "same matrix, right-hand side, Lanczos interval length and layout; FP64 outer iteration, "
+                    "dots and residuals in every variant; err_vs_oracle against the oracle's FP64 solution"}
 
 
 if __name__ == "__main__":

@@ -121,6 +121,10 @@ typedef struct {
                          Algorithm 2; PP_POLY_NEWTON: the Newton form of
                          Algorithm 1 (k = 2^nlev - 1, FP64 apply only;
                          2 nlev n doubles more workspace)                  */
+  int max_blocks;     /* > 0: at most this many thread blocks per launch of
+                         the step and vector kernels (the grid-stride loops
+                         then take more rounds), e.g. to leave SMs to other
+                         streams; 0: grids sized by the device            */
 } pp_options;
 
 typedef struct {
@@ -314,7 +318,12 @@ int pp_schur_workspace_size(const pp_dfn* d, const pp_options* opt, size_t* byte
 int schur_setup(pp_ctx** ctx, const pp_dfn* d, const pp_options* opt, void* workspace,
                 size_t ws_bytes, void* stream);
 
-/* y = S_u r (Algorithm 3; r, y device n_u; unscaled).  Asynchronous. */
+/* y = S_u r (Algorithm 3; r, y device n_u; unscaled).  Algorithm 3's
+ * three applications of A^{-1} become two: A^{-1} B r and A^{-1} G^h t
+ * (t = A^{-1} C r) enter S_u r only through C^T (A^{-1} G^h t - alpha
+ * A^{-1} B r), which by linearity is one application, to G^h t - alpha B r.
+ * Each application is a product with the trace blocks of A^{-1}.
+ * Asynchronous. */
 int schur_apply(pp_ctx* ctx, const double* r, double* y, void* stream);
 
 /* ds (device, n_u) = diag(S_u) computed at setup (Algorithm 4). */
@@ -425,6 +434,18 @@ int pp_mlp_train_step(pp_mlp* mlp, const float* x, const float* t, int batch, fl
                       float* loss_host, void* stream);
 int pp_mlp_destroy(pp_mlp* mlp);
 
+/* ---- measurement (no counterpart in the paper) ------------------------- */
+
+/* The FP64 fused multiply-add rate of the current device in TFLOP/s (2
+ * flops per FMA), for the arithmetic roofline of the FP64 step kernels:
+ * 4 or 8 blocks of 256 threads per SM, each thread 8 or 16 independent
+ * chains of 2,048 FMAs; for each of these four shapes one warm-up launch
+ * and `reps` (1..100) launches timed with CUDA events on `stream`; the
+ * fastest launch counts.  sink: device, 1 double,
+ * never written in practice (it keeps the loop from being removed).
+ * Synchronous.  PP_EINVAL on a NULL pointer or reps out of range. */
+int pp_fp64_fma_rate(double* sink, int reps, double* tflops, void* stream);
+
 /* ---- workspace-free apply (no counterpart in the paper) ---------------- */
 
 /* z = p_k(A) r for a CSR matrix on the device, without a workspace and
@@ -439,6 +460,8 @@ int pp_mlp_destroy(pp_mlp* mlp);
  * the process exits.  The polynomial is the one polyprec_apply uses with
  * seed_scaling = PP_SEED_NONE, format = PP_FMT_CSR and a given interval:
  * coefficients from polyprec_coeffs(alpha, beta, xi, k), k products by A.
+ * z must not overlap r (for k mod 3 == 1 the first step writes z while
+ * later steps still read r); an overlap returns PP_EINVAL.
  * n > 262,144 returns PP_EINVAL with a message; so do other bad arguments.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call

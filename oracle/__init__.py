@@ -42,21 +42,30 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_omp = None
+
+
+def _compile(out: str, srcs, extra, force: bool) -> str:
+    deps = list(srcs) + [os.path.join(_HERE, "oracle.h")]
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= max(os.path.getmtime(d) for d in deps):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off"] + extra + ["-o", tmp] + list(srcs) + [
+        "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc, -O2, portable flags)."""
+    """Compile oracle.c into liboracle.so (gcc, -O2, portable flags), and
+    oracle.c + oracle_omp.c into liboracle_omp.so (-fopenmp), the timed
+    all-core CPU baseline."""
     src = os.path.join(_HERE, "oracle.c")
-    hdr = os.path.join(_HERE, "oracle.h")
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, src, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    _compile(_OMP_PATH, [src, os.path.join(_HERE, "oracle_omp.c")], ["-fopenmp"], force)
+    return _compile(_LIB_PATH, [src], [], force)
 
 
 _d = ctypes.POINTER(ctypes.c_double)
@@ -408,3 +417,37 @@ class Schur:
         lib().oracle_pcg_schur(self._h, _p(ds, ctypes.c_double), _p(r, ctypes.c_double), _p(u, ctypes.c_double),
                                _p(v0, ctypes.c_double), ctypes.byref(o), ctypes.byref(st))
         return u, st.as_dict()
+
+
+def omp_lib():
+    """liboracle_omp.so: the oracle's loops with OpenMP over rows (timed CPU
+    baseline only; parity uses the single-thread lib())."""
+    global _omp
+    if _omp is None:
+        build()
+        L = ctypes.CDLL(_OMP_PATH)
+        L.oracle_omp_threads.restype = ctypes.c_int
+        L.oracle_omp_solve.argtypes = [ctypes.c_int, _i, _i, _d, _d, _d, _d, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(Stats), _d]
+        _omp = L
+    return _omp
+
+
+def omp_threads() -> int:
+    return int(omp_lib().oracle_omp_threads())
+
+
+def omp_solve(A, b, v0, k: int, lanczos_steps: int, rtol: float = 1e-8, maxit: int = 10000, xi: float = -1.0):
+    """All-core PCG solve from x = 0 (Jacobi seed, Lanczos interval, p_k by
+    Algorithm 2).  Returns (x, stats dict, setup seconds, PCG seconds)."""
+    b = _f64(b)
+    v0 = _f64(v0)
+    x = np.zeros(A.n)
+    st = Stats()
+    sec = np.zeros(2)
+    rp, ci, va = _i32(A.rowptr), _i32(A.col), _f64(A.val)
+    omp_lib().oracle_omp_solve(A.n, _p(rp, ctypes.c_int), _p(ci, ctypes.c_int), _p(va, ctypes.c_double),
+                               _p(b, ctypes.c_double), _p(x, ctypes.c_double), _p(v0, ctypes.c_double), int(k),
+                               int(lanczos_steps), float(xi), float(rtol), int(maxit), ctypes.byref(st),
+                               _p(sec, ctypes.c_double))
+    return x, st.as_dict(), float(sec[0]), float(sec[1])

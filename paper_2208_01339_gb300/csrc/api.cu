@@ -157,14 +157,22 @@ int validate_options(pp_ctx* c, const pp_options* o) {
     return fail(c, PP_EUNSUPPORTED, "the Newton form is applied in FP64 only");
   if (o->lowrank > 0 && o->lowrank_steps != 0 && (o->lowrank_steps < o->lowrank || o->lowrank_steps > kMaxLanczos))
     return fail(c, PP_EINVAL, "lowrank > 0 needs lowrank <= lowrank_steps <= 512 (0: 30)");
+  if (o->max_blocks < 0) return fail(c, PP_EINVAL, "max_blocks must be >= 0");
   if (o->lowrank > 30 && o->lowrank_steps == 0)
     return fail(c, PP_EINVAL, "lowrank > 30 needs lowrank_steps >= lowrank");
   return PP_OK;
 }
 
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  return dev < kMaxDevices ? dev : kMaxDevices - 1;
+}
+
 int num_sms() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
+  // 152: the SM count of GB300, used only if the attribute query fails
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
   return sms;
 }
@@ -239,49 +247,33 @@ struct DiaPlan {
 
 // Symmetric diagonal storage applies when every row has its diagonal entry,
 // no entry is repeated, the entries lie on at most kMaxDiag upper offsets
-// (and their mirrors) and a(j, i) == a(i, j) exactly.  Reads the column
-// indices and values to the host (synchronous).
-int plan_dia(const pp_csr* A, const std::vector<int>& rp, DiaPlan& P, cudaStream_t s, pp_ctx* c) {
-  const long long nnz = A->nnz;
-  std::vector<int> col((size_t)std::max<long long>(nnz, 1));
-  std::vector<double> val((size_t)std::max<long long>(nnz, 1));
-  cudaError_t e = cudaMemcpyAsync(col.data(), A->col, sizeof(int) * nnz, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(val.data(), A->val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "reading the matrix for DIA planning");
-  std::vector<long long> offs;
-  const int n = A->n;
-  for (int i = 0; i < n; ++i) {
-    bool diag = false;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-      const int j = col[p];
-      if (j < 0 || j >= n) return fail(c, PP_EINVAL, "column index out of range");
-      for (int q = rp[i]; q < p; ++q)
-        if (col[q] == j) return fail(c, PP_EUNSUPPORTED, "DIA: repeated entry in a row");
-      const long long d = (long long)j - i;
-      if (d == 0) diag = true;
-      if (d < 0) {  // mirror entry a(j, i) must exist with the same value
-        bool found = false;
-        for (int q = rp[j]; q < rp[j + 1]; ++q)
-          if (col[q] == i) {
-            found = val[q] == val[p];
-            break;
-          }
-        if (!found) return fail(c, PP_EUNSUPPORTED, "DIA: the matrix is not symmetric");
-        continue;
-      }
-      if (std::find(offs.begin(), offs.end(), d) == offs.end()) {
-        if ((int)offs.size() == kMaxDiag) return fail(c, PP_EUNSUPPORTED, "DIA: more than 16 upper diagonals");
-        offs.push_back(d);
-      }
+// (and their mirrors) and a(j, i) == a(i, j) exactly.  Checked on the device
+// (dia_plan, which also validates rowptr); synchronous.
+int plan_dia(const pp_csr* A, DiaPlan& P, cudaStream_t s, pp_ctx* c) {
+  DiaPlanTable t;
+  cudaError_t e = dia_plan(A->n, A->nnz, A->rowptr, A->col, A->val, &t, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "DIA planning");
+  if (t.err != ~0ull) {
+    const long long row = (long long)(t.err >> 8);
+    const std::string at = " (row " + std::to_string(row) + ")";
+    switch ((int)(t.err & 0xff)) {
+      case kDiaBadRowptr: return fail(c, PP_EINVAL, "rowptr is not monotone or does not span [0, nnz]" + at);
+      case kDiaBadCol: return fail(c, PP_EINVAL, "column index out of range" + at);
+      case kDiaRepeated: return fail(c, PP_EUNSUPPORTED, "DIA: repeated entry in a row" + at);
+      case kDiaNoDiagonal: return fail(c, PP_EUNSUPPORTED, "DIA: a row has no diagonal entry" + at);
+      case kDiaUnsymmetric: return fail(c, PP_EUNSUPPORTED, "DIA: the matrix is not symmetric" + at);
+      default: return fail(c, PP_EUNSUPPORTED, "DIA: more than 16 upper diagonals");
     }
-    if (!diag) return fail(c, PP_EUNSUPPORTED, "DIA: a row has no diagonal entry");
   }
+  std::vector<long long> offs{0};
+  for (int h = 0; h < kDiaSlots; ++h)
+    if (t.slot[h]) offs.push_back((long long)t.slot[h] - 1);
+  if (t.count != (int)offs.size() - 1) return fail(c, PP_ECUDA, "DIA planning: inconsistent offset table");
+  if ((int)offs.size() > kMaxDiag) return fail(c, PP_EUNSUPPORTED, "DIA: more than 16 upper diagonals");
   std::sort(offs.begin(), offs.end());
-  if (offs.empty() || offs[0] != 0 || offs.back() > 0x7fffffffLL)
-    return fail(c, PP_EUNSUPPORTED, "DIA: unsupported diagonal offsets");
+  if (offs.back() > 0x7fffffffLL) return fail(c, PP_EUNSUPPORTED, "DIA: unsupported diagonal offsets");
   P.nd = (int)offs.size();
-  for (int t = 0; t < P.nd; ++t) P.doff[t] = (int)offs[t];
+  for (int q = 0; q < P.nd; ++q) P.doff[q] = (int)offs[q];
   P.dpad = (offs.back() + 31) / 32 * 32;
   return PP_OK;
 }
@@ -319,6 +311,9 @@ void init_desc(pp_ctx* c, const pp_csr* A, const SellPlan& P, const DiaPlan& D) 
     for (int t = 0; t < kMaxDiag; ++t) c->A64.doff[t] = t < D.nd - unit ? D.doff[t + unit] : 0;
     c->A64.dpad = D.dpad;
     c->A64.dstride = D.dpad + c->n_pad;
+    // FP32/BF16 steps on the 7-point stencil: TMA-staged tiles when asked
+    // for (sell_variant = 2); direct loads otherwise
+    c->A64.tma = c->opt.sell_variant == 2;
     c->nnz_pad = (long long)std::max(1, D.nd - unit) * c->A64.dstride;
   } else if (c->A64.format == PP_FMT_SELL) {
     c->A64.C = P.C;
@@ -408,11 +403,12 @@ extern "C" int pp_workspace_size(const pp_csr* A, const pp_options* opt, size_t*
   SellPlan P;
   DiaPlan D;
   const int fmt = choose_format(*opt, A->n);
-  if (fmt == PP_FMT_SELL || fmt == PP_FMT_DIA) {
+  if (fmt == PP_FMT_SELL) {
     std::vector<int> h;
     if ((rc = read_rowptr(A, h, nullptr, &tmp))) return rc;
-    if (fmt == PP_FMT_SELL) P = plan_sell(h, A->n, choose_C(*opt), opt->sell_sigma);
-    if (fmt == PP_FMT_DIA && (rc = plan_dia(A, h, D, nullptr, &tmp))) return rc;
+    P = plan_sell(h, A->n, choose_C(*opt), opt->sell_sigma);
+  } else if (fmt == PP_FMT_DIA && (rc = plan_dia(A, D, nullptr, &tmp))) {
+    return rc;
   }
   init_desc(&tmp, A, P, D);
   *bytes = layout(&tmp, nullptr, P);
@@ -443,12 +439,15 @@ extern "C" int pcg_setup(pp_ctx** out, const pp_csr* A, const pp_options* opt, v
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
 
-  std::vector<int> h;
-  if ((rc = read_rowptr(A, h, s, c))) return bail(rc);
   SellPlan P;
   DiaPlan D;
-  if (choose_format(*opt, A->n) == PP_FMT_SELL) P = plan_sell(h, A->n, choose_C(*opt), opt->sell_sigma);
-  if (choose_format(*opt, A->n) == PP_FMT_DIA && (rc = plan_dia(A, h, D, s, c))) return bail(rc);
+  if (choose_format(*opt, A->n) == PP_FMT_DIA) {
+    if ((rc = plan_dia(A, D, s, c))) return bail(rc);  // validates rowptr on the device
+  } else {
+    std::vector<int> h;
+    if ((rc = read_rowptr(A, h, s, c))) return bail(rc);
+    if (choose_format(*opt, A->n) == PP_FMT_SELL) P = plan_sell(h, A->n, choose_C(*opt), opt->sell_sigma);
+  }
   init_desc(c, A, P, D);
   const size_t need = layout(c, nullptr, P);
   if (ws_bytes < need) return bail(fail(c, PP_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes"));
@@ -522,6 +521,11 @@ extern "C" int pcg_setup(pp_ctx** out, const pp_csr* A, const pp_options* opt, v
     // DIA kernels size their grid per variant (one resident wave); this is the cap
     if (c->A64.format == PP_FMT_DIA) c->grid_step = (int)std::max(1LL, std::min<long long>(kMaxGrid, want));
     c->grid_step_lp = c->grid_step;
+    if (opt->max_blocks > 0) {
+      c->grid_step = std::min(c->grid_step, opt->max_blocks);
+      c->grid_step_lp = std::min(c->grid_step_lp, opt->max_blocks);
+      c->grid_vec = std::min(c->grid_vec, opt->max_blocks);
+    }
   }
   rc = setup_interval_and_coeffs(c, s);
   if (rc) return bail(rc);

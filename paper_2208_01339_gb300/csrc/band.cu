@@ -422,7 +422,7 @@ __global__ void band_solve_kernel(BandDev D, double* z, double* y) {
 
 int grid_for(long long work, int block) {
   const long long g = (work + block - 1) / block;
-  return (int)std::max(1LL, std::min<long long>(g, 152LL * 16));
+  return (int)std::max(1LL, std::min<long long>(g, 16LL * num_sms()));
 }
 
 cudaError_t allow_smem(const void* fn, size_t bytes) {
@@ -668,7 +668,7 @@ cudaError_t band_trace_blocks(const BandDev& D, const long long* toff, const lon
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  band_symmetrize_kernel<<<152 * 8, 256, 0, s>>>(D.n_f, toff, moff, D.tposa, M);
+  band_symmetrize_kernel<<<8 * num_sms(), 256, 0, s>>>(D.n_f, toff, moff, D.tposa, M);
   return cudaGetLastError();
 }
 

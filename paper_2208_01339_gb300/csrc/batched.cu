@@ -742,7 +742,7 @@ __global__ void b_scale_kernel(BatchDev d, double* __restrict__ oval, float* __r
 
 int grid_b(long long nslices) {
   long long g = (nslices * 32 + kBlock - 1) / kBlock;
-  return (int)std::max(1LL, std::min<long long>(g, 152LL * 8));
+  return (int)std::max(1LL, std::min<long long>(g, 8LL * num_sms()));
 }
 
 }  // namespace
@@ -945,7 +945,7 @@ struct BLaunch {
 cudaError_t b_reduce(pp_batch_state* B, int op, double* lan_out, int j, cudaStream_t s) {
   const BatchDev& d = B->d;
   const int items = (op == kRedLanA || op == kRedLanB || op == kRedNrm) ? d.nb : d.ncols;
-  const int g = std::max(1, std::min(items, 152 * 8));
+  const int g = std::max(1, std::min(items, 8 * num_sms()));
   switch (op) {
     case kRedBB: b_reduce_kernel<kRedBB><<<g, kBlock, 0, s>>>(d, B->c, B->part0, B->part1, lan_out, j); break;
     case kRedPQ: b_reduce_kernel<kRedPQ><<<g, kBlock, 0, s>>>(d, B->c, B->part0, B->part1, lan_out, j); break;

@@ -13,7 +13,7 @@ struct pp_batch_state;  // batched.cu
 
 namespace pp {
 
-constexpr int kMaxGrid = 152 * 16;   // upper bound on blocks of any reducing kernel
+constexpr int kMaxGrid = 4096;      // upper bound on blocks of any reducing kernel (16 per SM up to 256 SMs)
 constexpr int kMaxCheck = 64;        // upper bound on iterations per host check
 
 struct SellPlan {
@@ -32,7 +32,6 @@ double auto_xi(double a, double b);
 void tridiag_extremes_jacobi(const std::vector<double>& a, const std::vector<double>& b, double* lmin,
                              double* lmax);
 int validate_options(pp_ctx* c, const pp_options* o);
-int num_sms();
 
 // solve.cu
 int setup_interval_and_coeffs(pp_ctx* c, cudaStream_t s);
@@ -96,7 +95,7 @@ struct pp_ctx {
   double* partials = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
-  int num_sms = 152, grid_step = 1, grid_vec = 1;
+  int num_sms = 0, grid_step = 1, grid_vec = 1;
   int grid_step_lp = 1;  // blocks of the step kernels on the apply-precision matrix (mixed)
   double alpha_hat = 0, beta_hat = 0, xi = 0, theta_bar = 0, delta = 0, sigma_bar = 0;
   std::vector<double> rho;

@@ -13,6 +13,13 @@ namespace pp {
 
 enum Prec { kF64 = 0, kF32 = 1, kBF16 = 2 };
 
+// Streaming multiprocessors of the current device (grid sizing), and the
+// current device's ordinal clamped to [0, kMaxDevices) for per-device
+// caches of launch attributes and occupancy (api.cu).
+constexpr int kMaxDevices = 64;
+int num_sms();
+int current_device();
+
 // One fused pass of a degree step (or a plain product) over the matrix:
 //   kSpmv    y = A x
 //   kResid   y = r - A x
@@ -147,6 +154,27 @@ cudaError_t csr_fill(int n, const int* rowptr, const int* col, const double* val
 cudaError_t sell_convert_values(long long nnz_pad, const double* in, void* out, int out_prec, cudaStream_t s);
 // DIA fill from CSR (entries with col >= row): val[t * dstride + dpad + row] = w_row a w_col (w may be null).
 cudaError_t dia_fill(const MatDesc& dst, const int* rowptr, const int* col, const double* val, const double* w,
+                     cudaStream_t s);
+
+// DIA planning on the device (setup.cu); dia_plan() is synchronous and
+// copies the finished table to the host struct *out.
+constexpr int kDiaSlots = 64;
+enum DiaPlanError {
+  kDiaOk = 0,
+  kDiaBadRowptr = 1,
+  kDiaBadCol = 2,
+  kDiaRepeated = 3,
+  kDiaNoDiagonal = 4,
+  kDiaUnsymmetric = 5,
+  kDiaTooMany = 6
+};
+struct DiaPlanTable {
+  unsigned long long slot[kDiaSlots];  // upper offset + 1, 0 = empty
+  int count;                           // distinct upper offsets
+  int pad_;
+  unsigned long long err;              // (row << 8) | DiaPlanError of the first error; ~0: none
+};
+cudaError_t dia_plan(int n, long long nnz, const int* rowptr, const int* col, const double* val, DiaPlanTable* t,
                      cudaStream_t s);
 
 // DIA step kernels (step_dia.cu).

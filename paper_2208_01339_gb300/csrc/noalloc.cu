@@ -24,7 +24,6 @@ constexpr long long kStaticMaxN = 262144;  // rows; 2 vectors x 2 MiB of FP64
 // Shared by every call on a device and kept until the process exits.
 static __device__ __align__(256) double g_static_scratch[2 * kStaticMaxN];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
@@ -53,6 +52,11 @@ extern "C" int polyprec_apply_csr_static(int n, long long nnz, const int* rowptr
                                          void* stream) {
   if (n <= 0 || nnz < 0 || nnz > 2147483647LL || !rowptr || !col || !val || !r || !z || k < 0)
     return fail(nullptr, PP_EINVAL, "polyprec_apply_csr_static: invalid argument");
+  // the recurrence reads r after step 1 has written z when k mod 3 == 1, so
+  // the two must not share memory
+  const uintptr_t rb = (uintptr_t)r, zb = (uintptr_t)z, bytes = (uintptr_t)n * sizeof(double);
+  if (rb < zb + bytes && zb < rb + bytes)
+    return fail(nullptr, PP_EINVAL, "polyprec_apply_csr_static: z must not overlap r");
   if ((long long)n > kStaticMaxN)
     return fail(nullptr, PP_EINVAL,
                 "polyprec_apply_csr_static: n = " + std::to_string(n) + " exceeds the static limit of " +
@@ -76,11 +80,11 @@ extern "C" int polyprec_apply_csr_static(int n, long long nnz, const int* rowptr
   const double avg = (double)nnz / n;
   A.csr_group = avg < 3 ? 1 : (avg < 40 ? 8 : 32);
   const long long want = ((long long)n * A.csr_group + kBlock - 1) / kBlock;
-  const int grid = (int)std::max(1LL, std::min<long long>(152LL * 8, want));
+  const int grid = (int)std::max(1LL, std::min<long long>(8LL * num_sms(), want));
 
   cudaError_t e = cudaSuccess;
   if (k == 0) {
-    VecLaunch L{(int)std::max(1LL, std::min<long long>(152LL * 8, ((long long)n + kBlock - 1) / kBlock)), nullptr, s};
+    VecLaunch L{(int)std::max(1LL, std::min<long long>(8LL * num_sms(), ((long long)n + kBlock - 1) / kBlock)), nullptr, s};
     e = vec_scale_dot(L, n, nullptr, r, z, kF64, 1.0 / theta_bar, nullptr, nullptr, nullptr, nullptr, nullptr);
   } else {
     // Algorithm 2 with y_k landing in z; y_1 .. y_{k-1} rotate through the

@@ -14,9 +14,13 @@
 // G_m = (K_y + lambda_m I)^{-1}, whose entries are U_{j<}(c) U_{ny-1-j>}(c) /
 // U_{ny}(c), c = 1 + lambda_m/2, U_k the Chebyshev polynomials of the second
 // kind (inverse of a symmetric tridiagonal Toeplitz matrix).  One S_u apply
-// is then 5 launches: two CSR gathers into trace space, one 2-RHS and one
-// 1-RHS block-dense product with M, and the final sparse products fused with
-// the caller's step epilogue (Chebyshev recurrence, Lanczos, dots).
+// is then 5 launches: the CSR gathers into trace space, a block-dense
+// product with M (t = A^{-1} C x), the trace-space combination
+// g = G^h t - alpha B x, a second product with M (A^{-1} g: Algorithm 3's
+// A^{-1} B x and A^{-1} G^h t enter the result only through the combination
+// C^T (A^{-1} G^h t - alpha A^{-1} B x), so by linearity one application
+// serves both), and the final sparse products fused with the caller's step
+// epilogue (Chebyshev recurrence, Lanczos, dots).
 // Algorithm 4 (D_S) uses the same M.  Full-vector solves with A (right-hand
 // side, recovery of h and p) use fast diagonalisation: sine transform along
 // x, a Thomas solve along y per mode, inverse transform.
@@ -69,11 +73,11 @@ struct SchurImpl {
   // the caller's full blocks (for right-hand side and recovery)
   DCsr C, B, Gh, CT, BT;
   // scratch
-  double *vT = nullptr, *zT = nullptr, *tT = nullptr, *wT = nullptr, *gT = nullptr, *w2T = nullptr;
+  double *vT = nullptr, *zT = nullptr, *tT = nullptr, *gT = nullptr, *w2T = nullptr;
   // FP32 copy of M and FP32 trace-space scratch for the preconditioner applied
   // in FP32 (apply_prec = F32; the outer products stay FP64)
   float* M32 = nullptr;
-  float *vT32 = nullptr, *zT32 = nullptr, *tT32 = nullptr, *wT32 = nullptr, *gT32 = nullptr, *w2T32 = nullptr;
+  float *vT32 = nullptr, *zT32 = nullptr, *tT32 = nullptr, *gT32 = nullptr, *w2T32 = nullptr;
   double *fa = nullptr, *fb = nullptr, *fc = nullptr, *fd = nullptr;
   double* ds = nullptr;  // diag(S_u)
 };
@@ -241,13 +245,14 @@ __global__ void trace_gather_kernel(int n_T, DCsr C_T, DCsr B_T, const double* _
   }
 }
 
-// gT = Gh_T tT
+// gT = Gh_T tT - alpha zT (zT may be null: gT = Gh_T tT)
 template <typename T>
-__global__ void trace_gh_kernel(int n_T, DCsr Gh_T, const T* __restrict__ tT, T* __restrict__ gT) {
+__global__ void trace_gh_kernel(int n_T, DCsr Gh_T, const T* __restrict__ tT, const T* __restrict__ zT, T alpha,
+                                T* __restrict__ gT) {
   for (long long r = gtid(); r < n_T; r += gstride()) {
     T g = (T)0;
     for (int p = Gh_T.rowptr[r]; p < Gh_T.rowptr[r + 1]; ++p) g += (T)Gh_T.val[p] * tT[Gh_T.col[p]];
-    gT[r] = g;
+    gT[r] = zT ? g - alpha * zT[r] : g;
   }
 }
 
@@ -258,13 +263,17 @@ __device__ __forceinline__ T warp_sum_t(T x) {
   return x;
 }
 
-// y_k = M x_k for NR right-hand sides: one warp per trace row, fixed order.
-template <int NR, typename T>
-__global__ void __launch_bounds__(kBlock) m_apply_kernel(int n_T, int nf, const long long* __restrict__ toff,
+// y = M x, M the dense trace blocks (fracture f's block M_f is t_f x t_f,
+// row-major, at moff[f]): one warp per trace row; each lane keeps kMU
+// independent partial sums over the columns lane, lane + 32, ... so that
+// kMU coalesced row loads per lane are in flight at once; partial sums and
+// lanes are added in a fixed order.
+constexpr int kMU = 4;
+template <typename T>
+__global__ void __launch_bounds__(kBlock) m_apply_kernel(int n_T, const long long* __restrict__ toff,
                                                          const long long* __restrict__ moff,
                                                          const int* __restrict__ tfrac, const T* __restrict__ M,
-                                                         const T* __restrict__ x0, const T* __restrict__ x1,
-                                                         T* __restrict__ y0, T* __restrict__ y1) {
+                                                         const T* __restrict__ x, T* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const long long gw = gtid() >> 5, nw = gstride() >> 5;
   for (long long r = gw; r < n_T; r += nw) {
@@ -272,27 +281,34 @@ __global__ void __launch_bounds__(kBlock) m_apply_kernel(int n_T, int nf, const 
     const long long t0 = toff[f];
     const int t = (int)(toff[f + 1] - t0);
     const T* row = M + moff[f] + (r - t0) * t;
-    T a0 = (T)0, a1 = (T)0;
-    for (int b = lane; b < t; b += 32) {
-      const T m = __ldcs(row + b);
-      a0 = fma(m, __ldg(x0 + t0 + b), a0);
-      if (NR > 1) a1 = fma(m, __ldg(x1 + t0 + b), a1);
+    const T* xf = x + t0;
+    T acc[kMU];
+#pragma unroll
+    for (int u = 0; u < kMU; ++u) acc[u] = (T)0;
+    int b = lane;
+    for (; b + 32 * (kMU - 1) < t; b += 32 * kMU) {
+      T m[kMU];
+#pragma unroll
+      for (int u = 0; u < kMU; ++u) m[u] = __ldcs(row + b + 32 * u);
+#pragma unroll
+      for (int u = 0; u < kMU; ++u) acc[u] = fma(m[u], __ldg(xf + b + 32 * u), acc[u]);
     }
-    a0 = warp_sum_t(a0);
-    if (NR > 1) a1 = warp_sum_t(a1);
-    if (lane == 0) {
-      y0[r] = a0;
-      if (NR > 1) y1[r] = a1;
-    }
+    for (; b < t; b += 32) acc[0] = fma(__ldcs(row + b), __ldg(xf + b), acc[0]);
+    T a = acc[0];
+#pragma unroll
+    for (int u = 1; u < kMU; ++u) a += acc[u];
+    a = warp_sum_t(a);
+    if (lane == 0) y[r] = a;
   }
 }
 
 // Final sparse products in u space fused with the caller's step epilogue:
-// s = w o (G^u (w o x) - alpha (BT_T t + CT_T w1) + CT_T w2) = (S_hat x)_row.
+// s = w o (G^u (w o x) - alpha BT_T t + CT_T w2) = (S_hat x)_row, with
+// t = M C (w o x) and w2 = M (G^h t - alpha B (w o x)).
 template <int MODE, int NDOT, typename T>
 __global__ void __launch_bounds__(kBlock) schur_final_kernel(int n_u, DCsr Gu, DCsr BT_T, DCsr CT_T, double alpha,
                                                              const double* __restrict__ w, const T* __restrict__ tT,
-                                                             const T* __restrict__ wT, const T* __restrict__ w2T,
+                                                             const T* __restrict__ w2T,
                                                              StepArgs<T> a, const Scalars* sc, double* partials,
                                                              unsigned int* counter) {
   if (sc && load_done(sc)) return;
@@ -309,7 +325,7 @@ __global__ void __launch_bounds__(kBlock) schur_final_kernel(int n_u, DCsr Gu, D
     for (int p = BT_T.rowptr[i]; p < BT_T.rowptr[i + 1]; ++p) bt += (T)BT_T.val[p] * tT[BT_T.col[p]];
     for (int p = CT_T.rowptr[i]; p < CT_T.rowptr[i + 1]; ++p) {
       const int c = CT_T.col[p];
-      ct += (T)CT_T.val[p] * (w2T[c] - al * wT[c]);
+      ct += (T)CT_T.val[p] * w2T[c];
     }
     T s = gu - al * bt + ct;
     if (w) s *= (T)w[i];
@@ -405,7 +421,7 @@ __global__ void trace_restrict_kernel(int n_T, const int* tnode, const double* _
 
 int grid_of(long long work, int per_block = kBlock) {
   long long g = (work + per_block - 1) / per_block;
-  return (int)std::max(1LL, std::min<long long>(g, 152LL * 16));
+  return (int)std::max(1LL, std::min<long long>(g, 16LL * num_sms()));
 }
 
 }  // namespace
@@ -684,7 +700,6 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
   S->vT = B.take<double>(P.n_T);
   S->zT = B.take<double>(P.n_T);
   S->tT = B.take<double>(P.n_T);
-  S->wT = B.take<double>(P.n_T);
   S->gT = B.take<double>(P.n_T);
   S->w2T = B.take<double>(P.n_T);
   S->fa = B.take<double>(d->n_h);
@@ -697,7 +712,6 @@ size_t layout_schur(pp_ctx* c, SchurImpl* S, const pp_dfn* d, const TracePlan& P
     S->vT32 = B.take<float>(P.n_T);
     S->zT32 = B.take<float>(P.n_T);
     S->tT32 = B.take<float>(P.n_T);
-    S->wT32 = B.take<float>(P.n_T);
     S->gT32 = B.take<float>(P.n_T);
     S->w2T32 = B.take<float>(P.n_T);
   }
@@ -750,17 +764,11 @@ cudaError_t ainv_full(const SchurImpl* S, const double* v, double* y, cudaStream
 }
 
 template <typename T>
-cudaError_t m_apply(const SchurImpl* S, const T* M, const T* x0, const T* x1, T* y0, T* y1, cudaStream_t s) {
+cudaError_t m_apply(const SchurImpl* S, const T* M, const T* x, T* y, int* err, cudaStream_t s) {
+  (void)err;  // the direct-load product has no device waits
   const int g = grid_of((long long)S->n_T * 32);
-  if (x1)
-    m_apply_kernel<2, T><<<g, kBlock, 0, s>>>(S->n_T, S->n_f, S->toff, S->moff, S->tfrac, M, x0, x1, y0, y1);
-  else
-    m_apply_kernel<1, T><<<g, kBlock, 0, s>>>(S->n_T, S->n_f, S->toff, S->moff, S->tfrac, M, x0, nullptr, y0, nullptr);
+  m_apply_kernel<T><<<g, kBlock, 0, s>>>(S->n_T, S->toff, S->moff, S->tfrac, M, x, y);
   return cudaGetLastError();
-}
-
-cudaError_t m_apply(const SchurImpl* S, const double* x0, const double* x1, double* y0, double* y1, cudaStream_t s) {
-  return m_apply<double>(S, S->M, x0, x1, y0, y1, s);
 }
 
 // Trace-space scratch and M in the vector type T.
@@ -772,7 +780,6 @@ struct SchurBufs<double> {
   static double* v(const SchurImpl* S) { return S->vT; }
   static double* z(const SchurImpl* S) { return S->zT; }
   static double* t(const SchurImpl* S) { return S->tT; }
-  static double* w(const SchurImpl* S) { return S->wT; }
   static double* g(const SchurImpl* S) { return S->gT; }
   static double* w2(const SchurImpl* S) { return S->w2T; }
 };
@@ -782,7 +789,6 @@ struct SchurBufs<float> {
   static float* v(const SchurImpl* S) { return S->vT32; }
   static float* z(const SchurImpl* S) { return S->zT32; }
   static float* t(const SchurImpl* S) { return S->tT32; }
-  static float* w(const SchurImpl* S) { return S->wT32; }
   static float* g(const SchurImpl* S) { return S->gT32; }
   static float* w2(const SchurImpl* S) { return S->w2T32; }
 };
@@ -794,7 +800,7 @@ cudaError_t final_go(pp_ctx* c, const double* w, const StepParams& p, const Scal
   using B = SchurBufs<T>;
   StepArgs<T> a = make_args<T>(p);
   schur_final_kernel<MODE, NDOT, T><<<c->grid_vec, kBlock, 0, s>>>(S->n_u, S->Gu, S->BT_T, S->CT_T, S->alpha, w,
-                                                                   B::t(S), B::w(S), B::w2(S), a, skip, c->partials,
+                                                                   B::t(S), B::w2(S), a, skip, c->partials,
                                                                    counter);
   return cudaGetLastError();
 }
@@ -823,10 +829,14 @@ cudaError_t schur_step(pp_ctx* c, const double* w, const StepParams& p, const Sc
   using B = SchurBufs<T>;
   const T* x = static_cast<const T*>(p.x);
   trace_gather_kernel<T><<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->C_T, S->B_T, w, x, B::v(S), B::z(S));
-  cudaError_t e = m_apply<T>(S, B::M(S), B::v(S), B::z(S), B::t(S), B::w(S), s);  // [t, w] = A^{-1} [v, z]
+  int* err = &c->sc->dev_error;
+  cudaError_t e = m_apply<T>(S, B::M(S), B::v(S), B::t(S), err, s);  // t = A^{-1} C x
   if (e != cudaSuccess) return e;
-  trace_gh_kernel<T><<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->Gh_T, B::t(S), B::g(S));  // v = G^h t
-  e = m_apply<T>(S, B::M(S), B::g(S), nullptr, B::w2(S), nullptr, s);                        // w = A^{-1} v
+  // Algorithm 3 applies A^{-1} to B x and to G^h t and uses the results only
+  // in C^T (A^{-1} G^h t - alpha A^{-1} B x); by linearity that is one
+  // application, to g = G^h t - alpha B x
+  trace_gh_kernel<T><<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->Gh_T, B::t(S), B::z(S), (T)S->alpha, B::g(S));
+  e = m_apply<T>(S, B::M(S), B::g(S), B::w2(S), err, s);  // w2 = A^{-1} g
   if (e != cudaSuccess) return e;
   switch (p.mode) {
     case kSpmv: return final_ndot<kSpmv, T>(c, w, p, skip, counter, s);
@@ -966,6 +976,7 @@ extern "C" int schur_setup(pp_ctx** out, const pp_dfn* d, const pp_options* opt,
   c->nnz_pad = P.m_elems;
   c->grid_vec = (int)std::max(1LL, std::min<long long>(std::min(kMaxGrid, c->num_sms * 8),
                                                        (c->n_pad / 2 + kBlock - 1) / kBlock));
+  if (c->opt.max_blocks > 0) c->grid_vec = std::min(c->grid_vec, c->opt.max_blocks);
   c->grid_step = c->grid_vec;
   cudaError_t e = cudaMemsetAsync(c->vec_begin, 0, (char*)c->vec_end - (char*)c->vec_begin, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->sc, 0, sizeof(Scalars), s);
@@ -1031,7 +1042,7 @@ extern "C" int schur_setup(pp_ctx** out, const pp_dfn* d, const pp_options* opt,
   if (e == cudaSuccess && dsm > 48 * 1024)
     e = cudaFuncSetAttribute(schur_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
   if (e == cudaSuccess) {
-    schur_diag_kernel<<<std::min(d->n_u, 152 * 16), 128, dsm, s>>>(d->n_u, S->n_f, S->toff, S->moff, S->tfrac,
+    schur_diag_kernel<<<std::min(d->n_u, 16 * num_sms()), 128, dsm, s>>>(d->n_u, S->n_f, S->toff, S->moff, S->tfrac,
                                                                   S->CT_T, S->BT_T, S->Gh_T, S->Gu, S->M, S->alpha,
                                                                   S->ds, d_bad);
     e = cudaGetLastError();
@@ -1107,8 +1118,8 @@ extern "C" int schur_rhs(pp_ctx* c, const double* q, double* r, void* stream) {
   cudaError_t e = ainv_full(S, q, S->fa, s);
   if (e == cudaSuccess) {
     trace_restrict_kernel<<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->tnode, S->fa, S->tT);
-    trace_gh_kernel<double><<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->Gh_T, S->tT, S->gT);
-    e = m_apply(S, S->gT, nullptr, S->w2T, nullptr, s);
+    trace_gh_kernel<double><<<grid_of(S->n_T), kBlock, 0, s>>>(S->n_T, S->Gh_T, S->tT, nullptr, 0.0, S->gT);
+    e = m_apply<double>(S, S->M, S->gT, S->w2T, &c->sc->dev_error, s);
   }
   if (e == cudaSuccess) {
     csr_axpy_kernel<<<grid_of(S->n_u), kBlock, 0, s>>>(S->BT_T, S->tT, 0.0, nullptr, S->alpha, c->t1);

@@ -3,6 +3,8 @@
 // CSR inside the caller's workspace, in FP64 / FP32 / BF16.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace pp {
@@ -110,6 +112,71 @@ __global__ void dia_fill_kernel(int n, const int* __restrict__ rowptr, const int
   }
 }
 
+// DIA planning on the device (one thread per row): every column in range,
+// no repeated entry, the diagonal present, a(j, i) == a(i, j) exactly for
+// every off-diagonal entry, and the set of upper offsets j - i > 0 collected
+// in an open-addressing table of kDiaSlots slots (offset + 1; 0 = empty).
+// Of the errors found, the one of the smallest row (then the smallest code)
+// is kept: err = row << 8 | code, reduced by atomicMin.
+__device__ __forceinline__ void dia_plan_error(DiaPlanTable* t, int code, long long row) {
+  atomicMin(&t->err, ((unsigned long long)row << 8) | (unsigned long long)code);
+}
+
+__global__ void dia_plan_kernel(int n, long long nnz, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                const double* __restrict__ val, DiaPlanTable* t) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int b = rowptr[i], e = rowptr[i + 1];
+    if (e < b || (i == 0 && b != 0) || (i == n - 1 && (long long)e != nnz) || b < 0 || (long long)e > nnz) {
+      dia_plan_error(t, kDiaBadRowptr, i);
+      continue;
+    }
+    bool diag = false;
+    for (int p = b; p < e; ++p) {
+      const int j = col[p];
+      if (j < 0 || j >= n) {
+        dia_plan_error(t, kDiaBadCol, i);
+        break;
+      }
+      for (int q = b; q < p; ++q)
+        if (col[q] == j) dia_plan_error(t, kDiaRepeated, i);
+      if (j == i) {
+        diag = true;
+        continue;
+      }
+      // the mirror entry a(j, i) must exist with the same value
+      const int bj = rowptr[j], ej = rowptr[j + 1];
+      bool mirror = false;
+      if (bj >= 0 && ej >= bj && (long long)ej <= nnz)
+        for (int q = bj; q < ej; ++q)
+          if (col[q] == i) {
+            mirror = val[q] == val[p];
+            break;
+          }
+      if (!mirror) dia_plan_error(t, kDiaUnsymmetric, i);
+      if (j < i) continue;
+      const unsigned long long key = (unsigned long long)(j - i) + 1ull;
+      unsigned int h = (unsigned int)((key * 0x9E3779B97F4A7C15ull) >> 58);  // 64 slots
+      bool placed = false;
+      for (int probe = 0; probe < kDiaSlots && !placed; ++probe, h = (h + 1) & (kDiaSlots - 1)) {
+        const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&t->slot[h]);
+        if (cur == key) {
+          placed = true;
+        } else if (cur == 0ull) {
+          const unsigned long long old = atomicCAS(&t->slot[h], 0ull, key);
+          if (old == 0ull) {
+            atomicAdd(&t->count, 1);
+            placed = true;
+          } else if (old == key) {
+            placed = true;
+          }
+        }
+      }
+      if (!placed) dia_plan_error(t, kDiaTooMany, i);
+    }
+    if (!diag) dia_plan_error(t, kDiaNoDiagonal, i);
+  }
+}
+
 template <typename TV>
 __global__ void convert_values_kernel(long long m, const double* __restrict__ in, TV* __restrict__ out) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
@@ -119,7 +186,8 @@ __global__ void convert_values_kernel(long long m, const double* __restrict__ in
 int grid_for(long long m) {
   long long g = (m + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
-  if (g > 152 * 16) g = 152 * 16;
+  const long long cap = 16LL * num_sms();
+  if (g > cap) g = cap;
   return (int)g;
 }
 
@@ -170,6 +238,38 @@ cudaError_t dia_fill(const MatDesc& dst, const int* rowptr, const int* col, cons
   d.dpad = dst.dpad;
   dia_fill_kernel<<<grid_for(dst.n), kBlock, 0, s>>>(dst.n, rowptr, col, val, w, d, (double*)const_cast<void*>(dst.val));
   return cudaGetLastError();
+}
+
+namespace {
+// The planning table: a few hundred bytes, so it lives in a file-scope device
+// array rather than in a caller buffer (pp_workspace_size has none).  Its
+// device address is looked up once per device; planning holds g_plan_mu from
+// the clear to the read-back, so concurrent setups take turns.
+__device__ DiaPlanTable g_dia_plan_table;
+std::mutex g_plan_mu;
+DiaPlanTable* g_plan_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+cudaError_t dia_plan(int n, long long nnz, const int* rowptr, const int* col, const double* val, DiaPlanTable* out,
+                     cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  const int dev = current_device();
+  if (!g_plan_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_dia_plan_table);
+    if (e != cudaSuccess) return e;
+    g_plan_ptr[dev] = static_cast<DiaPlanTable*>(p);
+  }
+  DiaPlanTable* t = g_plan_ptr[dev];
+  cudaError_t e = cudaMemsetAsync(t, 0, sizeof(DiaPlanTable), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&t->err, 0xff, sizeof(t->err), s);
+  if (e == cudaSuccess) {
+    dia_plan_kernel<<<grid_for(n), kBlock, 0, s>>>(n, nnz, rowptr, col, val, t);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, t, sizeof(DiaPlanTable), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
 }
 
 cudaError_t sell_convert_values(long long m, const double* in, void* out, int out_prec, cudaStream_t s) {

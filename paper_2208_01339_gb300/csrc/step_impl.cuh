@@ -641,11 +641,14 @@ cudaError_t go_sell(const MatDesc& A, const StepParams& p, const Scalars* sc, do
   if (A.tma) {
     using S = TmaStage<TV, TX, VW, MODE>;
     auto kern = sell_step_tma_kernel<TV, TX, VW, MODE, NDOT>;
-    static bool attr_set = false;  // per instantiation; the attribute is per function
-    if (!attr_set) {
+    // the attribute belongs to the function on one device: set it once per
+    // instantiation and device
+    static bool attr_set[kMaxDevices] = {false};
+    const int dev = current_device();
+    if (!attr_set[dev]) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBlockBytes);
       if (e != cudaSuccess) return e;
-      attr_set = true;
+      attr_set[dev] = true;
     }
     kern<<<grid, kBlock, S::kBlockBytes, s>>>(A.n, A.nslices, A.slice_ptr, A.col, static_cast<const TV*>(A.val),
                                              make_args<TX>(p), sc, partials, cnt);

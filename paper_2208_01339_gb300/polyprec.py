@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
                 ("flexible", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("zero_guess", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("sell_variant", ctypes.c_int), ("lowrank", ctypes.c_int),
-                ("lowrank_steps", ctypes.c_int), ("poly", ctypes.c_int)]
+                ("lowrank_steps", ctypes.c_int), ("poly", ctypes.c_int), ("max_blocks", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -148,6 +148,7 @@ SIGNATURES = [
     ("pp_mlp_grad", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp]),
     ("pp_mlp_train_step", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _vp, _vp]),
     ("pp_mlp_destroy", ctypes.c_int, [_vp]),
+    ("pp_fp64_fma_rate", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
     ("polyprec_apply_csr_static", ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp]),
 ]
@@ -263,6 +264,15 @@ def apply_csr_static(rowptr, col, val, n: int, alpha: float, beta: float, xi: fl
                                          xi, int(k), _ptr(r), _ptr(z), _stream(stream))
     _check(rc)
     return z
+
+
+def fp64_fma_rate(reps: int = 5, device="cuda", stream=None) -> float:
+    """Measured FP64 FMA rate of the device in TFLOP/s (pp_fp64_fma_rate)."""
+    torch = _torch()
+    sink = torch.zeros(1, dtype=torch.float64, device=device)
+    tf = ctypes.c_double()
+    _check(lib().pp_fp64_fma_rate(_ptr(sink), int(reps), ctypes.byref(tf), _stream(stream)))
+    return tf.value
 
 
 FORMAT_NAME = {1: "csr", 2: "sell", 3: "dia"}

@@ -116,3 +116,32 @@ def test_null_arguments_rejected_without_gpu(lib):
     off = np.array([0, 2], dtype=np.int64)
     assert lib.pp_fracture_bands(1, ctypes.c_void_p(off.ctypes.data), None, None, None, None, None) == P.PP_EINVAL
     assert b"NULL" in lib.pp_last_error(None)
+
+
+def test_static_apply_argument_checks_without_gpu(lib):
+    """polyprec_apply_csr_static checks its arguments before any CUDA call:
+    too many rows, z overlapping r, and a negative degree."""
+    one = ctypes.c_void_p(256)
+    f = lib.polyprec_apply_csr_static
+    assert f(262145, 262145, one, one, one, 1.0, 2.0, 0.0, 3, one, ctypes.c_void_p(1 << 24), None) == P.PP_EINVAL
+    assert b"262144" in lib.pp_last_error(None)
+    r, z = ctypes.c_void_p(4096), ctypes.c_void_p(4096 + 8 * 99)  # z starts inside r[0:100]
+    assert f(100, 300, one, one, one, 1.0, 2.0, 0.0, 4, r, z, None) == P.PP_EINVAL
+    assert b"overlap" in lib.pp_last_error(None)
+    assert f(100, 300, one, one, one, 1.0, 2.0, 0.0, 4, r, r, None) == P.PP_EINVAL
+    assert f(100, 300, one, one, one, 1.0, 2.0, 0.0, -1, r, ctypes.c_void_p(1 << 24), None) == P.PP_EINVAL
+
+
+def test_max_blocks_option_checked(lib):
+    bad = P.make_options(max_blocks=-1)
+    csr = P.Csr(10, 10, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16))
+    nbytes = ctypes.c_size_t()
+    assert lib.pp_workspace_size(ctypes.byref(csr), ctypes.byref(bad), ctypes.byref(nbytes)) == P.PP_EINVAL
+    assert b"max_blocks" in lib.pp_last_error(None)
+
+
+def test_fma_rate_argument_checks_without_gpu(lib):
+    out = ctypes.c_double()
+    assert lib.pp_fp64_fma_rate(None, 3, ctypes.byref(out), None) == P.PP_EINVAL
+    assert lib.pp_fp64_fma_rate(ctypes.c_void_p(256), 0, ctypes.byref(out), None) == P.PP_EINVAL
+    assert lib.pp_fp64_fma_rate(ctypes.c_void_p(256), 3, None, None) == P.PP_EINVAL

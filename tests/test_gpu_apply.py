@@ -8,7 +8,7 @@ rounding order of each row sum and in FMA contraction).
 import numpy as np
 import pytest
 
-from helpers import oracle_apply, oracle_interval, rel, to_np
+from helpers import assert_close, oracle_apply, oracle_interval, rel, to_np
 from paper_2208_01339_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -66,7 +66,7 @@ def test_apply_matches_oracle(mat, layout, k):
     z = S.apply(torch.as_tensor(r, device="cuda"))
     torch.cuda.synchronize()
     ref = oracle_apply(A, r, alpha, beta, xi, k)
-    assert rel(to_np(z), ref) <= APPLY_TOL
+    assert_close(to_np(z), ref, APPLY_TOL)
 
 
 @pytest.mark.parametrize("layout", range(len(LAYOUTS)))
@@ -76,7 +76,7 @@ def test_apply_without_seed_scaling(layout):
                            **LAYOUTS[layout])
     r = I.rhs_normal(A.n, 1)
     z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
-    assert rel(z, oracle_apply(A, r, 0.5, 14.0, 0.0, 5, seed_scaling=False)) <= APPLY_TOL
+    assert_close(z, oracle_apply(A, r, 0.5, 14.0, 0.0, 5, seed_scaling=False), APPLY_TOL)
 
 
 @pytest.mark.parametrize("layout", range(len(LAYOUTS)))
@@ -93,7 +93,7 @@ def test_apply_wide_slices(layout, which):
     S = P.Solver.from_host(A, k=6, interval="given", alpha=0.05, beta=1.95, xi=1e-3, **LAYOUTS[layout])
     r = I.rhs_normal(A.n, 2)
     z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
-    assert rel(z, oracle_apply(A, r, 0.05, 1.95, 1e-3, 6)) <= APPLY_TOL
+    assert_close(z, oracle_apply(A, r, 0.05, 1.95, 1e-3, 6), APPLY_TOL)
 
 
 def test_apply_multiple_rhs():
@@ -102,7 +102,7 @@ def test_apply_multiple_rhs():
     R = np.stack([I.rhs_normal(A.n, s) for s in range(3)])
     Z = to_np(S.apply(torch.as_tensor(R, device="cuda")))
     for j in range(3):
-        assert rel(Z[j], oracle_apply(A, R[j], 0.1, 1.9, 1e-3, 6)) <= APPLY_TOL
+        assert_close(Z[j], oracle_apply(A, R[j], 0.1, 1.9, 1e-3, 6), APPLY_TOL)
 
 
 @pytest.mark.parametrize("layout", range(len(LAYOUTS)))
@@ -135,7 +135,7 @@ def test_operator_product(layout):
     S = P.Solver.from_host(A, k=2, **LAYOUTS[layout])
     x = I.rhs_normal(A.n, 3)
     y = to_np(S.operator(torch.as_tensor(x, device="cuda")))
-    assert rel(y, A.matvec(x)) <= 1e-13
+    assert_close(y, A.matvec(x), 1e-13)
 
 
 def test_ragged_sizes_and_tiny():
@@ -146,7 +146,7 @@ def test_ragged_sizes_and_tiny():
                                    seed_scaling=False, format=fmt)
             r = I.rhs_uniform(n, 2)
             z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
-            assert rel(z, oracle_apply(A, r, 1.0, float(n) + 1.0, 0.0, 3, seed_scaling=False)) <= APPLY_TOL
+            assert_close(z, oracle_apply(A, r, 1.0, float(n) + 1.0, 0.0, 3, seed_scaling=False), APPLY_TOL)
 
 
 def test_invalid_setup_reports_error():
@@ -184,7 +184,7 @@ def test_dia_diagonals_for_the_7_point_stencil():
                                beta=14.0 if not scaling else 1.95)
         info = S.info()
         assert info["format"] == 3 and info["ndiag"] == nd
-        assert rel(to_np(S.operator(torch.as_tensor(x, device="cuda"))), A.matvec(x)) <= 1e-13
+        assert_close(to_np(S.operator(torch.as_tensor(x, device="cuda"))), A.matvec(x), 1e-13)
 
 
 @pytest.mark.parametrize("N", [16, 17, 18, 20])
@@ -198,6 +198,44 @@ def test_dia_partner_paths(N, k):
     S = P.Solver.from_host(A, k=k, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="dia")
     r = I.rhs_normal(A.n, 8)
     z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
-    assert rel(z, oracle_apply(A, r, 0.05, 1.95, 1e-3, k)) <= APPLY_TOL
+    assert_close(z, oracle_apply(A, r, 0.05, 1.95, 1e-3, k), APPLY_TOL)
     x = I.rhs_normal(A.n, 9)
-    assert rel(to_np(S.operator(torch.as_tensor(x, device="cuda"))), A.matvec(x)) <= 1e-13
+    assert_close(to_np(S.operator(torch.as_tensor(x, device="cuda"))), A.matvec(x), 1e-13)
+
+
+def mixed_width_matrix(N=12, seed=9):
+    """7-point diffusion matrix with extra symmetric couplings on a few
+    scattered rows: their slices are 8-10 entries wide (wider than the TMA
+    staging buffer, so loaded directly) while every other slice is at most
+    7 wide (staged), and the staged/direct paths alternate along a warp's
+    slice sequence."""
+    A = I.diffusion3d(N, 1.5, seed=seed)
+    D = A.to_dense()
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(A.n, size=12, replace=False)
+    for i in rows:
+        for j in rng.choice(A.n, size=3, replace=False):
+            if j != i:
+                D[i, j] = D[j, i] = -0.05
+    np.fill_diagonal(D, 0.0)
+    np.fill_diagonal(D, np.abs(D).sum(axis=1) + 0.5)
+    return I.dense_to_csr(D)
+
+
+@pytest.mark.parametrize("C", [32, 64, 128])
+@pytest.mark.parametrize("sigma", [0, 256])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_tma_mixed_staged_and_direct_slices(C, sigma, prec):
+    A = mixed_width_matrix()
+    S = P.Solver.from_host(A, k=6, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="sell", sell_C=C,
+                           sell_sigma=sigma, sell_variant=2, apply_prec=prec)
+    r = I.rhs_normal(A.n, 3)
+    z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
+    if prec == "f64":
+        assert_close(z, oracle_apply(A, r, 0.05, 1.95, 1e-3, 6), APPLY_TOL)
+    else:
+        import oracle as O
+
+        vh, w = O.jacobi_scale(A)
+        ref = w * O.cheb_apply(A, 0.05, 1.95, 1e-3, 6, w * r, val=vh.astype(np.float32).astype(np.float64))
+        assert_close(z, ref, 2e-5)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import rel, to_np
+from helpers import assert_close, rel, to_np
 from paper_2208_01339_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -42,9 +42,9 @@ def test_autotune_picks_fastest_and_solves(prec):
     assert st["status"] == 0
     if prec == "f64":
         assert st["iterations"] == so["iterations"]
-        assert rel(to_np(x), xo) <= 1e-10
+        assert_close(to_np(x), xo, 1e-10)
     else:
-        assert rel(to_np(x), xo) <= 1e-7
+        assert_close(to_np(x), xo, 1e-7)
 
 
 def test_autotune_skips_layouts_that_do_not_fit():

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import rel
+from helpers import assert_close, rel
 from paper_2208_01339_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -72,7 +72,7 @@ def test_batch_f64_matches_oracle_per_column(problem, graphs, k, fmt):
             xo, so = ref[g]
             assert stv[g] == 0 and so["status"] == 0
             assert it[g] == so["iterations"], (i, r)
-            assert rel(Xi[:, r], xo) <= 1e-10
+            assert_close(Xi[:, r], xo, 1e-10)
             g += 1
     abx = S.intervals()
     for i, A in enumerate(mats):
@@ -101,7 +101,7 @@ def test_batch_per_column_intervals(problem, fmt):
         for r in range(Xi.shape[1]):
             xo, so = ref[g]
             assert it[g] == so["iterations"]
-            assert rel(Xi[:, r], xo) <= 1e-10
+            assert_close(Xi[:, r], xo, 1e-10)
             g += 1
 
 
@@ -117,7 +117,7 @@ def test_batch_f32_apply_converges(problem, fmt):
     g = 0
     for i, Xi in enumerate(xs):
         for r in range(Xi.shape[1]):
-            assert rel(Xi[:, r], ref[g][0]) <= 1e-7
+            assert_close(Xi[:, r], ref[g][0], 1e-7)
             assert it[g] <= 2 * ref[g][1]["iterations"] + 5
             g += 1
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import rel, to_np
+from helpers import assert_close, rel, to_np
 from paper_2208_01339_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -40,7 +40,7 @@ def test_fixed_iterations_match_oracle(m, fmt):
     x, st = S.solve(dev(b))
     xo, so = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), **opts)
     assert st["iterations"] == so["iterations"] == 11
-    assert rel(to_np(x), xo) <= 1e-10
+    assert_close(to_np(x), xo, 1e-10)
     assert st["dots"] == (3 + m) * 11
 
 
@@ -55,7 +55,7 @@ def test_converged_solve_and_graphs(m):
         x, st = S.solve(dev(b))
         assert st["status"] == 0
         assert abs(st["iterations"] - so["iterations"]) <= 1
-        assert rel(to_np(x), xo) <= 1e-10
+        assert_close(to_np(x), xo, 1e-10)
         res.append((to_np(x), st["iterations"]))
     assert res[0][1] == res[1][1] and np.array_equal(res[0][0], res[1][0])
 
@@ -70,7 +70,7 @@ def test_mixed_precision_fcg_m(prec):
         S = P.Solver.from_host(A, k=12, rtol=1e-8, format="dia", apply_prec=prec, flexible=m)
         x, st = S.solve(dev(b))
         assert st["status"] == 0
-        assert rel(to_np(x), xo) <= 1e-7
+        assert_close(to_np(x), xo, 1e-7)
         its[m] = st["iterations"]
     assert its[4] <= its[1] + 2
 
@@ -85,7 +85,7 @@ def test_schur_fcg_m_matches_oracle():
     u, st = S.solve(dev(r))
     uo, so = ref.pcg(ref.diag(), r, v0=I.lanczos_start(net.n_u, 0), **opts)
     assert st["iterations"] == so["iterations"] == 9
-    assert rel(to_np(u), uo) <= 1e-10
+    assert_close(to_np(u), uo, 1e-10)
 
 
 def test_flexible_out_of_range_rejected():

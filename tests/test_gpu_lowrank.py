@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import rel, to_np
+from helpers import assert_close, rel, to_np
 from paper_2208_01339_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -66,11 +66,11 @@ def test_apply_with_caller_vectors(lay, p):
     r = I.rhs_normal(A.n, 3)
     z = to_np(S.apply(dev(r)))
     zo = w * O.lowrank_apply(Ah, 0.02, 1.9, 1e-3, 6, U / w[:, None], w * r)
-    assert rel(z, zo) <= 1e-12
+    assert_close(z, zo, 1e-12)
     # p = 0 removes the correction
     S.set_lowrank(torch.empty(0, dtype=torch.float64, device="cuda"))
     z0 = to_np(S.apply(dev(r)))
-    assert rel(z0, w * O.cheb_apply(Ah, 0.02, 1.9, 1e-3, 6, w * r)) <= 1e-12
+    assert_close(z0, w * O.cheb_apply(Ah, 0.02, 1.9, 1e-3, 6, w * r), 1e-12)
 
 
 def test_apply_mixed_precision_with_caller_vectors():
@@ -84,7 +84,7 @@ def test_apply_mixed_precision_with_caller_vectors():
     r = I.rhs_normal(A.n, 3)
     z = to_np(S.apply(dev(r)))
     zo = w * O.lowrank_apply(Ah, 0.02, 1.9, 1e-3, 6, U / w[:, None], w * r)
-    assert rel(z, zo) <= 2e-5
+    assert_close(z, zo, 2e-5)
 
 
 @pytest.mark.parametrize("fmt", ["csr", "sell"])
@@ -111,7 +111,7 @@ def test_ritz_vectors_and_interval(fmt):
     r = I.rhs_normal(A.n, 5)
     z = to_np(S.apply(dev(r)))
     zo = w * O.lowrank_apply(Ah, lo2, hi, 1e-3, k, V, w * r)
-    assert rel(z, zo) <= 1e-8
+    assert_close(z, zo, 1e-8)
 
 
 @pytest.mark.parametrize("p,flexible,graphs", [(1, 0, 0), (4, 0, 1), (2, 1, 0)])
@@ -124,7 +124,7 @@ def test_pcg_fixed_iterations(p, flexible, graphs):
     xo, so = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), **opts)
     assert st["status"] == P.PP_MAXIT and so["status"] == 1
     assert st["iterations"] == so["iterations"] == 6
-    assert rel(to_np(x), xo) <= 1e-9
+    assert_close(to_np(x), xo, 1e-9)
     assert st["dots"] == (3 + p) * 6  # Table 4 convention: (3 + p) per iteration
     assert st["mvp"] == 5 * 6
 
@@ -138,8 +138,8 @@ def test_pcg_converged_matches_oracle_and_dense():
     xo, so = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), **opts)
     assert st["status"] == 0 and so["status"] == 0
     assert abs(st["iterations"] - so["iterations"]) <= 1
-    assert rel(to_np(x), xo) <= 1e-10
-    assert rel(to_np(x), np.linalg.solve(A.to_dense(), b)) <= 1e-9
+    assert_close(to_np(x), xo, 1e-10)
+    assert_close(to_np(x), np.linalg.solve(A.to_dense(), b), 1e-9)
     assert st["dots"] == 6 * st["iterations"] and so["dots"] == 6 * so["iterations"]
 
 
@@ -183,5 +183,5 @@ def test_schur_lowrank_pcg_matches_oracle():
     uo, so = ref.pcg(ref.diag(), r, v0=I.lanczos_start(net.n_u, 0), **opts)
     assert st["iterations"] == so["iterations"] == 8
     assert st["alpha_hat"] == pytest.approx(so["alpha_hat"], rel=1e-9)
-    assert rel(to_np(u), uo) <= 1e-9
+    assert_close(to_np(u), uo, 1e-9)
     assert st["dots"] == 4 * 8

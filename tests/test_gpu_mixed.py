@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import rel, to_np
+from helpers import assert_close, rel, to_np
 from paper_2208_01339_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -64,22 +64,26 @@ def test_mixed_apply_matches_rounded_oracle(prec, C, var, k):
     r = I.rhs_normal(A.n, 3)
     z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
     ref = oracle_apply_rounded(A, r, alpha, beta, xi, k, prec)
-    assert rel(z, ref) <= 2e-5
+    assert_close(z, ref, 2e-5)
     exact = oracle_apply_exact(A, r, alpha, beta, xi, k)
     if prec == "f32":
-        assert rel(z, exact) <= 1e-4
+        assert_close(z, exact, 1e-4)
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("k", [0, 1, 2, 7])
 @pytest.mark.parametrize("N", [16, 17, 18])
-def test_mixed_dia_apply(prec, k, N):
-    """4 rows per thread: offsets N, N^2 multiples of 4 (16), not (17, 18)."""
+@pytest.mark.parametrize("variant", [1, 2])
+def test_mixed_dia_apply(prec, k, N, variant):
+    """Direct loads (variant 1; offsets N, N^2 multiples of the rows per
+    thread or not) and TMA-staged tiles (variant 2; tile ends, ranges clipped
+    at both ends of the vectors, unaligned shifted starts)."""
     A = I.diffusion3d(N, 2.0, seed=1)
-    S = P.Solver.from_host(A, k=k, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="dia", apply_prec=prec)
+    S = P.Solver.from_host(A, k=k, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="dia", apply_prec=prec,
+                           sell_variant=variant)
     r = I.rhs_normal(A.n, 3)
     z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
-    assert rel(z, oracle_apply_rounded(A, r, 0.05, 1.95, 1e-3, k, prec)) <= 2e-5
+    assert_close(z, oracle_apply_rounded(A, r, 0.05, 1.95, 1e-3, k, prec), 2e-5)
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
@@ -88,7 +92,7 @@ def test_mixed_csr_apply(prec):
     S = P.Solver.from_host(A, k=6, interval="given", alpha=0.1, beta=1.9, xi=1e-3, format="csr", apply_prec=prec)
     r = I.rhs_normal(A.n, 1)
     z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
-    assert rel(z, oracle_apply_rounded(A, r, 0.1, 1.9, 1e-3, 6, prec)) <= 2e-5
+    assert_close(z, oracle_apply_rounded(A, r, 0.1, 1.9, 1e-3, 6, prec), 2e-5)
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
@@ -103,8 +107,8 @@ def test_flexible_mixed_solve_reaches_rtol(prec):
     assert sm["rel_res"] <= 1e-10
     xo, so = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), k=16, rtol=1e-12)
     # both GPU solutions are within the accuracy their residual allows
-    assert rel(to_np(x64), xo) <= 1e-7
-    assert rel(to_np(xm), xo) <= 1e-7
+    assert_close(to_np(x64), xo, 1e-7)
+    assert_close(to_np(xm), xo, 1e-7)
     # lower-precision preconditioner: a few more iterations at most
     assert sm["iterations"] <= 2 * s64["iterations"] + 5
 

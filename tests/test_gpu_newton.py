@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import oracle_apply, rel, to_np
+from helpers import assert_close, oracle_apply, rel, to_np
 from paper_2208_01339_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -45,9 +45,9 @@ def test_newton_apply_matches_oracle(nlev, fmt):
     S = P.Solver.from_host(A, k=k, interval="given", alpha=0.05, beta=1.95, xi=1e-3, poly="newton", format=fmt)
     r = I.rhs_normal(A.n, 4)
     z = to_np(S.apply(dev(r)))
-    assert rel(z, oracle_newton(A, r, 0.05, 1.95, 1e-3, nlev)) <= 1e-12
+    assert_close(z, oracle_newton(A, r, 0.05, 1.95, 1e-3, nlev), 1e-12)
     if nlev <= 5:
-        assert rel(z, oracle_apply(A, r, 0.05, 1.95, 1e-3, k)) <= 1e-10
+        assert_close(z, oracle_apply(A, r, 0.05, 1.95, 1e-3, k), 1e-10)
 
 
 def test_newton_pcg_matches_chebyshev_pcg():
@@ -57,12 +57,12 @@ def test_newton_pcg_matches_chebyshev_pcg():
     x, st = S.solve(dev(b))
     xo, so = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), k=7, rtol=0.0, maxit=6)
     assert st["iterations"] == 6
-    assert rel(to_np(x), xo) <= 1e-9
+    assert_close(to_np(x), xo, 1e-9)
     S2 = P.Solver.from_host(A, k=15, poly="newton", rtol=1e-10, use_graphs=1, check_every=4)
     x2, st2 = S2.solve(dev(b))
     xo2, so2 = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), k=15, rtol=1e-10)
     assert st2["status"] == 0 and abs(st2["iterations"] - so2["iterations"]) <= 1
-    assert rel(to_np(x2), xo2) <= 1e-9
+    assert_close(to_np(x2), xo2, 1e-9)
     assert st2["mvp"] == 16 * st2["iterations"]
 
 
@@ -75,7 +75,7 @@ def test_newton_on_schur():
     u, st = S.solve(dev(r))
     uo, so = ref.pcg(ref.diag(), r, v0=I.lanczos_start(net.n_u, 0), k=3, lanczos_steps=10, xi=1e-3, maxit=5, rtol=0.0)
     assert st["iterations"] == 5
-    assert rel(to_np(u), uo) <= 1e-9
+    assert_close(to_np(u), uo, 1e-9)
 
 
 def test_newton_rejects_bad_degree_and_mixed():

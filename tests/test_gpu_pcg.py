@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import rel, to_np
+from helpers import assert_close, rel, to_np
 from paper_2208_01339_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -55,7 +55,7 @@ def test_poisson32_k20_matches_oracle(fmt):
     assert sg["iterations"] == so["iterations"]
     assert sg["alpha_hat"] == pytest.approx(so["alpha_hat"], rel=1e-9)
     assert sg["beta_hat"] == pytest.approx(so["beta_hat"], rel=1e-9)
-    assert rel(xg, xo) <= 1e-10
+    assert_close(xg, xo, 1e-10)
     assert sg["mvp"] == sg["iterations"] * 21 and sg["dots"] == 3 * sg["iterations"]
     assert np.linalg.norm(b - A.matvec(xg)) / np.linalg.norm(b) <= 1e-7
 
@@ -65,7 +65,7 @@ def test_tight_solve_matches_dense():
     b = I.rhs_normal(A.n, 2)
     xg, sg, _ = gpu_solve(A, b, k=10, rtol=1e-13, lanczos_steps=20)
     assert sg["status"] == 0
-    assert rel(xg, np.linalg.solve(A.to_dense(), b)) <= 1e-10
+    assert_close(xg, np.linalg.solve(A.to_dense(), b), 1e-10)
 
 
 @pytest.mark.parametrize("fmt,C,sigma,var", [("csr", 0, 0, 0), ("sell", 32, 0, 1), ("sell", 64, 0, 1),
@@ -79,7 +79,7 @@ def test_fixed_iterations_iterates(fmt, C, sigma, var):
     xo, so = oracle_solve(A, b, **opts)
     assert sg["status"] == P.PP_MAXIT and so["status"] == 1
     assert sg["iterations"] == 3
-    assert rel(xg, xo) <= 1e-11
+    assert_close(xg, xo, 1e-11)
 
 
 def test_results_independent_of_check_interval_and_graphs():
@@ -114,7 +114,7 @@ def test_nonzero_initial_guess():
     xg, sg, _ = gpu_solve(A, b, x0=x0, k=6, rtol=1e-10, zero_guess=0)
     xo, so = oracle_solve(A, b, x0=x0, k=6, rtol=1e-10)
     assert sg["status"] == 0 and sg["iterations"] == so["iterations"]
-    assert rel(xg, xo) <= 1e-10
+    assert_close(xg, xo, 1e-10)
     assert sg["mvp"] == sg["iterations"] * 7 + 1
 
 
@@ -126,8 +126,8 @@ def test_flexible_cg():
     xo, so = oracle_solve(A, b, k=8, rtol=1e-10, flexible=True)
     assert s2["status"] == 0 and abs(s1["iterations"] - s2["iterations"]) <= 1
     assert s2["iterations"] == so["iterations"]
-    assert rel(x2, xo) <= 1e-10
-    assert rel(x1, x2) <= 1e-8
+    assert_close(x2, xo, 1e-10)
+    assert_close(x1, x2, 1e-8)
 
 
 def test_zero_rhs_and_degree_zero():
@@ -188,9 +188,9 @@ def test_full_size_192_apply_and_iterations():
     info = S.info()
     z = to_np(S.apply(torch.as_tensor(b, device="cuda")))
     ref = oracle_apply(A, b, info["alpha_hat"], info["beta_hat"], info["xi"], 20)
-    assert rel(z, ref) <= 1e-12
+    assert_close(z, ref, 1e-12)
     x, st = S.solve(torch.as_tensor(b, device="cuda"), allow=(0, 1))
     xo, so = O.pcg_csr(A, b, v0=I.lanczos_start(A.n, 0), k=20, lanczos_steps=10, rtol=0.0, maxit=3)
     assert so["alpha_hat"] == pytest.approx(info["alpha_hat"], rel=1e-9)
     assert st["iterations"] == 3
-    assert rel(to_np(x), xo) <= 1e-11
+    assert_close(to_np(x), xo, 1e-11)

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import rel, to_np
+from helpers import assert_close, rel, to_np
 from paper_2208_01339_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -74,8 +74,8 @@ def test_ainv(pair):
     S = P.SchurSolver(net, general=True, k=4)
     v = I.rhs_normal(net.n_h, 3)
     y = to_np(S.ainv(dev(v)))
-    assert rel(y, ref.ainv(v)) <= TOL
-    assert rel(net.A.matvec(y), v) <= TOL
+    assert_close(y, ref.ainv(v), TOL)
+    assert_close(net.A.matvec(y), v, TOL)
     info = S.info()
     assert info["band_max"] > 0 and info["band_elems"] > 0 and info["t_factor_ms"] > 0 and info["t_trace_ms"] > 0
 
@@ -85,20 +85,20 @@ def test_schur_apply_and_diag(pair):
     S = P.SchurSolver(net, general=True, k=4)
     for seed in (1, 2):
         r = I.rhs_normal(net.n_u, seed)
-        assert rel(to_np(S.schur_apply(dev(r))), ref.apply(r)) <= TOL
-    assert rel(to_np(S.diag()), ref.diag()) <= TOL
+        assert_close(to_np(S.schur_apply(dev(r))), ref.apply(r), TOL)
+    assert_close(to_np(S.diag()), ref.diag(), TOL)
 
 
 def test_rhs_and_recovery(pair):
     net, ref = pair
     S = P.SchurSolver(net, general=True, k=4)
     r = to_np(S.rhs(dev(net.q)))
-    assert rel(r, ref.rhs(net.q)) <= TOL
+    assert_close(r, ref.rhs(net.q), TOL)
     u = I.rhs_normal(net.n_u, 4)
     h, p = S.recover(dev(net.q), dev(u))
     ho, po = ref.recover(net.q, u)
-    assert rel(to_np(h), ho) <= TOL
-    assert rel(to_np(p), po) <= TOL
+    assert_close(to_np(h), ho, TOL)
+    assert_close(to_np(p), po, TOL)
 
 
 @pytest.mark.parametrize("k", [0, 5])
@@ -117,10 +117,10 @@ def test_pcg_on_scaled_schur(pair, k):
     d_it = abs(st["iterations"] - so["iterations"])
     if so["iterations"] <= 100:
         assert d_it <= 1
-        assert rel(to_np(x), xo) <= (1e-9 if d_it == 0 else 1e-7)
+        assert_close(to_np(x), xo, (1e-9 if d_it == 0 else 1e-7))
     else:
         assert d_it <= 0.03 * so["iterations"]
-        assert rel(to_np(x), xo) <= 1e-7
+        assert_close(to_np(x), xo, 1e-7)
 
 
 def test_factor_path_equals_closed_form_on_rectangles():
@@ -128,16 +128,16 @@ def test_factor_path_equals_closed_form_on_rectangles():
     G = P.SchurSolver(net, general=True, k=5, lanczos_steps=10)
     R = P.SchurSolver(net, general=False, k=5, lanczos_steps=10)
     r = I.rhs_normal(net.n_u, 7)
-    assert rel(to_np(G.schur_apply(dev(r))), to_np(R.schur_apply(dev(r)))) <= 1e-12
-    assert rel(to_np(G.diag()), to_np(R.diag())) <= 1e-12
+    assert_close(to_np(G.schur_apply(dev(r))), to_np(R.schur_apply(dev(r))), 1e-12)
+    assert_close(to_np(G.diag()), to_np(R.diag()), 1e-12)
     v = I.rhs_normal(net.n_h, 8)
-    assert rel(to_np(G.ainv(dev(v))), to_np(R.ainv(dev(v)))) <= 1e-12
+    assert_close(to_np(G.ainv(dev(v))), to_np(R.ainv(dev(v))), 1e-12)
     rhs = to_np(R.rhs(dev(net.q)))
-    assert rel(to_np(G.rhs(dev(net.q))), rhs) <= 1e-12
+    assert_close(to_np(G.rhs(dev(net.q))), rhs, 1e-12)
     xg, sg = G.solve(dev(rhs))
     xr, sr = R.solve(dev(rhs))
     assert sg["iterations"] == sr["iterations"]
-    assert rel(to_np(xg), to_np(xr)) <= 1e-10
+    assert_close(to_np(xg), to_np(xr), 1e-10)
     # natural numbering of a rectangle already has the narrowest band it can get
     assert R.info()["band_max"] == 0
     assert G.info()["band_max"] <= int(np.maximum(net.nx, net.ny).max())
@@ -165,7 +165,7 @@ def test_fp32_preconditioner_on_general_blocks():
     x32, s32 = S32.solve(dev(r))
     assert s64["status"] == 0 and s32["status"] == 0
     assert abs(s32["iterations"] - s64["iterations"]) <= 2
-    assert rel(ref.apply(to_np(x32)), r) <= 1e-7
+    assert_close(ref.apply(to_np(x32)), r, 1e-7)
 
 
 def _with_block(net, f, fn):
