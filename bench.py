@@ -51,13 +51,16 @@ WORKLOADS = {
     "dfn200": dict(dfn=True, seed=2, k=3, lanczos=30, prec="f64"),
     # p_k(S_hat) with the FP32 copy of the trace blocks, outer FP64 FCG(1)
     "dfn200_f32": dict(dfn=True, seed=2, k=15, lanczos=30, prec="f32", flexible=1),
+    # its first 40 fractures with the closed-form blocks: a small case of the S_u kernels for profiler captures
+    "dfn40": dict(dfn=True, seed=2, n_f=40, k=3, lanczos=30, prec="f64"),
     # the same network with general fracture blocks (P1 stiffness on jittered triangulations,
     # lognormal coefficients): A^{-1} from banded Cholesky factors built on the GPU
     "dfn200_p1": dict(dfn=True, seed=2, k=3, lanczos=30, prec="f64", general="p1"),
     # its first 40 fractures (0.4M nodes): a small case of the same kernels for profiler captures
     "dfn40_p1": dict(dfn=True, seed=2, n_f=40, k=3, lanczos=30, prec="f64", general="p1"),
     # per-instance symmetric DIA in the batch (the instances are 7-point stencils)
-    "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32", fmt="dia"),
+    # layout chosen by pp_batch_autotune (per-instance DIA or the global SELL-32 slice list)
+    "batched64": dict(batch=True, seed=4, count=64, k=20, lanczos=10, prec="f32", fmt="auto"),
 }
 METRIC = "PCG time-to-rtol-1e-8 (s) and polyprec_apply HBM GB/s vs plain FP64, 1 GB300"
 VAL_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
@@ -124,10 +127,18 @@ def fp64_peak_tflops() -> float:
     return 152 * 4 * 2.07e9 / 1e12
 
 
-def source_sha() -> str:
+# the sources of each captured kernel family (traffic is reported only while they are unchanged)
+KERNEL_SOURCES = {
+    "dia": ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_dia.cuh", "step_dia.cu"),
+    "dia_tma": ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_dia.cuh", "step_dia_tma.cu"),
+    "sell": ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_f64.cu", "step_lp.cu"),
+}
+
+
+def source_sha(files=KERNEL_SOURCES["dia"]) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2208_01339_gb300", "csrc")
-    for f in ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_f64.cu", "step_lp.cu", "step_dia.cu"):
+    for f in files:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -152,7 +163,9 @@ def traffic_from_profile(workload: str, k: int, prec: str, layout: str):
     with open(p) as fh:
         j = json.load(fh)
     e = j.get(f"{workload}/k{k}/{prec}")
-    if not e or e.get("source_sha") != source_sha() or e.get("layout") != layout:
+    if not e or e.get("layout") != layout:
+        return None
+    if e.get("source_sha") != source_sha(KERNEL_SOURCES[e.get("family", "dia")]):
         return None
     return {"bytes": e.get("dram_bytes_per_launch"), "launch": e.get("kernel"),
             "algorithmic_bytes_same_launch": e.get("algorithmic_bytes_same_launch"), "from": e.get("captured_on")}
@@ -338,35 +351,62 @@ def run_dfn_sweep(args, w, net, dopts, dev):
         S.close()
 
 
+def batch_step_bytes(specs, fmt: str, prec: str) -> float:
+    """Algorithmic bytes of one batched degree step over every column: each
+    instance's matrix streamed once for all its right-hand sides (DIA: 3
+    stored diagonals of n values; SELL: value + int32 index per nonzero),
+    and per column the vectors x, x_old, r read and y written (the later
+    steps' 4 passes)."""
+    sv, sx = VAL_BYTES[prec], VEC_BYTES[prec]
+    tot = 0.0
+    for sp in specs:
+        n = sp.N ** 3
+        nnz = 7 * n - 6 * sp.N ** 2
+        tot += (3 * n * sv if fmt == "dia" else nnz * (sv + 4)) + 4 * n * sp.nrhs * sx
+    return tot
+
+
 def run_batch(args, w, specs, k, dev, world, rank):
     """Config-5 shape: many uneven instances with several RHS each, solved by
-    the batched solver (FP32 p_k, FP64 flexible CG, CUDA graphs) and, for
-    comparison, one column at a time by the plain FP64 single-instance solver."""
+    the batched solver (FP32 p_k, FP64 flexible CG, CUDA graphs) in the
+    layout pp_batch_autotune picks and, for comparison, one column at a
+    time by the plain FP64 single-instance solver.  With N ranks the
+    instances are dealt to ranks by work (heaviest first, least-loaded
+    rank) and each rank solves its share; no data crosses ranks."""
     import torch
 
     from paper_2208_01339_gb300 import inputs as I
+    from paper_2208_01339_gb300 import learn as Lrn
     from paper_2208_01339_gb300 import polyprec as P
+    from paper_2208_01339_gb300 import replicas
 
+    all_specs = specs
+    mine = replicas.shard_balanced([s.N ** 3 * s.nrhs for s in all_specs], rank, world)
+    specs = [all_specs[i] for i in mine]
     mats = [I.batch_instance(s) for s in specs]
     rhs = [I.batch_rhs(s) for s in specs]
-    S = P.BatchSolver(mats, [s.nrhs for s in specs], device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8,
-                      format=w.get("fmt", "auto"),
-                      apply_prec=w["prec"], flexible=1, use_graphs=1, check_every=10, maxit=5000)
+    nrhs = [s.nrhs for s in specs]
+    common = dict(k=k, lanczos_steps=w["lanczos"], rtol=1e-8, apply_prec=w["prec"], flexible=1, use_graphs=1,
+                  check_every=10, maxit=5000)
+    fmt, tune = w.get("fmt", "auto"), None
+    if fmt == "auto":
+        fmt, table = P.batch_autotune(mats, nrhs, device=dev, **common)
+        tune = [[t["format"], round(t["us_per_step"], 2)] for t in table if t["status"] == 0]
+    S = P.BatchSolver(mats, nrhs, device=dev, format=fmt, **common)
     bt = S.pack(rhs)
+    abx0 = S.intervals()
+    cols = np.cumsum([0] + nrhs)
+    base = np.array([abx0[cols[i], :2] for i in range(len(specs))])
     mlp_used = 0
-    from paper_2208_01339_gb300 import learn as Lrn
-
     if os.path.exists(Lrn.WEIGHTS):
         model = Lrn.Model.load()
-        abx0 = S.intervals()
-        cols = np.cumsum([0] + [s.nrhs for s in specs])
-        base = np.array([abx0[cols[i], :2] for i in range(len(specs))])
         ab, used = Lrn.predicted_intervals(model, S.features(), base, device=dev)
-        S.intervals(np.concatenate([np.repeat(ab[i:i + 1], specs[i].nrhs, axis=0) for i in range(len(specs))]))
+        abx_mlp = np.concatenate([np.repeat(ab[i:i + 1], nrhs[i], axis=0) for i in range(len(specs))])
+        S.intervals(abx_mlp)
         mlp_used = int(used.sum())
     for _ in range(max(3, args.warmup)):
         S.solve(bt)
-    torch.cuda.synchronize(dev)
+    replicas.barrier(dev)
     stream = torch.cuda.current_stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -375,16 +415,33 @@ def run_batch(args, w, specs, k, dev, world, rank):
         x, it, stv, st = S.solve(bt)
         stats.append(st)
     ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1) / args.steps
+    replicas.barrier(dev)
+    ms = replicas.max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev)
     xs = S.unpack(x)
+    it_mlp = it.copy()
+    # the same batch with the Lanczos interval and the 10/kappa rule, and with
+    # the most frequent sweep label as one constant setting (iterations only)
+    arms = {}
+    for name, abx in (("fallback", abx0),
+                      ("fixed", np.column_stack([abx0[:, 0] * Lrn.FIXED_BEST[0], abx0[:, 1] * Lrn.FIXED_BEST[1],
+                                                 np.full(len(abx0), Lrn.FIXED_BEST[2])]))):
+        S.intervals(abx)
+        _, ita, sta, _ = S.solve(bt)
+        arms[name] = {"iterations_mean": float(ita.mean()), "iterations_max": int(ita.max()),
+                      "converged": int((sta == 0).sum())}
+    arms["mlp" if mlp_used else "mlp (not trained)"] = {"iterations_mean": float(it_mlp.mean()),
+                                                       "iterations_max": int(it_mlp.max())}
+    step_us = S.time_step(reps=5)
+    bytes_step = batch_step_bytes(specs, fmt, w["prec"])
+    peak, peak_src = measured_peak()
+    S.close()
+    del S
     # plain FP64 one column at a time (same k, Lanczos interval per instance)
     t_seq = 0.0
     err = 0.0
     its64 = []
     for i, (A, Bm) in enumerate(zip(mats, rhs)):
-        S64 = P.Solver.from_host(A, device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8, seed=i,
-                                 format=w.get("fmt", "auto"))
+        S64 = P.Solver.from_host(A, device=dev, k=k, lanczos_steps=w["lanczos"], rtol=1e-8, seed=i, format="dia")
         for r in range(Bm.shape[1]):
             b = torch.as_tensor(np.ascontiguousarray(Bm[:, r]), device=dev)
             S64.solve(b)  # warm
@@ -400,20 +457,31 @@ def run_batch(args, w, specs, k, dev, world, rank):
             err = max(err, float(np.linalg.norm(xs[i][:, r] - xr) / np.linalg.norm(xr)))
         S64.close()
         del S64
-    rows = sum(s.N ** 3 for s in specs)
+    t_seq = replicas.max_over_ranks(t_seq, dev)
+    err = replicas.max_over_ranks(err, dev)
+    rows = sum(s.N ** 3 for s in all_specs)
     if rank == 0:
+        ach = bytes_step / (step_us * 1e-6) / 1e9
         out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
-               "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+               "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "strong",
                "vs_baseline": None, "dtype": w["prec"], "data": "synthetic",
-               "config": {"workload": args.workload, "instances": len(specs), "rows": rows,
-                          "columns": int(sum(s.nrhs for s in specs)), "k": k, "apply": w["prec"],
+               "config": {"workload": args.workload, "instances": len(all_specs), "rows": rows,
+                          "columns": int(sum(s.nrhs for s in all_specs)), "k": k, "apply": w["prec"],
                           "outer": "f64 flexible CG", "graphs": 1, "interval": f"mlp ({mlp_used} instances)"
-                          if mlp_used else "lanczos", "layout": w.get("fmt", "auto"),
-                          "sequential_baseline": "each column alone, plain FP64 PCG, same layout, Lanczos interval"},
+                          if mlp_used else "lanczos", "layout": fmt,
+                          "autotune": ("pp_batch_autotune [format(2 SELL-32, 3 DIA), us/step] " + json.dumps(tune))
+                          if tune else "off",
+                          "ranks": f"{world} (instances dealt by work, heaviest first)",
+                          "sequential_baseline": "each column alone, plain FP64 PCG, DIA, Lanczos interval"},
                "iterations_max": int(max(stats[-1]["iterations"], 0)),
                "sequential_f64_s": t_seq, "speedup_vs_sequential_f64": t_seq / (ms / 1e3),
                "max_rel_diff_vs_f64": err, "iterations_f64_max": int(max(its64)),
-               "setup_ms": S.info_setup_ms if hasattr(S, "info_setup_ms") else None,
+               "interval_arms": arms,
+               "roofline": {"bound": "hbm", "kernel": f"b_cheb_kernel ({w['prec']}, {fmt}), one degree step over "
+                                                      f"every column (rank 0's share)",
+                            "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                            "traffic": None, "peak_source": peak_src, "avg_launch_us": round(step_us, 2),
+                            "algorithmic_bytes_per_launch": int(bytes_step)},
                "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
         print(json.dumps(out), flush=True)
 
@@ -584,7 +652,7 @@ def main():
         net = A
         dopts = dict(lanczos_steps=w["lanczos"], rtol=1e-8, check_every=args.check_every or 8,
                      use_graphs=max(args.graphs, 0), apply_prec=w["prec"], flexible=w.get("flexible", 0),
-                     maxit=5000, lowrank=args.lowrank, poly=args.poly)
+                     maxit=5000, lowrank=args.lowrank, poly=args.poly, sell_variant=args.sell_variant)
         dopts["general"] = True if args.general else None
         if args.k_sweep:
             return run_dfn_sweep(args, w, net, dopts, dev)
@@ -661,7 +729,7 @@ def main():
 
     it = [s["iterations"] for s in stats]
     fmt_name = {1: "CSR", 2: "SELL", 3: "DIA"}[info["format"]]
-    layout = layout_name(info, variant)
+    layout = layout_name(info, variant, w["prec"])
     fp64_peak = None
     if w["prec"] == "f64" or not args.no_variants:
         fp64_peak = P.fp64_fma_rate(reps=5)
@@ -723,10 +791,12 @@ def main():
         dist.destroy_process_group()
 
 
-def layout_name(info, variant) -> str:
+def layout_name(info, variant, prec="f64") -> str:
     if info["format"] == 2:
         return f"SELL C={info['sell_C']} sigma={info['sell_sigma']} {'direct' if variant == 1 else 'tma'}"
-    return f"DIA ndiag={info['ndiag']}" if info["format"] == 3 else "CSR"
+    if info["format"] == 3:
+        return f"DIA ndiag={info['ndiag']}" + (" tma" if prec != "f64" and variant == 2 else "")
+    return "CSR"
 
 
 def solution_error(xg, xo, it_gpu, it_oracle):
@@ -751,9 +821,10 @@ def step_roofline(info, stats, A, k, prec, workload, variant, fp64_peak):
     avg_s = t_apply / 1e3 / n_launch
     peak, peak_src = measured_peak()
     ach = bpl / avg_s / 1e9
-    layout = layout_name(info, variant)
+    layout = layout_name(info, variant, prec)
+    dia_tma = prec != "f64" and variant == 2
     kname = {2: f"sell_step_{'tma_' if variant != 1 else ''}kernel ({prec}, C={info['sell_C']})",
-             3: f"dia_step_kernel ({prec}, {info['ndiag']} stored diagonals)",
+             3: f"dia_step_{'tma_' if dia_tma else ''}kernel ({prec}, {info['ndiag']} stored diagonals)",
              1: f"csr_step_kernel ({prec})"}[info["format"]]
     tr = traffic_from_profile(workload, k, prec, layout)
     hbm = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
@@ -794,8 +865,13 @@ def run_variants(args, A, rp, ci, va, bt, opts, x_oracle, fp64_peak, fp64_s, dev
     stream = torch.cuda.current_stream(dev)
     out = []
     reps = max(3, min(args.steps, 10))
+    # the step storage of each apply precision, chosen by pp_autotune in that precision
+    layouts = {"f64": {key: opts[key] for key in ("format", "sell_C", "sell_sigma", "sell_variant")}}
+    for prec in sorted({v[1] for v in VARIANTS} - {"f64"}):
+        chosen, _ = P.autotune(rp, ci, va, A.n, **dict(opts, apply_prec=prec, k=20))
+        layouts[prec] = {key: chosen[key] for key in ("format", "sell_C", "sell_sigma", "sell_variant")}
     for name, prec, kk, flex in VARIANTS:
-        o = dict(opts, apply_prec=prec, k=kk, flexible=flex)
+        o = dict(opts, apply_prec=prec, k=kk, flexible=flex, **layouts[prec])
         S = P.Solver(rp, ci, va, A.n, **o)
         info = S.info()
         x = torch.zeros_like(bt)
@@ -813,7 +889,8 @@ def run_variants(args, A, rp, ci, va, bt, opts, x_oracle, fp64_peak, fp64_s, dev
         t = e0.elapsed_time(e1) / reps / 1e3
         roof = step_roofline(info, stats, A, kk, prec, f"diffusion192{'' if prec == 'f64' else '_' + prec}",
                              o.get("sell_variant", 0), fp64_peak)
-        ent = {"name": name, "apply": prec, "k": kk, "outer": "FCG(1)" if flex else "PCG", "time_s": round(t, 5),
+        ent = {"name": name, "apply": prec, "k": kk, "outer": "FCG(1)" if flex else "PCG",
+               "layout": layout_name(info, o.get("sell_variant", 0), prec), "time_s": round(t, 5),
                "iterations": int(stats[-1]["iterations"]), "rel_res": stats[-1]["rel_res"],
                "speedup_vs_fp64_k5": round(fp64_s / t, 3), "steps_timed": reps,
                "step_roofline": {kk2: roof[kk2] for kk2 in ("bound", "achieved", "peak", "unit", "frac",

@@ -104,8 +104,12 @@ typedef struct {
                          reads (>= 1); results do not depend on it          */
   int use_graphs;     /* 1: replay each block of check_every iterations as
                          one captured CUDA graph                            */
-  int sell_variant;   /* SELL kernel: 0 auto, 1 direct global loads,
-                         2 slices staged in shared memory by TMA bulk copies */
+  int sell_variant;   /* load path of the streaming step kernels: 0 auto,
+                         1 direct global loads, 2 staged in shared memory by
+                         bulk copies (TMA) completing on mbarriers -- SELL
+                         slices, and the FP32/BF16 steps on a Jacobi-scaled
+                         3-diagonal (7-point) DIA matrix.  Auto stages SELL
+                         slices and loads DIA rows directly              */
   int lowrank;        /* p in [0, 32]: low-rank acceleration of Section 3.1,
                          P_hat = p_k(A_hat) + V (V^T A_hat V)^{-1} V^T with V
                          the Ritz vectors of the p smallest Ritz values of
@@ -244,12 +248,14 @@ int pp_autotune_workspace_size(const pp_csr* A, const pp_options* opt, size_t* b
 
 /* Choose the storage of the fused degree step (Algorithm 2) for A: build
  * the seed-scaled matrix in each candidate layout (CSR; DIA when the matrix
- * is symmetric-banded; SELL-C-sigma with C in {32, 64, 128}, sigma in
- * {none, 1024}, direct or TMA-staged loads) that fits in the workspace, time min(k, 8)-step applications of p_k in
- * opt->apply_prec with CUDA events (one warm-up, 5 timed), and write the
- * fastest layout into opt (timings within 3% of the fastest count as a tie,
- * won by the first in the order DIA, SELL C = 32 .. 128, CSR) (format, sell_C, sell_sigma, sell_variant; the
- * rest of opt is unchanged).  The method is unchanged by the choice.
+ * is symmetric-banded -- for FP32/BF16 applies with direct or TMA-staged
+ * loads; SELL-C-sigma with C in {32, 64, 128}, sigma in {none, 1024},
+ * direct or TMA-staged loads) that fits in the workspace, time
+ * min(k, 8)-step applications of p_k in opt->apply_prec with CUDA events
+ * (one warm-up, 5 timed), and write the fastest layout into opt (timings
+ * within 3% of the fastest count as a tie, won by the first in the order
+ * DIA, SELL C = 32 .. 128, CSR) (format, sell_C, sell_sigma, sell_variant;
+ * the rest of opt is unchanged).  The method is unchanged by the choice.
  * workspace: device scratch, 256-byte aligned.  entries (host, may be
  * NULL) receives up to max_entries results in trial order; *count (may be
  * NULL) the number of layouts tried.  PP_EINVAL if none fits.
@@ -401,6 +407,32 @@ int pp_batch_features(const pp_ctx* ctx, double* feat);
  * Returns the worst status.  Synchronous. */
 int pp_batch_solve(pp_ctx* ctx, const double* b, double* x, int* iters, int* status,
                    pp_stats* stats, void* stream);
+
+/* Device time of one degree step of p_k (Algorithm 2) over every column of
+ * the batch, in the context's apply precision: one warm-up application of
+ * the k steps, then `reps` (1..1000) applications timed with CUDA events on
+ * `stream`, on the batch's current residuals (every column active).
+ * *us_per_step = microseconds per step.  Overwrites the recurrence vectors;
+ * call it between solves.  Synchronous.  No counterpart in the paper. */
+int pp_batch_time_step(pp_ctx* ctx, int reps, double* us_per_step, void* stream);
+
+/* Workspace bytes pp_batch_autotune needs (the largest candidate). */
+int pp_batch_autotune_workspace_size(const pp_batch_item* items, int count, const pp_options* opt,
+                                     size_t* bytes);
+
+/* Choose the storage of the batch's degree step by timing it: every
+ * candidate layout that applies and fits in the workspace -- per-instance
+ * symmetric DIA (stencil instances) and the global SELL-32 slice list -- is
+ * set up with a given interval and timed by pp_batch_time_step in
+ * opt->apply_prec with min(k, 8) steps; the fastest is written to
+ * opt->format (timings within 3% are a tie, won by DIA).  entries (host,
+ * may be NULL) receives up to max_entries results in trial order, *tried
+ * (may be NULL) the number of candidates.  PP_EINVAL if none fits.  The
+ * method is unchanged by the choice.  Synchronous.  No counterpart in the
+ * paper. */
+int pp_batch_autotune(const pp_batch_item* items, int count, pp_options* opt, void* workspace,
+                      size_t ws_bytes, pp_tune_entry* entries, int max_entries, int* tried,
+                      void* stream);
 
 /* ---- learned interval predictor --------------------------------------- */
 

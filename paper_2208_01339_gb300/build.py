@@ -6,7 +6,9 @@ that the process uses a single runtime (the one PyTorch has loaded).
 """
 from __future__ import annotations
 
+import hashlib
 import os
+import platform
 import subprocess
 import sys
 
@@ -36,11 +38,30 @@ def _deps() -> list[str]:
     return out
 
 
+STAMP = os.path.join(BUILD, "stamp.txt")
+
+
+def _stamp() -> str:
+    """What the library must have been built from: this machine's
+    architecture, the flags and every source and header (content hash)."""
+    h = hashlib.sha256()
+    h.update(platform.machine().encode())
+    h.update(" ".join(NVCC_FLAGS).encode())
+    for d in sorted(_deps()):
+        with open(d, "rb") as fh:
+            h.update(os.path.basename(d).encode())
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    """The library exists and was built here from the current sources (a
+    library copied from another machine or built from older sources is
+    rebuilt)."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    with open(STAMP) as fh:
+        return fh.read().strip() == _stamp()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -73,6 +94,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(_stamp() + "\n")
     return LIB
 
 

@@ -965,18 +965,14 @@ cudaError_t b_vec(pp_batch_state* B, const double* bin, double* xout, int first,
   return cudaGetLastError();
 }
 
-// z = p_k(A_hat) r for every active column, then (r,z), (q,z) -> rz_new, zq.
-cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
+// The k degree steps of Algorithm 2 for every active column: from r (or
+// r32) into z (or z32), in the apply precision.
+cudaError_t b_cheb_steps(pp_batch_state* B, cudaStream_t s) {
   const BatchDev& d = B->d;
   const int k = d.k;
   const int g = grid_b(d.nslices);
   cudaError_t e = cudaSuccess;
-  if (k == 0) {
-    e = b_vec<kBDeg0>(B, nullptr, nullptr, 0, s);
-    return e == cudaSuccess ? b_reduce(B, kRedRZ, nullptr, 0, s) : e;
-  }
   if (B->apply_prec == PP_PREC_F32) {
-    e = b_vec<kBTo32>(B, nullptr, nullptr, 0, s);
     float* buf[3] = {B->u32, B->v32, B->z32};
     const int off = ((2 - k) % 3 + 3) % 3;
     auto Y = [&](int j) { return buf[(j + off) % 3]; };
@@ -991,7 +987,6 @@ cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
                                                                cj);
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = b_vec<kBFrom32>(B, nullptr, nullptr, 0, s);
   } else {
     double* buf[3] = {B->t1, B->t2, B->z};
     const int off = ((2 - k) % 3 + 3) % 3;
@@ -1007,6 +1002,24 @@ cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
                                                                  B->c.done, cj);
       e = cudaGetLastError();
     }
+  }
+  return e;
+}
+
+// z = p_k(A_hat) r for every active column, then (r,z), (q,z) -> rz_new, zq.
+cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
+  const int k = B->d.k;
+  cudaError_t e = cudaSuccess;
+  if (k == 0) {
+    e = b_vec<kBDeg0>(B, nullptr, nullptr, 0, s);
+    return e == cudaSuccess ? b_reduce(B, kRedRZ, nullptr, 0, s) : e;
+  }
+  if (B->apply_prec == PP_PREC_F32) {
+    e = b_vec<kBTo32>(B, nullptr, nullptr, 0, s);
+    if (e == cudaSuccess) e = b_cheb_steps(B, s);
+    if (e == cudaSuccess) e = b_vec<kBFrom32>(B, nullptr, nullptr, 0, s);
+  } else {
+    e = b_cheb_steps(B, s);
     if (e == cudaSuccess) e = b_vec<kBZtoP>(B, nullptr, nullptr, 0, s);
   }
   return e == cudaSuccess ? b_reduce(B, kRedRZ, nullptr, 0, s) : e;
@@ -1466,4 +1479,117 @@ extern "C" int pp_batch_solve(pp_ctx* c, const double* b, double* x, int* iters,
     st->status = worst;
   }
   return worst;
+}
+
+// ---------------------------------------------------------------------------
+// timing and storage choice of the batched degree step
+// ---------------------------------------------------------------------------
+extern "C" int pp_batch_time_step(pp_ctx* c, int reps, double* us_per_step, void* stream) {
+  if (!c || c->kind != 2 || !us_per_step || reps < 1 || reps > 1000)
+    return fail(c, PP_EINVAL, "pp_batch_time_step: bad argument");
+  pp_batch_state* B = c->batch;
+  if (B->d.k < 1) return fail(c, PP_EINVAL, "pp_batch_time_step: the degree k must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // every column active; the steps run on the current residuals (the values
+  // do not change the work)
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->c.done, 0, sizeof(int) * B->d.ncols, s);
+  if (e == cudaSuccess) e = b_cheb_steps(B, s);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = b_cheb_steps(B, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pp_batch_time_step");
+  *us_per_step = 1e3 * (double)ms / ((double)reps * B->d.k);
+  return PP_OK;
+}
+
+namespace {
+
+// candidate layouts in preference order for ties (fewest bytes first)
+const int kBatchFormats[2] = {PP_FMT_DIA, PP_FMT_SELL};
+
+pp_options batch_candidate(const pp_options& base, int fmt) {
+  pp_options o = base;
+  o.format = fmt;
+  o.interval = PP_INTERVAL_GIVEN;  // the timing needs valid coefficients only
+  o.alpha = 1e-2;
+  o.beta = 2.0;
+  o.xi = 0.0;
+  o.k = std::max(1, std::min(base.k, 8));
+  o.use_graphs = 0;
+  return o;
+}
+
+}  // namespace
+
+extern "C" int pp_batch_autotune_workspace_size(const pp_batch_item* items, int count, const pp_options* opt,
+                                                size_t* bytes) {
+  if (!opt || !bytes) return fail(nullptr, PP_EINVAL, "NULL argument");
+  size_t most = 0;
+  for (int fmt : kBatchFormats) {
+    pp_options o = batch_candidate(*opt, fmt);
+    size_t b = 0;
+    const int rc = pp_batch_workspace_size(items, count, &o, &b);
+    if (rc == PP_EUNSUPPORTED) continue;  // layout not applicable to these instances
+    if (rc) return rc;
+    most = std::max(most, b);
+  }
+  *bytes = most;
+  return PP_OK;
+}
+
+extern "C" int pp_batch_autotune(const pp_batch_item* items, int count, pp_options* opt, void* ws, size_t ws_bytes,
+                                 pp_tune_entry* entries, int max_entries, int* tried_out, void* stream) {
+  if (!opt) return fail(nullptr, PP_EINVAL, "NULL argument");
+  if (!ws || ((uintptr_t)ws & 255)) return fail(nullptr, PP_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (max_entries < 0) return fail(nullptr, PP_EINVAL, "max_entries must be >= 0");
+  int rc = check_items(items, count);
+  if (rc) return rc;
+  if ((rc = check_batch_opts(opt))) return rc;
+  std::vector<pp_tune_entry> res;
+  int best = -1;
+  for (int fmt : kBatchFormats) {
+    pp_options o = batch_candidate(*opt, fmt);
+    pp_tune_entry e{};
+    e.format = fmt;
+    e.sell_C = fmt == PP_FMT_SELL ? 32 : 0;
+    size_t need = 0;
+    e.status = pp_batch_workspace_size(items, count, &o, &need);
+    if (e.status == PP_OK && need > ws_bytes) e.status = PP_EINVAL;  // does not fit: skipped
+    if (e.status == PP_OK) {
+      pp_ctx* c = nullptr;
+      e.status = pp_batch_setup(&c, items, count, &o, ws, ws_bytes, stream);
+      if (e.status == PP_OK) {
+        e.status = pp_batch_time_step(c, 5, &e.us_per_step, stream);
+        pp_destroy(c);
+      }
+      if (e.status == PP_ECUDA) {
+        res.push_back(e);
+        for (int i = 0; entries && i < (int)res.size() && i < max_entries; ++i) entries[i] = res[i];
+        if (tried_out) *tried_out = (int)res.size();
+        return PP_ECUDA;  // the device is in an unknown state: stop
+      }
+    }
+    if (e.status == PP_OK && (best < 0 || e.us_per_step < res[best].us_per_step)) best = (int)res.size();
+    res.push_back(e);
+  }
+  for (int i = 0; entries && i < (int)res.size() && i < max_entries; ++i) entries[i] = res[i];
+  if (tried_out) *tried_out = (int)res.size();
+  if (best < 0) return fail(nullptr, PP_EINVAL, "pp_batch_autotune: no candidate layout fits in the workspace");
+  // timings within 3% of the fastest are a tie, won by the first in order
+  const double fastest = res[best].us_per_step;
+  for (int i = 0; i < (int)res.size(); ++i)
+    if (res[i].status == PP_OK && res[i].us_per_step <= 1.03 * fastest) {
+      best = i;
+      break;
+    }
+  opt->format = res[best].format;
+  return PP_OK;
 }

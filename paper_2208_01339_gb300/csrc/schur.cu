@@ -264,41 +264,85 @@ __device__ __forceinline__ T warp_sum_t(T x) {
 }
 
 // y = M x, M the dense trace blocks (fracture f's block M_f is t_f x t_f,
-// row-major, at moff[f]): one warp per trace row; each lane keeps kMU
-// independent partial sums over the columns lane, lane + 32, ... so that
-// kMU coalesced row loads per lane are in flight at once; partial sums and
-// lanes are added in a fixed order.
-constexpr int kMU = 4;
+// row-major, at moff[f]).  A warp takes kMRows rows at a time, kMG lanes per
+// row: each lane reads 16 bytes of the row per step (the kMG lanes of a row
+// cover 128 contiguous bytes), so a warp-wide load fetches whole lines, and
+// the row's sum needs log2(kMG) shuffle-add steps instead of 5 -- those adds
+// run on the FP64 pipe, which bounds this product (one FMA per entry).  The
+// row's unaligned head (before its first 16-byte boundary) is added by its
+// first lane.  Partial sums are combined in a fixed order.
+constexpr int kMG = 8;              // lanes per row
+constexpr int kMRows = 32 / kMG;    // rows per warp pass
+
+template <typename T>
+struct MVec;
+template <>
+struct MVec<double> {
+  static constexpr int W = 2;
+  __device__ static void ld(const double* p, double (&o)[2]) {
+    const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+};
+template <>
+struct MVec<float> {
+  static constexpr int W = 4;
+  __device__ static void ld(const float* p, float (&o)[4]) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+  }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) m_apply_kernel(int n_T, const long long* __restrict__ toff,
                                                          const long long* __restrict__ moff,
                                                          const int* __restrict__ tfrac, const T* __restrict__ M,
                                                          const T* __restrict__ x, T* __restrict__ y) {
-  const int lane = threadIdx.x & 31;
+  constexpr int W = MVec<T>::W;  // elements per 16 bytes
+  const int lane = threadIdx.x & 31, q = lane / kMG, l = lane % kMG;
   const long long gw = gtid() >> 5, nw = gstride() >> 5;
-  for (long long r = gw; r < n_T; r += nw) {
-    const int f = tfrac[r];
-    const long long t0 = toff[f];
-    const int t = (int)(toff[f + 1] - t0);
-    const T* row = M + moff[f] + (r - t0) * t;
-    const T* xf = x + t0;
-    T acc[kMU];
+  for (long long r0 = gw * kMRows; r0 < n_T; r0 += nw * kMRows) {
+    const long long r = r0 + q;
+    T a = (T)0;
+    if (r < n_T) {
+      const int f = tfrac[r];
+      const long long t0 = toff[f];
+      const int t = (int)(toff[f + 1] - t0);
+      const long long e = moff[f] + (r - t0) * t;  // element index of the row's first entry
+      const T* row = M + e;
+      const T* xf = x + t0;
+      const int head = (int)((W - e % W) % W) < t ? (int)((W - e % W) % W) : t;  // entries before alignment
+      T acc0 = (T)0, acc1 = (T)0;
+      if (l == 0)
+        for (int j = 0; j < head; ++j) acc0 = fma(__ldcs(row + j), __ldg(xf + j), acc0);
+      int j = head + l * W;
+      // two 16-byte loads in flight per lane per step
+      for (; j + kMG * W + W <= t; j += 2 * kMG * W) {
+        T m0[W], m1[W];
+        MVec<T>::ld(row + j, m0);
+        MVec<T>::ld(row + j + kMG * W, m1);
 #pragma unroll
-    for (int u = 0; u < kMU; ++u) acc[u] = (T)0;
-    int b = lane;
-    for (; b + 32 * (kMU - 1) < t; b += 32 * kMU) {
-      T m[kMU];
+        for (int u = 0; u < W; ++u) acc0 = fma(m0[u], __ldg(xf + j + u), acc0);
 #pragma unroll
-      for (int u = 0; u < kMU; ++u) m[u] = __ldcs(row + b + 32 * u);
+        for (int u = 0; u < W; ++u) acc1 = fma(m1[u], __ldg(xf + j + kMG * W + u), acc1);
+      }
+      for (; j + W <= t; j += kMG * W) {
+        T m0[W];
+        MVec<T>::ld(row + j, m0);
 #pragma unroll
-      for (int u = 0; u < kMU; ++u) acc[u] = fma(m[u], __ldg(xf + b + 32 * u), acc[u]);
+        for (int u = 0; u < W; ++u) acc0 = fma(m0[u], __ldg(xf + j + u), acc0);
+      }
+      for (int u = 0; u < W; ++u)  // the tail after the last full 16 bytes
+        if (j + u < t) acc0 = fma(__ldcs(row + j + u), __ldg(xf + j + u), acc0);
+      a = acc0 + acc1;
     }
-    for (; b < t; b += 32) acc[0] = fma(__ldcs(row + b), __ldg(xf + b), acc[0]);
-    T a = acc[0];
 #pragma unroll
-    for (int u = 1; u < kMU; ++u) a += acc[u];
-    a = warp_sum_t(a);
-    if (lane == 0) y[r] = a;
+    for (int o = kMG / 2; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o, kMG);
+    if (r < n_T && l == 0) y[r] = a;
   }
 }
 
@@ -553,6 +597,7 @@ int plan_traces(const pp_dfn* d, TracePlan& P, cudaStream_t s) {
     P.yoff[g + 1] = P.yoff[g] + d->ny[g];
   }
   P.m_elems = P.moff[nf];
+
   // restrict the row side of C, B, G^h and remap the column side of C^T, B^T, G^h
   auto restrict_rows = [&](const HCsr& X, HCsr& Y, bool remap_cols) -> int {
     Y.nrows = P.n_T;
@@ -765,7 +810,7 @@ cudaError_t ainv_full(const SchurImpl* S, const double* v, double* y, cudaStream
 
 template <typename T>
 cudaError_t m_apply(const SchurImpl* S, const T* M, const T* x, T* y, int* err, cudaStream_t s) {
-  (void)err;  // the direct-load product has no device waits
+  (void)err;  // no device waits in the product
   const int g = grid_of((long long)S->n_T * 32);
   m_apply_kernel<T><<<g, kBlock, 0, s>>>(S->n_T, S->toff, S->moff, S->tfrac, M, x, y);
   return cudaGetLastError();

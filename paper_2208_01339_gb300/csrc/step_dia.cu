@@ -8,17 +8,10 @@
 // i - offset, which another thread of the same sweep has just read, so the
 // second read is served by L2.  Consecutive row groups on consecutive
 // lanes: every stream is coalesced.
-#include "step_impl.cuh"
+#include "step_dia.cuh"
 
 namespace pp {
 namespace {
-
-struct DiaArgs {
-  int nd;
-  int unit;  // 1: the main diagonal is 1 and not stored
-  int doff[kMaxDiag];
-  long long dstride, dpad, n_pad;
-};
 
 template <typename TV, typename TX>
 __device__ __forceinline__ TX ldv(const TV* p) {
@@ -133,6 +126,35 @@ __device__ __forceinline__ void ldvals(const TV* p, TX (&o)[R]) {
   }
 }
 
+// Loads with an L2 eviction priority, for the FP32/BF16 steps (2 rows per
+// thread): the stored diagonals stream through once per step (evict first),
+// while r is read by every step of an application and x, x_old are the two
+// previous steps' outputs, so the vectors stay in L2 between steps when the
+// matrix does not push them out.
+template <typename TV>
+__device__ __forceinline__ void ld2_hint(const TV* p, float (&o)[2], uint64_t pol) {
+  if constexpr (std::is_same<TV, __nv_bfloat16>::value) {
+    unsigned int u;
+    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(u) : "l"(p), "l"(pol));
+    o[0] = bf16_lo(u);
+    o[1] = bf16_hi(u);
+  } else {
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(o[0]), "=f"(o[1]) : "l"(p), "l"(pol));
+  }
+}
+template <typename TV>
+__device__ __forceinline__ float ld1_hint(const TV* p, uint64_t pol) {
+  if constexpr (std::is_same<TV, __nv_bfloat16>::value) {
+    unsigned short u;
+    asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(u) : "l"(p), "l"(pol));
+    return __uint_as_float(((unsigned int)u) << 16);
+  } else {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+  }
+}
+
 // ND > 0: that many stored diagonals, unrolled, the main one first unless
 // UNIT; ND = 0: d.nd and d.unit at run time.  UNIT (the Jacobi-scaled matrix,
 // whose diagonal is 1 by construction) starts each row sum from x_i and
@@ -158,13 +180,22 @@ __global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* _
   // sum starts from u, so a row costs 2 + 2 nd + 1 FP64 operations (9 for
   // the 7-point stencil) instead of 2 nd + 4.
   constexpr bool kFold = ND > 0 && UNIT && (MODE == kChebK || MODE == kCheb2);
+  constexpr bool kHint = std::is_same<TX, float>::value && R == 2;  // L2 priorities (see ld2_hint)
+  uint64_t pol_first = 0, pol_last = 0;
+  if constexpr (kHint) {
+    pol_first = policy_evict_first();
+    pol_last = policy_evict_last();
+  }
   for (long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R; i0 < d.n_pad;
        i0 += (long long)gridDim.x * blockDim.x * R) {
     TX xs[R], acc[R], u[R];
     Vec<TX, R>::ld(a.x + i0, xs);
     if constexpr (kFold) {
       TX rs[R], xo[R], y[R];
-      Vec<TX, R>::ld(a.r + i0, rs);
+      if constexpr (kHint)
+        ld2_hint<float>(reinterpret_cast<const float*>(a.r + i0), reinterpret_cast<float(&)[2]>(rs), pol_last);
+      else
+        Vec<TX, R>::ld(a.r + i0, rs);
       if constexpr (MODE == kChebK) {
         Vec<TX, R>::ld(a.xold + i0, xo);
 #pragma unroll
@@ -177,11 +208,18 @@ __global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* _
       for (int t = 0; t < ND; ++t) {
         const long long o = d.doff[t];
         const TV* vt = base + (long long)t * d.dstride;
-        ldvals<TV, TX, R>(vt + i0, u);
+        if constexpr (kHint)
+          ld2_hint<TV>(vt + i0, reinterpret_cast<float(&)[2]>(u), pol_first);
+        else
+          ldvals<TV, TX, R>(vt + i0, u);
 #pragma unroll
         for (int e = 0; e < R; ++e) {
           const long long i = i0 + e;
-          const TX lo = ldv<TV, TX>(vt + i - o);
+          TX lo;
+          if constexpr (kHint)
+            lo = ld1_hint<TV>(vt + i - o, pol_first);
+          else
+            lo = ldv<TV, TX>(vt + i - o);
           const long long ju = i + o < last ? i + o : last;
           const long long jl = i - o > 0 ? i - o : 0;
           acc[e] = fma(-u[e], __ldg(a.x + ju), acc[e]);
@@ -213,11 +251,18 @@ __global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* _
       }
       const long long o = d.doff[t];
       const TV* vt = base + (long long)t * d.dstride;
-      ldvals<TV, TX, R>(vt + i0, u);  // a(i, i + o); 0 past the last row
+      if constexpr (kHint)  // a(i, i + o); 0 past the last row
+        ld2_hint<TV>(vt + i0, reinterpret_cast<float(&)[2]>(u), pol_first);
+      else
+        ldvals<TV, TX, R>(vt + i0, u);
 #pragma unroll
       for (int e = 0; e < R; ++e) {
         const long long i = i0 + e;
-        const TX lo = ldv<TV, TX>(vt + i - o);  // a(i - o, i) = a(i, i - o); 0 in the front pad
+        TX lo;  // a(i - o, i) = a(i, i - o); 0 in the front pad
+        if constexpr (kHint)
+          lo = ld1_hint<TV>(vt + i - o, pol_first);
+        else
+          lo = ldv<TV, TX>(vt + i - o);
         const long long ju = i + o < last ? i + o : last;
         const long long jl = i - o > 0 ? i - o : 0;
         acc[e] = fma(u[e], __ldg(a.x + ju), acc[e]);
@@ -227,7 +272,12 @@ __global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* _
     TX rs[R], xo[R], y[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) rs[e] = xo[e] = (TX)0;
-    if constexpr (mode_needs_r<MODE>()) Vec<TX, R>::ld(a.r + i0, rs);
+    if constexpr (mode_needs_r<MODE>()) {
+      if constexpr (kHint)
+        ld2_hint<float>(reinterpret_cast<const float*>(a.r + i0), reinterpret_cast<float(&)[2]>(rs), pol_last);
+      else
+        Vec<TX, R>::ld(a.r + i0, rs);
+    }
     if constexpr (mode_needs_xold<MODE>()) {
       if (MODE == kChebK || a.xold) Vec<TX, R>::ld(a.xold + i0, xo);
     }
@@ -239,230 +289,6 @@ __global__ void __launch_bounds__(kBlock) dia_step_kernel(DiaArgs d, const TV* _
     Vec<TX, R>::st(a.y + i0, y);
   }
   finish_dots<TX, NDOT>(a, dot, partials, counter);
-}
-
-// ------------------------------------------ TMA-staged low-precision step ----
-// The FP32/BF16 steps move few bytes per row and have little arithmetic, so
-// the load latency, not the bandwidth, limits the direct kernel above.  Here
-// every stream of a tile of kDT consecutive rows is a contiguous range --
-// the 3 stored diagonals at the tile's rows (upper entries) and at the rows
-// shifted by -offset (lower entries), x at the tile's rows and shifted by
-// +-offset, r and x_old -- so one thread per CTA moves them into shared
-// memory with cp.async.bulk (completing on an mbarrier), kDStages tiles
-// ahead, and the CTA's threads compute rows from shared memory.  The shifted
-// ranges were (or soon will be) read by the tiles they belong to, so they
-// come from L2.  Starts are rounded down to 16 bytes (the copy's alignment
-// rule) and the vector ranges are clipped to [0, n_pad); a row's neighbour
-// index is clipped the same way, where the matrix entry is 0.  The Jacobi-
-// scaled 7-point stencil only: 3 upper diagonals, unit main diagonal.
-constexpr int kDT = 1024;     // rows per tile
-constexpr int kDStages = 3;   // tiles in flight per CTA
-constexpr int kDThreads = 256;
-constexpr int kDRanges = 15;  // 3 upper + 3 lower value ranges, 7 x ranges, r, x_old
-
-template <typename TV>
-struct DiaTma {
-  static constexpr int kAV = 16 / (int)sizeof(TV);  // alignment unit of the value ranges (elements)
-  static constexpr int kAX = 4;                     // of the FP32 vector ranges
-  static constexpr int kUpB = kDT * (int)sizeof(TV);
-  // a shifted range of kDT rows spans at most kDT + 2 (alignment unit) - 2
-  // elements once its ends are rounded out to 16 bytes
-  static constexpr int kLoB = (((kDT + 2 * kAV) * (int)sizeof(TV)) + 127) / 128 * 128;
-  static constexpr int kXB = (((kDT + 2 * kAX) * 4) + 127) / 128 * 128;
-  static constexpr int kVB = kDT * 4;
-  static constexpr int kOffLo = 3 * kUpB;
-  static constexpr int kOffX = kOffLo + 3 * kLoB;
-  static constexpr int kOffR = kOffX + 7 * kXB;
-  static constexpr int kOffXo = kOffR + kVB;
-  static constexpr int kStage = kOffXo + kVB;
-  static constexpr int kSmem = kStage * kDStages;
-};
-
-__device__ __forceinline__ void bulk_g2s_plain(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-
-template <typename TV>
-__device__ __forceinline__ float smem_val(const unsigned char* p, long long k) {
-  if constexpr (std::is_same<TV, __nv_bfloat16>::value)
-    return __uint_as_float(((unsigned int)reinterpret_cast<const unsigned short*>(p)[k]) << 16);
-  else
-    return reinterpret_cast<const float*>(p)[k];
-}
-
-template <typename TV, int MODE>
-__global__ void __launch_bounds__(kDThreads, 1) dia_step_tma_kernel(DiaArgs d, const TV* __restrict__ val,
-                                                                    StepArgs<float> a, const Scalars* sc) {
-  using L = DiaTma<TV>;
-  extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t bars[kDStages];
-  __shared__ long long rstart[kDStages][kDRanges];  // row coordinate of each range's first staged element
-  if (sc && load_done(sc)) return;
-  const long long n_pad = d.n_pad;
-  const long long ntiles = (n_pad + kDT - 1) / kDT;
-  if (threadIdx.x == 0) {
-    for (int b = 0; b < kDStages; ++b) mbar_init(&bars[b], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  const bool has_xo = MODE == kChebK;
-
-  // Stage tile `tile` into buffer b (thread 0 only).
-  auto issue = [&](long long tile, int b) {
-    unsigned char* st = dsm + (size_t)b * L::kStage;
-    const long long i0 = tile * kDT;
-    const long long len = (n_pad - i0 < kDT) ? n_pad - i0 : kDT;
-    const char* vbase = reinterpret_cast<const char*>(val);
-    long long src[kDRanges];
-    int dst[kDRanges];
-    uint32_t nb[kDRanges];
-    int nr = 0;
-    // upper entries a(i, i + o_t): rows [i0, i0 + len) of diagonal t
-    for (int t = 0; t < 3; ++t) {
-      const long long e0 = (long long)t * d.dstride + d.dpad + i0;
-      src[nr] = e0 * (long long)sizeof(TV);
-      dst[nr] = t * L::kUpB;
-      nb[nr] = (uint32_t)(len * (long long)sizeof(TV));
-      rstart[b][nr++] = i0;
-    }
-    // lower entries a(i, i - o_t) = a(i - o_t, i): positions [i0 - o_t, i0 - o_t + len)
-    for (int t = 0; t < 3; ++t) {
-      const long long o = d.doff[t];
-      const long long dbeg = (long long)t * d.dstride;  // diagonal t's storage (front pad included)
-      const long long dend = dbeg + d.dpad + n_pad;
-      long long e0 = dbeg + d.dpad + i0 - o;
-      const long long sh = e0 % L::kAV;
-      e0 -= sh;
-      long long e1 = dbeg + d.dpad + i0 - o + len;
-      e1 = (e1 + L::kAV - 1) / L::kAV * L::kAV;
-      if (e1 > dend) e1 = dend;
-      src[nr] = e0 * (long long)sizeof(TV);
-      dst[nr] = L::kOffLo + t * L::kLoB;
-      nb[nr] = (uint32_t)((e1 - e0) * (long long)sizeof(TV));
-      rstart[b][nr++] = i0 - o - sh;
-    }
-    // x at the tile's rows and shifted by +-o_t, clipped to [0, n_pad)
-    for (int q = 0; q < 7; ++q) {
-      const long long sft = q == 0 ? 0 : (q & 1 ? (long long)d.doff[(q - 1) / 2] : -(long long)d.doff[(q - 1) / 2]);
-      long long r0 = i0 + sft, r1 = i0 + sft + len;
-      if (r0 < 0) r0 = 0;
-      if (r1 > n_pad) r1 = n_pad;
-      if (r1 <= r0) {  // the whole range lies outside: stage one aligned group at the nearest end
-        r0 = sft < 0 ? 0 : n_pad - L::kAX;
-        r1 = r0 + L::kAX;
-      }
-      r0 = r0 / L::kAX * L::kAX;
-      r1 = (r1 + L::kAX - 1) / L::kAX * L::kAX;
-      src[nr] = -1 - q;  // vector range, resolved below
-      dst[nr] = L::kOffX + q * L::kXB;
-      nb[nr] = (uint32_t)((r1 - r0) * 4);
-      rstart[b][nr++] = r0;
-    }
-    uint32_t total = 0;
-    for (int k = 0; k < nr; ++k) total += nb[k];
-    total += (uint32_t)(len * 4);
-    if (has_xo) total += (uint32_t)(len * 4);
-    // order this CTA's earlier generic reads of buffer b before the refill
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(&bars[b], total);
-    for (int k = 0; k < nr; ++k) {
-      const void* g = src[k] >= 0 ? (const void*)(vbase + src[k]) : (const void*)(a.x + rstart[b][k]);
-      bulk_g2s_plain(st + dst[k], g, nb[k], &bars[b]);
-    }
-    bulk_g2s_plain(st + L::kOffR, a.r + i0, (uint32_t)(len * 4), &bars[b]);
-    if (has_xo) bulk_g2s_plain(st + L::kOffXo, a.xold + i0, (uint32_t)(len * 4), &bars[b]);
-  };
-
-  const long long g = gridDim.x;
-  uint32_t inflight = 0u;  // bit b: stage b has a copy in flight (the same in every thread)
-  uint32_t phase = 0u;     // bit b: parity of stage b's next completion
-  for (int p = 0; p < kDStages - 1; ++p) {
-    const long long tl = blockIdx.x + p * g;
-    if (tl < ntiles) {
-      if (threadIdx.x == 0) issue(tl, p);
-      inflight |= 1u << p;
-    }
-  }
-  bool ok = true;
-  long long k = 0;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += g, ++k) {
-    const int b = (int)(k % kDStages);
-    {
-      const long long nxt = tile + (long long)(kDStages - 1) * g;
-      const int bn = (int)((k + kDStages - 1) % kDStages);
-      if (nxt < ntiles) {
-        if (threadIdx.x == 0) issue(nxt, bn);
-        inflight |= 1u << bn;
-      }
-    }
-    const bool arrived = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
-    if (!__syncthreads_and(arrived)) {
-      ok = false;
-      break;
-    }
-    inflight &= ~(1u << b);
-    phase ^= 1u << b;
-    const unsigned char* st = dsm + (size_t)b * L::kStage;
-    const long long i0 = tile * kDT;
-    const int len = (int)((n_pad - i0 < kDT) ? n_pad - i0 : kDT);
-    // per tile: index of row i0's entry in each staged range, and the
-    // clipping bounds of the neighbour indices (in staged-range units)
-    int clo[3], cxp[3], cxm[3], hip[3], lom[3];
-    const int cx0 = (int)(i0 - rstart[b][6]);
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const long long o = d.doff[t];
-      clo[t] = (int)(i0 - o - rstart[b][3 + t]);
-      cxp[t] = (int)(i0 + o - rstart[b][7 + 2 * t]);
-      cxm[t] = (int)(i0 - o - rstart[b][8 + 2 * t]);
-      hip[t] = (int)(n_pad - 1 - rstart[b][7 + 2 * t]);  // x[n_pad - 1]
-      lom[t] = (int)(-rstart[b][8 + 2 * t]);             // x[0]
-    }
-    const float* xsm = reinterpret_cast<const float*>(st + L::kOffX);
-    const float* rsm = reinterpret_cast<const float*>(st + L::kOffR);
-    const float* xosm = reinterpret_cast<const float*>(st + L::kOffXo);
-    float* yg = a.y + i0;
-    for (int li = threadIdx.x; li < len; li += kDThreads) {
-      const float xs = xsm[li + cx0];
-      const float rs = rsm[li];
-      float acc;
-      if constexpr (MODE == kChebK) {
-        acc = fmaf(a.ce, xosm[li], fmaf(a.cd, xs, rs));
-      } else if constexpr (MODE == kCheb2) {
-        acc = fmaf(a.cd, xs, a.ce * rs);
-      } else {
-        acc = xs;  // kCheb1: x = r and A x = x + S x
-      }
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const float up = smem_val<TV>(st + t * L::kUpB, li);
-        const float lo = smem_val<TV>(st + L::kOffLo + t * L::kLoB, li + clo[t]);
-        const int jp = min(li + cxp[t], hip[t]);
-        const int jm = max(li + cxm[t], lom[t]);
-        const float xp = reinterpret_cast<const float*>(st + L::kOffX + (1 + 2 * t) * L::kXB)[jp];
-        const float xm = reinterpret_cast<const float*>(st + L::kOffX + (2 + 2 * t) * L::kXB)[jm];
-        if constexpr (MODE == kCheb1) {
-          acc = fmaf(up, xp, acc);
-          acc = fmaf(lo, xm, acc);
-        } else {
-          acc = fmaf(-up, xp, acc);
-          acc = fmaf(-lo, xm, acc);
-        }
-      }
-      yg[li] = MODE == kCheb1 ? fmaf(a.cb, acc, a.ca * rs) : a.cc * acc;
-    }
-    __syncthreads();  // stage b is read; it may be refilled
-  }
-  if (!ok) {
-    // a staged copy did not arrive in time: record it, and wait (bounded)
-    // for this CTA's copies still in flight so that none lands after exit
-    if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
-    for (int b = 0; b < kDStages; ++b)
-      if ((inflight >> b) & 1u) mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
-  }
 }
 
 // Whole resident waves per launch: the grid-stride loops split the rows evenly
@@ -487,48 +313,6 @@ int wave_grid(int cap) {
   return blocks[dev] < cap ? blocks[dev] : cap;
 }
 
-DiaArgs dia_args(const MatDesc& A) {
-  DiaArgs d;
-  d.nd = A.ndiag;
-  d.unit = A.dia_unit;
-  for (int t = 0; t < kMaxDiag; ++t) d.doff[t] = t < A.ndiag ? A.doff[t] : 0;
-  d.dstride = A.dstride;
-  d.dpad = A.dpad;
-  d.n_pad = A.n_pad;
-  return d;
-}
-
-// TMA-staged launch: one CTA per SM (the stages take most of its shared
-// memory), capped by the caller's grid and the number of tiles.
-template <typename TV, int MODE>
-cudaError_t go_dia_tma(const MatDesc& A, const StepParams& p, const Scalars* sc, int grid, cudaStream_t s) {
-  using L = DiaTma<TV>;
-  auto kern = dia_step_tma_kernel<TV, MODE>;
-  static bool attr_set[kMaxDevices] = {false};
-  static int per_sm[kMaxDevices] = {0};
-  const int dev = current_device();
-  if (!attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem);
-    if (e != cudaSuccess) return e;
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kDThreads, L::kSmem);
-    if (e != cudaSuccess) return e;
-    per_sm[dev] = nb > 0 ? nb : 1;
-    attr_set[dev] = true;
-  }
-  StepArgs<float> args = make_args<float>(p);
-  if (MODE == kChebK || MODE == kCheb2) {  // folded coefficients, as in dia_step_kernel
-    args.cd = (float)(p.ca / p.cc - 1.0);
-    args.ce = (float)(MODE == kChebK ? p.cb / p.cc : p.cb / p.cc + 1.0);
-  }
-  const long long tiles = (A.n_pad + kDT - 1) / kDT;
-  long long g = (long long)num_sms() * per_sm[dev];
-  if (g > tiles) g = tiles;
-  if (g > grid) g = grid;
-  if (g < 1) g = 1;
-  kern<<<(int)g, kDThreads, L::kSmem, s>>>(dia_args(A), static_cast<const TV*>(A.val), args, sc);
-  return cudaGetLastError();
-}
 
 template <typename TV, typename TX, int MODE, int NDOT>
 cudaError_t go_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, double* partials, unsigned int* cnt,
@@ -538,7 +322,7 @@ cudaError_t go_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, dou
   } else {
     if constexpr (std::is_same<TX, float>::value && NDOT == 0 &&
                   (MODE == kCheb1 || MODE == kCheb2 || MODE == kChebK)) {
-      if (A.tma && A.ndiag == 3 && A.dia_unit) return go_dia_tma<TV, MODE>(A, p, sc, grid, s);
+      if (A.tma && dia_tma_applies(A)) return launch_step_dia_tma(A, p, sc, grid, s);
     }
     constexpr int R = std::is_same<TX, double>::value ? 4 : 2;
     const TV* v = static_cast<const TV*>(A.val);

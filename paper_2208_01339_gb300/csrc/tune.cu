@@ -1,6 +1,7 @@
 // Autotuner of the storage of the fused degree step: it builds the matrix
 // in every candidate layout that applies and fits in the caller's
-// workspace (CSR; symmetric DIA for banded matrices; SELL-C-sigma with
+// workspace (CSR; symmetric DIA for banded matrices, for FP32/BF16 applies
+// with direct or TMA-staged loads; SELL-C-sigma with
 // C = 32, 64, 128 rows per slice -- 1, 2 or 4 rows per lane -- and sort
 // windows sigma = C or 1024, with direct loads or TMA-staged slices),
 // times applications of p_k on it with CUDA events and reports the
@@ -21,10 +22,15 @@ struct Candidate {
   int format, C, sigma, variant;
 };
 
-std::vector<Candidate> candidates() {
+std::vector<Candidate> candidates(int apply_prec) {
   // preference order for ties: fewest bytes per step first
   std::vector<Candidate> out;
-  out.push_back({PP_FMT_DIA, 0, 0, 0});
+  if (apply_prec == PP_PREC_F64) {
+    out.push_back({PP_FMT_DIA, 0, 0, 0});
+  } else {  // FP32/BF16 DIA steps: direct loads or TMA-staged tiles
+    out.push_back({PP_FMT_DIA, 0, 0, 1});
+    out.push_back({PP_FMT_DIA, 0, 0, 2});
+  }
   for (int C : {32, 64, 128})
     for (int sigma : {0, 1024})
       for (int variant : {1, 2}) out.push_back({PP_FMT_SELL, C, sigma, variant});
@@ -55,7 +61,7 @@ pp_options candidate_options(const pp_options& base, const Candidate& cd) {
 extern "C" int pp_autotune_workspace_size(const pp_csr* A, const pp_options* opt, size_t* bytes) {
   if (!opt || !bytes) return fail(nullptr, PP_EINVAL, "NULL argument");
   size_t most = 0;
-  for (const Candidate& cd : candidates()) {
+  for (const Candidate& cd : candidates(opt->apply_prec)) {
     pp_options o = candidate_options(*opt, cd);
     size_t b = 0;
     const int rc = pp_workspace_size(A, &o, &b);
@@ -74,7 +80,7 @@ extern "C" int pp_autotune(const pp_csr* A, pp_options* opt, void* ws, size_t ws
   if (max_entries < 0) return fail(nullptr, PP_EINVAL, "max_entries must be >= 0");
   int rc = validate_options(nullptr, opt);
   if (rc) return rc;
-  const std::vector<Candidate> cands = candidates();
+  const std::vector<Candidate> cands = candidates(opt->apply_prec);
   int tried = 0, best = -1;
   double best_us = 0.0;
   std::vector<pp_tune_entry> res;

@@ -141,6 +141,11 @@ SIGNATURES = [
     ("pp_batch_intervals", ctypes.c_int, [_vp, _vp, _vp]),
     ("pp_batch_features", ctypes.c_int, [_vp, _vp]),
     ("pp_batch_solve", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(Stats), _vp]),
+    ("pp_batch_time_step", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
+    ("pp_batch_autotune_workspace_size", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(Options),
+                                                        ctypes.POINTER(ctypes.c_size_t)]),
+    ("pp_batch_autotune", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(Options), _vp, ctypes.c_size_t,
+                                         ctypes.POINTER(TuneEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp]),
     ("pp_mlp_workspace_size", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("pp_mlp_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_ulonglong, _vp, ctypes.c_size_t]),
     ("pp_mlp_params", ctypes.c_int, [_vp, _vp, _vp]),
@@ -464,6 +469,35 @@ class SchurSolver(Solver):
         return y
 
 
+def batch_items(mats, nrhs, device="cuda"):
+    """(ctypes array of pp_batch_item, device tensors to keep alive)."""
+    items = (BatchItem * len(mats))()
+    keep = []
+    for i, A in enumerate(mats):
+        rp, ci, va = to_device_csr(A, device)
+        keep.append((rp, ci, va))
+        items[i] = BatchItem(A.n, int(A.nnz), _ptr(rp), _ptr(ci), _ptr(va), int(nrhs[i]))
+    return items, keep
+
+
+def batch_autotune(mats, nrhs, device="cuda", stream=None, **options):
+    """Time the batch's degree step in every applicable layout
+    (pp_batch_autotune); returns (format name, list of per-layout results)."""
+    torch = _torch()
+    opts = make_options(**options)
+    items, keep = batch_items(mats, nrhs, device)
+    nbytes = ctypes.c_size_t()
+    _check(lib().pp_batch_autotune_workspace_size(ctypes.cast(items, _vp), len(mats), ctypes.byref(opts),
+                                                  ctypes.byref(nbytes)))
+    ws = torch.empty(max(256, int(nbytes.value)), dtype=torch.uint8, device=device)
+    ent = (TuneEntry * 4)()
+    cnt = ctypes.c_int()
+    _check(lib().pp_batch_autotune(ctypes.cast(items, _vp), len(mats), ctypes.byref(opts), _ptr(ws), ws.numel(), ent,
+                                   4, ctypes.byref(cnt), _stream(stream)))
+    del ws, keep
+    return FORMAT_NAME.get(opts.format, "sell"), [ent[i].as_dict() for i in range(cnt.value)]
+
+
 class BatchSolver:
     """Many SPD instances (each with 1..8 right-hand sides) solved together
     by one set of persistent launches (pp_batch_setup / pp_batch_solve)."""
@@ -473,12 +507,7 @@ class BatchSolver:
         self.opts = make_options(**options)
         self.nrhs = [int(r) for r in nrhs]
         self.sizes = [int(A.n) for A in mats]
-        items = (BatchItem * len(mats))()
-        keep = []
-        for i, A in enumerate(mats):
-            rp, ci, va = to_device_csr(A, device)
-            keep.append((rp, ci, va))
-            items[i] = BatchItem(A.n, int(A.nnz), _ptr(rp), _ptr(ci), _ptr(va), self.nrhs[i])
+        items, keep = batch_items(mats, self.nrhs, device)
         self._items = items
         nbytes = ctypes.c_size_t()
         _check(lib().pp_batch_workspace_size(ctypes.cast(items, _vp), len(mats), ctypes.byref(self.opts),
@@ -529,6 +558,12 @@ class BatchSolver:
         d = st.as_dict()
         d["status"] = rc
         return x, it, stv, d
+
+    def time_step(self, reps: int = 5, stream=None) -> float:
+        """Microseconds per degree step of p_k over all columns (pp_batch_time_step)."""
+        us = ctypes.c_double()
+        _check(lib().pp_batch_time_step(self.ctx, int(reps), ctypes.byref(us), _stream(stream)), self.ctx)
+        return us.value
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -23,6 +23,19 @@ def shard(n_items: int, rank: int, world: int) -> range:
     return range(start, start + q + (1 if rank < r else 0))
 
 
+def shard_balanced(weights, rank: int, world: int) -> list:
+    """Indices owned by `rank` when items of the given work weights are
+    dealt, heaviest first, to the least-loaded rank (ties: lowest rank);
+    every rank computes the same assignment.  Returned in index order."""
+    load = [0.0] * world
+    own = [[] for _ in range(world)]
+    for i in sorted(range(len(weights)), key=lambda j: (-float(weights[j]), j)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += float(weights[i])
+        own[r].append(i)
+    return sorted(own[rank])
+
+
 def max_over_ranks(value: float, device=None) -> float:
     """The largest `value` over all ranks (the value itself without a process group)."""
     import torch

@@ -145,3 +145,15 @@ def test_fma_rate_argument_checks_without_gpu(lib):
     assert lib.pp_fp64_fma_rate(None, 3, ctypes.byref(out), None) == P.PP_EINVAL
     assert lib.pp_fp64_fma_rate(ctypes.c_void_p(256), 0, ctypes.byref(out), None) == P.PP_EINVAL
     assert lib.pp_fp64_fma_rate(ctypes.c_void_p(256), 3, None, None) == P.PP_EINVAL
+
+
+def test_batch_tuning_argument_checks_without_gpu(lib):
+    o = P.make_options()
+    us = ctypes.c_double()
+    assert lib.pp_batch_time_step(None, 3, ctypes.byref(us), None) == P.PP_EINVAL
+    nbytes = ctypes.c_size_t()
+    assert lib.pp_batch_autotune_workspace_size(None, 1, None, ctypes.byref(nbytes)) == P.PP_EINVAL
+    assert lib.pp_batch_autotune(None, 1, ctypes.byref(o), ctypes.c_void_p(256), 1 << 20, None, 0, None,
+                                 None) == P.PP_EINVAL
+    assert lib.pp_batch_autotune(None, 1, ctypes.byref(o), ctypes.c_void_p(8), 1 << 20, None, 0, None,
+                                 None) == P.PP_EINVAL  # unaligned workspace

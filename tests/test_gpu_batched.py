@@ -152,3 +152,33 @@ def test_batch_dia_rejects_unbanded_instance(problem):
     with pytest.raises(P.PolyPrecError) as ei:
         P.BatchSolver([mats[0], D], [1, 2], k=3, format="dia")
     assert ei.value.status in (P.PP_EUNSUPPORTED,)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batch_autotune_and_step_timer(problem, prec):
+    """pp_batch_autotune times both layouts of these stencil instances and
+    picks one; the solve in the chosen layout still matches the oracle;
+    pp_batch_time_step reports a positive time and leaves the solver usable."""
+    mats, rhs = problem
+    fmt, table = P.batch_autotune(mats, [s.nrhs for s in SPECS], k=6, apply_prec=prec,
+                                  flexible=1 if prec == "f32" else 0)
+    assert fmt in ("dia", "sell")
+    assert {t["format"] for t in table if t["status"] == 0} == {2, 3}
+    assert all(t["us_per_step"] > 0 for t in table if t["status"] == 0)
+    S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=6, lanczos_steps=8, rtol=1e-10, format=fmt, apply_prec=prec,
+                      flexible=1 if prec == "f32" else 0, seed=100)
+    assert S.time_step(reps=3) > 0
+    x, it, st, _ = S.solve(S.pack(rhs))
+    assert (st == 0).all()
+    xs = S.unpack(x)
+    ref = oracle_cols(mats, rhs, 6, 100, 8)
+    g = 0
+    for i, B in enumerate(rhs):
+        for r in range(B.shape[1]):
+            xo, so = ref[g]
+            if prec == "f64":
+                assert it[g] == so["iterations"]
+                assert_close(xs[i][:, r], xo, 1e-10)
+            else:
+                assert_close(xs[i][:, r], xo, 1e-7)
+            g += 1

@@ -29,22 +29,36 @@ def _dev():
 
 
 @pytest.fixture(scope="module")
-def model():
+def trained():
     specs = L.training_specs(150, seed=11, nmin=12, nmax=28)
     feats, iters, base = L.sweep(specs, k=12, chunk=150)
     assert np.isfinite(iters.min(axis=1)).all()
     y, _ = L.labels(iters)
     m, losses = L.train(feats, y, steps=800)
     assert losses[-1] < 0.5 * losses[0]
-    return m
+    return m, L.most_frequent_setting(iters)
 
 
-def test_learned_interval_beats_fallback(model):
+@pytest.fixture(scope="module")
+def model(trained):
+    return trained[0]
+
+
+def test_learned_interval_beats_fallback(trained):
+    """On held-out instances the predicted intervals need fewer iterations
+    than the Lanczos interval with the 10/kappa rule; the most frequent sweep
+    label used as one constant setting for all instances is reported beside
+    them (the MLP is only required not to lose to it by more than 5%: the
+    labels of this small training sweep are dominated by that setting)."""
+    model, fixed = trained
     specs = I.batch_specs(12, seed=12, nmin=16, nmax=40)
-    res = L.evaluate(specs, model, k=12, apply_prec="f64")
-    assert res["fallback"]["converged"] == res["fallback"]["columns"]
-    assert res["mlp"]["converged"] == res["mlp"]["columns"]
+    res = L.evaluate(specs, model, k=12, apply_prec="f64", fixed=fixed)
+    for arm in ("fallback", "fixed", "mlp"):
+        assert res[arm]["converged"] == res[arm]["columns"]
+    print("iterations mean: fallback %.1f, fixed %s %.1f, mlp %.1f" % (
+        res["fallback"]["iterations_mean"], fixed, res["fixed"]["iterations_mean"], res["mlp"]["iterations_mean"]))
     assert res["mlp"]["iterations_mean"] < 0.9 * res["fallback"]["iterations_mean"]
+    assert res["mlp"]["iterations_mean"] <= 1.05 * res["fixed"]["iterations_mean"]
 
 
 def test_predicted_interval_solve_matches_oracle(model):
