@@ -24,6 +24,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "driver.cuh"
@@ -308,6 +309,142 @@ __device__ __forceinline__ void b_cheb_slice(const BatchDev& d, long long s, int
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if ((act >> r) & 1u) y[e0 + r] = out[r];
+}
+
+// DIA mode with 3 stored diagonals (the 7-point stencil), kBChunk slices of
+// one instance per warp work item: the instance's metadata and column
+// coefficients are read once per item instead of once per slice, and each
+// lane walks kBChunk rows (row0 + lane + 32 q).  Stored diagonals stream with
+// an evict-first L2 priority, r (read by every step) with evict-last.
+constexpr int kBChunk = 4;
+
+__device__ __forceinline__ uint64_t b_policy(bool last) {
+  uint64_t pol;
+  if (last)
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  else
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_pol(const T* p, uint64_t pol) {
+  if constexpr (std::is_same<T, double>::value) {
+    double v;
+    asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+  } else {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+  }
+}
+
+template <typename TV, typename TX, int R, int MODE>
+__device__ __forceinline__ void b_cheb_dia3_chunk(const BatchDev& d, int i, long long row0, const TV* val,
+                                                  const TX* x, const TX* xold, const TX* rin, TX* y,
+                                                  const double* coef, unsigned act, uint64_t pol_first,
+                                                  uint64_t pol_last) {
+  const int lane = threadIdx.x & 31;
+  const long long vo = d.voff[i];
+  const TX* xi = x + vo;
+  const long long base = d.dia_base[i] + d.dia_pad[i];
+  const long long str = d.dia_stride[i];
+  const long long last = (d.sbase[i + 1] - d.sbase[i]) * 32 - 1;
+  const long long o[3] = {d.dia_off[i * kBDiag], d.dia_off[i * kBDiag + 1], d.dia_off[i * kBDiag + 2]};
+  const double* cf0 = coef + (long long)d.cbase[i] * 3;
+#pragma unroll 1
+  for (int q = 0; q < kBChunk; ++q) {
+    const long long row = row0 + lane + 32 * q;
+    TX acc[R];
+    {
+      RowVec<TX, R> xs0;
+      xs0.load(xi + row * R);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = xs0.v[r];  // the unit diagonal
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const TV* U = val + base + t * str;
+      const TX up = (TX)ld_pol<TV>(U + row, pol_first);
+      const TX lo = (TX)ld_pol<TV>(U + row - o[t], pol_first);
+      const long long ju = row + o[t] < last ? row + o[t] : last;
+      const long long jl = row - o[t] > 0 ? row - o[t] : 0;
+      RowVec<TX, R> xu, xl;
+      xu.load(xi + ju * R);
+      xl.load(xi + jl * R);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = fma(up, xu.v[r], fma(lo, xl.v[r], acc[r]));
+    }
+    const long long e0 = vo + row * R;
+    TX rs[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) rs[r] = ld_pol<TX>(rin + e0 + r, pol_last);
+    RowVec<TX, R> xs, xo;
+    if (MODE != kCheb1) xs.load(x + e0);
+    if (MODE == kChebK) xo.load(xold + e0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const TX ca = (TX)__ldg(cf0 + 3 * r), cb = (TX)__ldg(cf0 + 3 * r + 1), cc = (TX)__ldg(cf0 + 3 * r + 2);
+      TX out;
+      if (MODE == kCheb1)
+        out = fma(cb, acc[r], ca * rs[r]);
+      else if (MODE == kCheb2)
+        out = fma(cc, rs[r] - acc[r], fma(cb, rs[r], ca * xs.v[r]));
+      else
+        out = fma(cc, rs[r] - acc[r], fma(cb, xo.v[r], ca * xs.v[r]));
+      if ((act >> r) & 1u) y[e0 + r] = out;
+    }
+  }
+}
+
+template <typename TV, typename TX, int MODE>
+__global__ void __launch_bounds__(kBlock, std::is_same<TX, float>::value ? 3 : 2) b_cheb_dia3_kernel(BatchDev d, const TV* __restrict__ val,
+                                                             const TX* __restrict__ x, const TX* __restrict__ xold,
+                                                             const TX* __restrict__ rin, TX* __restrict__ y,
+                                                             const int* __restrict__ done,
+                                                             const double* __restrict__ coef) {
+  const uint64_t pol_first = b_policy(false), pol_last = b_policy(true);
+  const long long nchunks = (d.nslices + kBChunk - 1) / kBChunk;
+  for (long long c = bgw(); c < nchunks; c += bnw()) {
+    const long long s0 = c * kBChunk;
+    const long long s1 = s0 + kBChunk <= d.nslices ? s0 + kBChunk : d.nslices;
+    const int i = d.s_inst[s0];
+    const int R = d.R[i];
+    const unsigned act = active_mask(done, d.cbase[i], R);
+    const bool whole = s1 - s0 == kBChunk && d.s_inst[s1 - 1] == i && d.dia_nd[i] == 3;
+    if (!whole) {  // an item that spans instances (or is short): slice by slice
+      for (long long s = s0; s < s1; ++s) {
+        const int is = d.s_inst[s];
+        const int Rs = d.R[is];
+        const unsigned as = active_mask(done, d.cbase[is], Rs);
+        if (!as) continue;
+        switch (Rs) {
+          case 1: b_cheb_slice<TV, TX, 1, MODE>(d, s, is, val, x, xold, rin, y, coef, as); break;
+          case 2: b_cheb_slice<TV, TX, 2, MODE>(d, s, is, val, x, xold, rin, y, coef, as); break;
+          case 3: b_cheb_slice<TV, TX, 3, MODE>(d, s, is, val, x, xold, rin, y, coef, as); break;
+          case 4: b_cheb_slice<TV, TX, 4, MODE>(d, s, is, val, x, xold, rin, y, coef, as); break;
+          case 5: b_cheb_slice<TV, TX, 5, MODE>(d, s, is, val, x, xold, rin, y, coef, as); break;
+          case 6: b_cheb_slice<TV, TX, 6, MODE>(d, s, is, val, x, xold, rin, y, coef, as); break;
+          case 7: b_cheb_slice<TV, TX, 7, MODE>(d, s, is, val, x, xold, rin, y, coef, as); break;
+          default: b_cheb_slice<TV, TX, 8, MODE>(d, s, is, val, x, xold, rin, y, coef, as); break;
+        }
+      }
+      continue;
+    }
+    if (!act) continue;
+    const long long row0 = d.s_row0[s0];
+    switch (R) {
+      case 1: b_cheb_dia3_chunk<TV, TX, 1, MODE>(d, i, row0, val, x, xold, rin, y, coef, act, pol_first, pol_last); break;
+      case 2: b_cheb_dia3_chunk<TV, TX, 2, MODE>(d, i, row0, val, x, xold, rin, y, coef, act, pol_first, pol_last); break;
+      case 3: b_cheb_dia3_chunk<TV, TX, 3, MODE>(d, i, row0, val, x, xold, rin, y, coef, act, pol_first, pol_last); break;
+      case 4: b_cheb_dia3_chunk<TV, TX, 4, MODE>(d, i, row0, val, x, xold, rin, y, coef, act, pol_first, pol_last); break;
+      case 5: b_cheb_dia3_chunk<TV, TX, 5, MODE>(d, i, row0, val, x, xold, rin, y, coef, act, pol_first, pol_last); break;
+      case 6: b_cheb_dia3_chunk<TV, TX, 6, MODE>(d, i, row0, val, x, xold, rin, y, coef, act, pol_first, pol_last); break;
+      case 7: b_cheb_dia3_chunk<TV, TX, 7, MODE>(d, i, row0, val, x, xold, rin, y, coef, act, pol_first, pol_last); break;
+      default: b_cheb_dia3_chunk<TV, TX, 8, MODE>(d, i, row0, val, x, xold, rin, y, coef, act, pol_first, pol_last); break;
+    }
+  }
 }
 
 template <typename TV, typename TX, int MODE>
@@ -970,37 +1107,46 @@ cudaError_t b_vec(pp_batch_state* B, const double* bin, double* xout, int first,
 cudaError_t b_cheb_steps(pp_batch_state* B, cudaStream_t s) {
   const BatchDev& d = B->d;
   const int k = d.k;
-  const int g = grid_b(d.nslices);
+  // DIA: work items of kBChunk slices; SELL: one slice per warp
+  const int g = d.dia ? grid_b((d.nslices + kBChunk - 1) / kBChunk) : grid_b(d.nslices);
   cudaError_t e = cudaSuccess;
+  auto step = [&](auto tv, auto tx, const auto* val, const auto* xin, const auto* xo, const auto* rin, auto* yout,
+                  int mode, const double* cj) {
+    using TV = std::remove_cv_t<std::remove_pointer_t<decltype(tv)>>;
+    using TX = std::remove_cv_t<std::remove_pointer_t<decltype(tx)>>;
+    const TV* v = reinterpret_cast<const TV*>(val);
+    if (d.dia) {
+      if (mode == kCheb1) b_cheb_dia3_kernel<TV, TX, kCheb1><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+      else if (mode == kCheb2) b_cheb_dia3_kernel<TV, TX, kCheb2><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+      else b_cheb_dia3_kernel<TV, TX, kChebK><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+    } else {
+      if (mode == kCheb1) b_cheb_kernel<TV, TX, kCheb1><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+      else if (mode == kCheb2) b_cheb_kernel<TV, TX, kCheb2><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+      else b_cheb_kernel<TV, TX, kChebK><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+    }
+    return cudaGetLastError();
+  };
   if (B->apply_prec == PP_PREC_F32) {
     float* buf[3] = {B->u32, B->v32, B->z32};
     const int off = ((2 - k) % 3 + 3) % 3;
     auto Y = [&](int j) { return buf[(j + off) % 3]; };
+    const float* val = d.dia ? d.dval32 : d.val32;
     for (int j = 1; j <= k && e == cudaSuccess; ++j) {
       const double* cj = B->coefT + (size_t)j * d.ncols * 3;
-      if (j == 1)
-        b_cheb_kernel<float, float, kCheb1><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval32 : d.val32, B->r32, nullptr, B->r32, Y(1), B->c.done, cj);
-      else if (j == 2)
-        b_cheb_kernel<float, float, kCheb2><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval32 : d.val32, Y(1), nullptr, B->r32, Y(2), B->c.done, cj);
-      else
-        b_cheb_kernel<float, float, kChebK><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval32 : d.val32, Y(j - 1), Y(j - 2), B->r32, Y(j), B->c.done,
-                                                               cj);
-      e = cudaGetLastError();
+      if (j == 1) e = step((float*)nullptr, (float*)nullptr, val, B->r32, (const float*)nullptr, B->r32, Y(1), kCheb1, cj);
+      else if (j == 2) e = step((float*)nullptr, (float*)nullptr, val, Y(1), (const float*)nullptr, B->r32, Y(2), kCheb2, cj);
+      else e = step((float*)nullptr, (float*)nullptr, val, Y(j - 1), Y(j - 2), B->r32, Y(j), kChebK, cj);
     }
   } else {
     double* buf[3] = {B->t1, B->t2, B->z};
     const int off = ((2 - k) % 3 + 3) % 3;
     auto Y = [&](int j) { return buf[(j + off) % 3]; };
+    const double* val = d.dia ? d.dval64 : d.val64;
     for (int j = 1; j <= k && e == cudaSuccess; ++j) {
       const double* cj = B->coefT + (size_t)j * d.ncols * 3;
-      if (j == 1)
-        b_cheb_kernel<double, double, kCheb1><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval64 : d.val64, B->r, nullptr, B->r, Y(1), B->c.done, cj);
-      else if (j == 2)
-        b_cheb_kernel<double, double, kCheb2><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval64 : d.val64, Y(1), nullptr, B->r, Y(2), B->c.done, cj);
-      else
-        b_cheb_kernel<double, double, kChebK><<<g, kBlock, 0, s>>>(d, d.dia ? d.dval64 : d.val64, Y(j - 1), Y(j - 2), B->r, Y(j),
-                                                                 B->c.done, cj);
-      e = cudaGetLastError();
+      if (j == 1) e = step((double*)nullptr, (double*)nullptr, val, B->r, (const double*)nullptr, B->r, Y(1), kCheb1, cj);
+      else if (j == 2) e = step((double*)nullptr, (double*)nullptr, val, Y(1), (const double*)nullptr, B->r, Y(2), kCheb2, cj);
+      else e = step((double*)nullptr, (double*)nullptr, val, Y(j - 1), Y(j - 2), B->r, Y(j), kChebK, cj);
     }
   }
   return e;
