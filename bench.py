@@ -131,6 +131,7 @@ def fp64_peak_tflops() -> float:
 KERNEL_SOURCES = {
     "dia": ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_dia.cuh", "step_dia.cu"),
     "dia_tma": ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_dia.cuh", "step_dia_tma.cu"),
+    "dia_z": ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_dia.cuh", "step_dia_z.cu"),
     "sell": ("common.cuh", "kernels.cuh", "step_impl.cuh", "step_f64.cu", "step_lp.cu"),
 }
 
@@ -592,7 +593,8 @@ def main():
     ap.add_argument("--workload", default="diffusion192", choices=list(WORKLOADS))
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--graphs", type=int, default=-1, help="CUDA graphs for PCG blocks (default: per workload)")
-    ap.add_argument("--sell-variant", type=int, default=0, help="0 auto, 1 direct loads, 2 TMA-staged")
+    ap.add_argument("--sell-variant", type=int, default=0,
+                    help="0 auto, 1 direct loads, 2 TMA-staged, 3 plane marching (FP32/BF16 DIA)")
     ap.add_argument("--sell-C", type=int, default=0)
     ap.add_argument("--sell-sigma", type=int, default=0)
     ap.add_argument("--check-every", type=int, default=0, help="PCG iterations per host check (default: per workload)")
@@ -805,7 +807,7 @@ def layout_name(info, variant, prec="f64") -> str:
     if info["format"] == 2:
         return f"SELL C={info['sell_C']} sigma={info['sell_sigma']} {'direct' if variant == 1 else 'tma'}"
     if info["format"] == 3:
-        return f"DIA ndiag={info['ndiag']}" + (" tma" if prec != "f64" and variant == 2 else "")
+        return f"DIA ndiag={info['ndiag']}" + ({2: " tma", 3: " z-march"}.get(variant, "") if prec != "f64" else "")
     return "CSR"
 
 
@@ -832,9 +834,9 @@ def step_roofline(info, stats, A, k, prec, workload, variant, fp64_peak):
     peak, peak_src = measured_peak()
     ach = bpl / avg_s / 1e9
     layout = layout_name(info, variant, prec)
-    dia_tma = prec != "f64" and variant == 2
+    dia_kind = {2: "tma_", 3: "z_"}.get(variant, "") if prec != "f64" else ""
     kname = {2: f"sell_step_{'tma_' if variant != 1 else ''}kernel ({prec}, C={info['sell_C']})",
-             3: f"dia_step_{'tma_' if dia_tma else ''}kernel ({prec}, {info['ndiag']} stored diagonals)",
+             3: f"dia_step_{dia_kind}kernel ({prec}, {info['ndiag']} stored diagonals)",
              1: f"csr_step_kernel ({prec})"}[info["format"]]
     tr = traffic_from_profile(workload, k, prec, layout)
     hbm = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),

@@ -108,8 +108,12 @@ typedef struct {
                          1 direct global loads, 2 staged in shared memory by
                          bulk copies (TMA) completing on mbarriers -- SELL
                          slices, and the FP32/BF16 steps on a Jacobi-scaled
-                         3-diagonal (7-point) DIA matrix.  Auto stages SELL
-                         slices and loads DIA rows directly              */
+                         3-diagonal (7-point) DIA matrix; 3 (DIA FP32/BF16
+                         on an Nx x Ny x Nz grid, Nx even) walks z through
+                         tiles of grid columns, keeping the z-neighbours in
+                         registers.  Auto stages SELL slices and walks z
+                         for FP32/BF16 DIA where the grid allows it (direct
+                         loads otherwise); pp_autotune tries them all      */
   int lowrank;        /* p in [0, 32]: low-rank acceleration of Section 3.1,
                          P_hat = p_k(A_hat) + V (V^T A_hat V)^{-1} V^T with V
                          the Ritz vectors of the p smallest Ritz values of

@@ -147,7 +147,7 @@ int validate_options(pp_ctx* c, const pp_options* o) {
   if (!(o->rtol >= 0.0)) return fail(c, PP_EINVAL, "rtol must be >= 0");
   if (o->check_every < 0 || o->check_every > kMaxCheck) return fail(c, PP_EINVAL, "check_every must be in [0, 64]");
   if (o->sell_sigma < 0) return fail(c, PP_EINVAL, "sell_sigma must be >= 0");
-  if (o->sell_variant < 0 || o->sell_variant > 2) return fail(c, PP_EINVAL, "sell_variant must be 0, 1 or 2");
+  if (o->sell_variant < 0 || o->sell_variant > 3) return fail(c, PP_EINVAL, "sell_variant must be in [0, 3]");
   if (o->lowrank < 0 || o->lowrank > kMaxLowRank) return fail(c, PP_EINVAL, "lowrank must be in [0, 32]");
   if (o->flexible < 0 || o->flexible > kMaxFcg) return fail(c, PP_EINVAL, "flexible must be in [0, 8]");
   if (o->poly != PP_POLY_CHEB && o->poly != PP_POLY_NEWTON) return fail(c, PP_EINVAL, "poly must be CHEB or NEWTON");
@@ -311,9 +311,10 @@ void init_desc(pp_ctx* c, const pp_csr* A, const SellPlan& P, const DiaPlan& D) 
     for (int t = 0; t < kMaxDiag; ++t) c->A64.doff[t] = t < D.nd - unit ? D.doff[t + unit] : 0;
     c->A64.dpad = D.dpad;
     c->A64.dstride = D.dpad + c->n_pad;
-    // FP32/BF16 steps on the 7-point stencil: TMA-staged tiles when asked
-    // for (sell_variant = 2); direct loads otherwise
-    c->A64.tma = c->opt.sell_variant == 2;
+    // FP32/BF16 steps on the 7-point stencil: direct loads (1), TMA-staged
+    // tiles (2) or plane marching (3, and auto where the grid structure
+    // allows it: measured fastest)
+    c->A64.tma = c->opt.sell_variant == 0 ? 3 : c->opt.sell_variant;
     c->nnz_pad = (long long)std::max(1, D.nd - unit) * c->A64.dstride;
   } else if (c->A64.format == PP_FMT_SELL) {
     c->A64.C = P.C;

@@ -33,7 +33,8 @@ struct Scalars {
   int flexible;
   int lan_steps;   // Lanczos steps completed without breakdown
   int dev_error;   // 1: a bounded wait inside a kernel expired (PP_ETIMEOUT)
-  int pad_;
+  int x_pending;   // 1: the solve stopped after an r update whose x update (fused
+                   // into the next first degree step) did not run
   unsigned int counters[8];
   double fcg_pq[kMaxFcg];  // FCG(m): (p_j, A p_j) of the directions in the window, by ring slot
   double fcg_zq[kMaxFcg];  // FCG(m): (z, A p_j) of the latest preconditioned residual, by ring slot

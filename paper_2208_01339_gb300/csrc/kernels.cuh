@@ -49,7 +49,8 @@ struct MatDesc {
   const int* rowptr;     // CSR only
   int csr_group;         // CSR: lanes per row (1, 8, 32)
   int prec;
-  int tma;               // SELL: stage slices through shared memory with cp.async.bulk
+  int tma;               // SELL: stage slices through shared memory with cp.async.bulk;
+                         // DIA FP32/BF16: 2 TMA-staged tiles, 3 plane marching
   // DIA (symmetric; rows in natural order): the stored diagonals t =
   // 0..ndiag-1 at offsets doff[t] -- the main diagonal (doff[0] = 0) and the
   // upper ones, or, with dia_unit = 1 (Jacobi-scaled matrix, whose diagonal
@@ -116,10 +117,15 @@ cudaError_t vec_scale_out(const VecLaunch& L, long long n, const double* w, cons
 // xh[i] = x[perm ? perm[i] : i] / w[i]
 cudaError_t vec_unscale_in(const VecLaunch& L, long long n, long long n_pad, const double* w, const int* perm,
                            const double* x, double* xh);
-// PCG updates (device scalars in sc).
+// PCG updates (device scalars in sc).  vec_update_xr with x = nullptr
+// updates r only and leaves x += alpha p to vec_update_p (given x), which
+// reads p anyway; x_pending is set when the solve stops in between, and
+// vec_finish_x applies that pending update.
 cudaError_t vec_update_xr(const VecLaunch& L, long long n, Scalars* sc, double* x, double* r, const double* p,
                           const double* q);
-cudaError_t vec_update_p(const VecLaunch& L, long long n, Scalars* sc, const double* z, double* p, int first);
+cudaError_t vec_finish_x(const VecLaunch& L, long long n, const Scalars* sc, double* x, const double* p);
+cudaError_t vec_update_p(const VecLaunch& L, long long n, Scalars* sc, const double* z, double* p, int first,
+                         double* x = nullptr);
 cudaError_t pcg_init(Scalars* sc, double rtol, int maxit, int flexible, cudaStream_t s);
 // z = double(z32); (r, z) -> sc->rz_new, (q, z) -> sc->zq when q != nullptr.
 cudaError_t vec_from32_dot(const VecLaunch& L, long long n, const Scalars* skip, const float* z32, double* z,

@@ -79,6 +79,13 @@ cudaError_t cheb_core(pp_ctx* c, const Scalars* skip, const void* rin, void* zou
   return cudaSuccess;
 }
 
+// The PCG update x += alpha p runs in the p update of the same iteration
+// (p = z + beta p reads p already) instead of in the r update, which saves
+// one vector read per iteration; a solve that stops right after an r update
+// applies the pending x update at its end.  FCG(m), m >= 2, keeps its own
+// p update and the plain x update.
+bool fuse_x_update(const pp_ctx* c) { return c->fcg_m == 0; }
+
 // z = p_k(A_hat) r on the internal FP64 vectors r, z, with (r, z) -> rz_new
 // and, for flexible CG, (q, z) -> zq.  With a low-rank correction in use
 // (Section 3.1) c = G^{-1} V^T r is formed first and z += V c, fused with
@@ -110,7 +117,8 @@ cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s, cudaEvent_t 
     if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   } else if (!c->mixed) {
     if (ev0) e = cudaEventRecord(ev0, s);
-    if (e == cudaSuccess) e = cheb_core(c, skip, c->r, c->z, nd, rz, qd, &sc->zq, s);
+    if (e == cudaSuccess)
+      e = cheb_core(c, skip, c->r, c->z, nd, rz, qd, &sc->zq, s);
     if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   } else {
     e = vec_convert(L, c->n, c->r, kF64, c->r32, kF32, skip);
@@ -174,13 +182,14 @@ cudaError_t pcg_iteration(pp_ctx* c, cudaStream_t s, cudaEvent_t ev0, cudaEvent_
   p.y = qv;
   p.dot_out0 = &sc->pq;
   cudaError_t e = op_step(c, false, p, sc, &sc->counters[kCntStep], s);
-  if (e == cudaSuccess) e = vec_update_xr(L, c->n, sc, c->xh, c->r, pv, qv);
+  const bool fuse = fuse_x_update(c);
+  if (e == cudaSuccess) e = vec_update_xr(L, c->n, sc, fuse ? nullptr : c->xh, c->r, pv, qv);
   if (e == cudaSuccess) e = precond(c, sc, s, ev0, ev1);
   if (m) {
     if (e == cudaSuccess) e = fcg_dots(c, s_cur, s);
     if (e == cudaSuccess) e = fcg_update_p(c, s_cur, (b + 1) % m, 0, s);
   } else if (e == cudaSuccess) {
-    e = vec_update_p(L, c->n, sc, c->z, c->p, 0);
+    e = vec_update_p(L, c->n, sc, c->z, c->p, 0, fuse ? c->xh : nullptr);
   }
   return e;
 }
@@ -493,7 +502,12 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
     iter_before = host[2];
     if (host[0]) break;
   }
-  e = vec_scale_out(L, c->n, c->w, c->perm, c->xh, kF64, x, 0);
+  e = cudaSuccess;
+  if (fuse_x_update(c)) {
+    e = vec_finish_x(L, c->n, sc, c->xh, c->p);
+    launches += 1;
+  }
+  if (e == cudaSuccess) e = vec_scale_out(L, c->n, c->w, c->perm, c->xh, kF64, x, 0);
   if (e == cudaSuccess) e = cudaEventRecord(ev_end, s);
   double rr = 0.0, bb = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&rr, &sc->rr, sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -135,22 +135,22 @@ template <typename TV>
 __device__ __forceinline__ void ld2_hint(const TV* p, float (&o)[2], uint64_t pol) {
   if constexpr (std::is_same<TV, __nv_bfloat16>::value) {
     unsigned int u;
-    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(u) : "l"(p), "l"(pol));
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(u) : "l"(p), "l"(pol));
     o[0] = bf16_lo(u);
     o[1] = bf16_hi(u);
   } else {
-    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(o[0]), "=f"(o[1]) : "l"(p), "l"(pol));
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(o[0]), "=f"(o[1]) : "l"(p), "l"(pol));
   }
 }
 template <typename TV>
 __device__ __forceinline__ float ld1_hint(const TV* p, uint64_t pol) {
   if constexpr (std::is_same<TV, __nv_bfloat16>::value) {
     unsigned short u;
-    asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(u) : "l"(p), "l"(pol));
+    asm("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(u) : "l"(p), "l"(pol));
     return __uint_as_float(((unsigned int)u) << 16);
   } else {
     float v;
-    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
     return v;
   }
 }
@@ -322,7 +322,8 @@ cudaError_t go_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, dou
   } else {
     if constexpr (std::is_same<TX, float>::value && NDOT == 0 &&
                   (MODE == kCheb1 || MODE == kCheb2 || MODE == kChebK)) {
-      if (A.tma && dia_tma_applies(A)) return launch_step_dia_tma(A, p, sc, grid, s);
+      if (A.tma == 2 && dia_tma_applies(A)) return launch_step_dia_tma(A, p, sc, grid, s);
+      if (A.tma == 3 && dia_z_applies(A)) return launch_step_dia_z(A, p, sc, s);
     }
     constexpr int R = std::is_same<TX, double>::value ? 4 : 2;
     const TV* v = static_cast<const TV*>(A.val);

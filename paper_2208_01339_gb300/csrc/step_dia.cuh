@@ -36,4 +36,14 @@ inline bool dia_tma_applies(const MatDesc& A) {
 // FP32 vectors, TMA-staged; A must satisfy dia_tma_applies.
 cudaError_t launch_step_dia_tma(const MatDesc& A, const StepParams& p, const Scalars* sc, int grid, cudaStream_t s);
 
+// The plane-marching FP32/BF16 step (step_dia_z.cu) applies to the Jacobi-
+// scaled matrix of a structured Nx x Ny x Nz grid: upper offsets 1, Nx and
+// Nx*Ny with Nx even, and n = Nx*Ny*Nz.
+inline bool dia_z_applies(const MatDesc& A) {
+  if (A.ndiag != 3 || !A.dia_unit || A.prec == kF64 || A.doff[0] != 1 || A.doff[1] < 2 || (A.doff[1] & 1)) return false;
+  if (A.doff[2] % A.doff[1] != 0 || A.doff[2] <= A.doff[1]) return false;
+  return (long long)A.n % A.doff[2] == 0 && (long long)A.n / A.doff[2] >= 1;
+}
+cudaError_t launch_step_dia_z(const MatDesc& A, const StepParams& p, const Scalars* sc, cudaStream_t s);
+
 }  // namespace pp

@@ -27,9 +27,10 @@ std::vector<Candidate> candidates(int apply_prec) {
   std::vector<Candidate> out;
   if (apply_prec == PP_PREC_F64) {
     out.push_back({PP_FMT_DIA, 0, 0, 0});
-  } else {  // FP32/BF16 DIA steps: direct loads or TMA-staged tiles
+  } else {  // FP32/BF16 DIA steps: direct loads, TMA-staged tiles, plane marching
     out.push_back({PP_FMT_DIA, 0, 0, 1});
     out.push_back({PP_FMT_DIA, 0, 0, 2});
+    out.push_back({PP_FMT_DIA, 0, 0, 3});
   }
   for (int C : {32, 64, 128})
     for (int sigma : {0, 1024})

@@ -48,8 +48,11 @@ __global__ void __launch_bounds__(kBlock) unscale_in_kernel(long long n, long lo
   for (long long i = gtid(); i < n_pad; i += gstride()) xh[i] = i < n ? x[perm ? perm[i] : i] / w[i] : 0.0;
 }
 
-// x += alpha p, r -= alpha q with alpha = (r,z)/(p,q); ||r||^2 and the
-// stopping test (rtol, maxit) are evaluated by the last block.
+// x += alpha p (UPD_X) and r -= alpha q with alpha = (r,z)/(p,q); ||r||^2
+// and the stopping test (rtol, maxit) are evaluated by the last block.
+// Without UPD_X the x update runs in the p update of the same iteration,
+// which reads p anyway, and x_pending records a stop before it ran.
+template <bool UPD_X>
 __global__ void __launch_bounds__(kBlock) update_xr_kernel(long long n2, Scalars* sc, double2* __restrict__ x,
                                                            double2* __restrict__ r, const double2* __restrict__ p,
                                                            const double2* __restrict__ q, double* partials) {
@@ -60,12 +63,15 @@ __global__ void __launch_bounds__(kBlock) update_xr_kernel(long long n2, Scalars
   if (!bad) {
     const double alpha = rz / pq;
     for (long long i = gtid(); i < n2; i += gstride()) {
-      double2 xi = x[i], pi = p[i], ri = r[i], qi = __ldcs(q + i);
-      xi.x += alpha * pi.x;
-      xi.y += alpha * pi.y;
+      double2 ri = r[i], qi = __ldcs(q + i);
+      if constexpr (UPD_X) {
+        double2 xi = x[i], pi = p[i];
+        xi.x += alpha * pi.x;
+        xi.y += alpha * pi.y;
+        x[i] = xi;
+      }
       ri.x -= alpha * qi.x;
       ri.y -= alpha * qi.y;
-      x[i] = xi;
       r[i] = ri;
       acc[0] += ri.x * ri.x + ri.y * ri.y;
     }
@@ -84,26 +90,52 @@ __global__ void __launch_bounds__(kBlock) update_xr_kernel(long long n2, Scalars
       } else if (rr <= sc->rtol2) {
         sc->done = 1;
         sc->status = 0;
+        if (!UPD_X) sc->x_pending = 1;
       } else if (sc->iter >= sc->maxit) {
         sc->done = 1;
         sc->status = 1;
+        if (!UPD_X) sc->x_pending = 1;
       }
     }
   }
 }
 
+// The x update the stop left pending: x += alpha p with the last alpha.
+__global__ void __launch_bounds__(kBlock) finish_x_kernel(long long n2, const Scalars* sc, double2* __restrict__ x,
+                                                          const double2* __restrict__ p) {
+  if (!*reinterpret_cast<const volatile int*>(&sc->x_pending)) return;
+  const double alpha = sc->rz / sc->pq;
+  for (long long i = gtid(); i < n2; i += gstride()) {
+    double2 xi = x[i];
+    const double2 pi = p[i];
+    xi.x += alpha * pi.x;
+    xi.y += alpha * pi.y;
+    x[i] = xi;
+  }
+}
+
 // p = z + beta p; beta = (r,z)_new/(r,z) (plain) or -(z_new,q)/(p,q)
 // (flexible, FCG(1)); first = 1 gives p = z.
+template <bool UPD_X>
 __global__ void __launch_bounds__(kBlock) update_p_kernel(long long n2, Scalars* sc, const double2* __restrict__ z,
-                                                          double2* __restrict__ p, int first) {
+                                                          double2* __restrict__ p, double2* __restrict__ x, int first) {
   if (load_done(sc)) return;
   const double rzn = sc->rz_new;
   const bool bad = !(rzn > 0.0) || !isfinite(rzn);
   double beta = 0.0;
   if (!first) beta = sc->flexible ? -sc->zq / sc->pq : rzn / sc->rz;
+  // with UPD_X, the x update of this iteration (alpha = (r,z)/(p,q) with the
+  // direction p before it changes)
+  const double alpha = UPD_X ? sc->rz / sc->pq : 0.0;
   if (!bad) {
     for (long long i = gtid(); i < n2; i += gstride()) {
       double2 zi = __ldcs(z + i), pi = p[i];
+      if constexpr (UPD_X) {
+        double2 xi = x[i];
+        xi.x += alpha * pi.x;
+        xi.y += alpha * pi.y;
+        x[i] = xi;
+      }
       pi.x = zi.x + beta * pi.x;
       pi.y = zi.y + beta * pi.y;
       p[i] = pi;
@@ -113,6 +145,8 @@ __global__ void __launch_bounds__(kBlock) update_p_kernel(long long n2, Scalars*
     if (bad) {
       sc->done = 1;
       sc->status = isfinite(rzn) ? -2 : -3;
+      // the pending x update (UPD_X) is still valid: alpha came from (p,q) > 0
+      if (UPD_X) sc->x_pending = 1;
     } else {
       sc->rz = rzn;
     }
@@ -121,6 +155,7 @@ __global__ void __launch_bounds__(kBlock) update_p_kernel(long long n2, Scalars*
 
 __global__ void pcg_init_kernel(Scalars* sc, double rtol, int maxit, int flexible) {
   sc->done = 0;
+  sc->x_pending = 0;
   sc->status = 1;
   sc->iter = 0;
   sc->maxit = maxit;
@@ -295,13 +330,28 @@ cudaError_t vec_unscale_in(const VecLaunch& L, long long n, long long n_pad, con
 
 cudaError_t vec_update_xr(const VecLaunch& L, long long n, Scalars* sc, double* x, double* r, const double* p,
                           const double* q) {
-  update_xr_kernel<<<L.grid, kBlock, 0, L.s>>>((n + 1) / 2, sc, (double2*)x, (double2*)r, (const double2*)p,
-                                               (const double2*)q, L.partials);
+  if (x)
+    update_xr_kernel<true><<<L.grid, kBlock, 0, L.s>>>((n + 1) / 2, sc, (double2*)x, (double2*)r, (const double2*)p,
+                                                       (const double2*)q, L.partials);
+  else
+    update_xr_kernel<false><<<L.grid, kBlock, 0, L.s>>>((n + 1) / 2, sc, nullptr, (double2*)r, (const double2*)p,
+                                                        (const double2*)q, L.partials);
   return cudaGetLastError();
 }
 
-cudaError_t vec_update_p(const VecLaunch& L, long long n, Scalars* sc, const double* z, double* p, int first) {
-  update_p_kernel<<<L.grid, kBlock, 0, L.s>>>((n + 1) / 2, sc, (const double2*)z, (double2*)p, first);
+cudaError_t vec_finish_x(const VecLaunch& L, long long n, const Scalars* sc, double* x, const double* p) {
+  finish_x_kernel<<<L.grid, kBlock, 0, L.s>>>((n + 1) / 2, sc, (double2*)x, (const double2*)p);
+  return cudaGetLastError();
+}
+
+cudaError_t vec_update_p(const VecLaunch& L, long long n, Scalars* sc, const double* z, double* p, int first,
+                         double* x) {
+  if (x)
+    update_p_kernel<true><<<L.grid, kBlock, 0, L.s>>>((n + 1) / 2, sc, (const double2*)z, (double2*)p, (double2*)x,
+                                                      first);
+  else
+    update_p_kernel<false><<<L.grid, kBlock, 0, L.s>>>((n + 1) / 2, sc, (const double2*)z, (double2*)p, nullptr,
+                                                       first);
   return cudaGetLastError();
 }
 

@@ -29,8 +29,8 @@ def test_autotune_picks_fastest_and_solves(prec):
     rp, ci, va = P.to_device_csr(A)
     base = dict(k=6, rtol=1e-10, apply_prec=prec, flexible=1 if prec != "f64" else 0)
     chosen, table = P.autotune(rp, ci, va, A.n, **base)
-    # CSR, DIA (FP32/BF16: direct and TMA-staged) and 12 SELL layouts
-    assert len(table) == (14 if prec == "f64" else 15)
+    # CSR, DIA (FP32/BF16: direct, TMA-staged, plane marching) and 12 SELL layouts
+    assert len(table) == (14 if prec == "f64" else 16)
     assert all(t["status"] == 0 and t["us_per_step"] > 0 for t in table)
     best = min(t["us_per_step"] for t in table)
     pick = next(t for t in table if t["us_per_step"] <= 1.03 * best)  # ties within 3%: first in order

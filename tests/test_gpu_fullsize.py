@@ -82,7 +82,7 @@ def test_dia_192_f64_three_pcg_iterations(diff192):
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_dia_192_low_precision_apply(diff192, prec, variant):
     A, b = diff192
     S = P.Solver.from_host(A, k=5, interval="given", alpha=ALPHA, beta=BETA, xi=XI, format="dia", apply_prec=prec,
@@ -135,7 +135,7 @@ def test_dia_128_pcg_fused_dots(diff128, flexible):
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("k", [1, 2, 5])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_dia_128_low_precision_apply(diff128, prec, k, variant):
     A, b = diff128
     S = P.Solver.from_host(A, k=k, interval="given", alpha=0.004, beta=2.0, xi=1e-3, format="dia", apply_prec=prec,

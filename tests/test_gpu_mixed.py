@@ -73,11 +73,12 @@ def test_mixed_apply_matches_rounded_oracle(prec, C, var, k):
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("k", [0, 1, 2, 7])
 @pytest.mark.parametrize("N", [16, 17, 18])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_mixed_dia_apply(prec, k, N, variant):
     """Direct loads (variant 1; offsets N, N^2 multiples of the rows per
-    thread or not) and TMA-staged tiles (variant 2; tile ends, ranges clipped
-    at both ends of the vectors, unaligned shifted starts)."""
+    thread or not), TMA-staged tiles (variant 2; tile ends, ranges clipped
+    at both ends of the vectors, unaligned shifted starts) and plane marching
+    (variant 3; even N, odd N falls back to direct loads)."""
     A = I.diffusion3d(N, 2.0, seed=1)
     S = P.Solver.from_host(A, k=k, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="dia", apply_prec=prec,
                            sell_variant=variant)
