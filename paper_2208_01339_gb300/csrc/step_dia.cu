@@ -323,7 +323,7 @@ cudaError_t go_dia(const MatDesc& A, const StepParams& p, const Scalars* sc, dou
     if constexpr (std::is_same<TX, float>::value && NDOT == 0 &&
                   (MODE == kCheb1 || MODE == kCheb2 || MODE == kChebK)) {
       if (A.tma == 2 && dia_tma_applies(A)) return launch_step_dia_tma(A, p, sc, grid, s);
-      if (A.tma == 3 && dia_z_applies(A)) return launch_step_dia_z(A, p, sc, s);
+      if (A.tma == 3 && dia_z_applies(A)) return launch_step_dia_z(A, p, sc, grid, s);
     }
     constexpr int R = std::is_same<TX, double>::value ? 4 : 2;
     const TV* v = static_cast<const TV*>(A.val);

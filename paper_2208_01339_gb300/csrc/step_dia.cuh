@@ -44,6 +44,9 @@ inline bool dia_z_applies(const MatDesc& A) {
   if (A.doff[2] % A.doff[1] != 0 || A.doff[2] <= A.doff[1]) return false;
   return (long long)A.n % A.doff[2] == 0 && (long long)A.n / A.doff[2] >= 1;
 }
-cudaError_t launch_step_dia_z(const MatDesc& A, const StepParams& p, const Scalars* sc, cudaStream_t s);
+// One degree step (kCheb1, kCheb2, kChebK) by plane marching; A must
+// satisfy dia_z_applies; grid_cap > 0 caps the blocks of the launch.
+cudaError_t launch_step_dia_z(const MatDesc& A, const StepParams& p, const Scalars* sc, int grid_cap,
+                              cudaStream_t s);
 
 }  // namespace pp

@@ -88,6 +88,35 @@ def test_mixed_dia_apply(prec, k, N, variant):
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("N", [66, 68])
+def test_mixed_dia_plane_marching_ragged_tiles(prec, N):
+    """Plane marching with two 64-wide tiles in x, the second one ragged:
+    N = 68 takes four grid columns per thread (16-row tiles in y), N = 66
+    two (8-row tiles)."""
+    A = I.diffusion3d(N, 2.0, seed=4)
+    S = P.Solver.from_host(A, k=5, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="dia", apply_prec=prec,
+                           sell_variant=3)
+    r = I.rhs_normal(A.n, 3)
+    z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
+    assert_close(z, oracle_apply_rounded(A, r, 0.05, 1.95, 1e-3, 5, prec), 2e-5)
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("N", [18, 20])
+@pytest.mark.parametrize("blocks", [1, 3])
+def test_mixed_dia_plane_marching_capped_grid(prec, N, blocks):
+    """max_blocks below the number of (tile, z chunk) items: the blocks walk
+    the items with a grid stride (two and four grid columns per thread)."""
+    A = I.diffusion3d(N, 2.0, seed=5)
+    S = P.Solver.from_host(A, k=7, interval="given", alpha=0.05, beta=1.95, xi=1e-3, format="dia", apply_prec=prec,
+                           sell_variant=3, max_blocks=blocks)
+    assert S.info()["grid_blocks"] <= blocks
+    r = I.rhs_normal(A.n, 6)
+    z = to_np(S.apply(torch.as_tensor(r, device="cuda")))
+    assert_close(z, oracle_apply_rounded(A, r, 0.05, 1.95, 1e-3, 7, prec), 2e-5)
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
 def test_mixed_csr_apply(prec):
     A = I.diffusion3d(9, 1.0, seed=2)
     S = P.Solver.from_host(A, k=6, interval="given", alpha=0.1, beta=1.9, xi=1e-3, format="csr", apply_prec=prec)
