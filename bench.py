@@ -367,6 +367,12 @@ def batch_step_bytes(specs, fmt: str, prec: str) -> float:
     return tot
 
 
+def batch_step_kernel(fmt: str, prec: str) -> str:
+    if fmt != "dia":
+        return "b_cheb_kernel"
+    return "b_cheb_z_kernel (plane marching)" if prec == "f32" else "b_cheb_dia3_kernel"
+
+
 def run_batch(args, w, specs, k, dev, world, rank):
     """Config-5 shape: many uneven instances with several RHS each, solved by
     the batched solver (FP32 p_k, FP64 flexible CG, CUDA graphs) in the
@@ -478,8 +484,8 @@ def run_batch(args, w, specs, k, dev, world, rank):
                "sequential_f64_s": t_seq, "speedup_vs_sequential_f64": t_seq / (ms / 1e3),
                "max_rel_diff_vs_f64": err, "iterations_f64_max": int(max(its64)),
                "interval_arms": arms,
-               "roofline": {"bound": "hbm", "kernel": f"{'b_cheb_dia3_kernel' if fmt == 'dia' else 'b_cheb_kernel'} ({w['prec']}, {fmt}), one degree step over "
-                                                      f"every column (rank 0's share)",
+               "roofline": {"bound": "hbm", "kernel": f"{batch_step_kernel(fmt, w['prec'])} ({w['prec']}, {fmt}), one degree step "
+                                                      f"over every column (rank 0's share)",
                             "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                             "traffic": None, "peak_source": peak_src, "avg_launch_us": round(step_us, 2),
                             "algorithmic_bytes_per_launch": int(bytes_step)},

@@ -34,6 +34,15 @@ namespace pp {
 constexpr int kBR = 8;     // maximum right-hand sides per instance
 constexpr int kBDiag = 8;  // DIA mode: stored upper diagonals per instance
 
+// One plane-marching work item: a 32 x 8 tile (x0, y0) of instance inst's
+// grid through planes [z0, z1).
+struct BZItem {
+  int inst, x0, y0;
+  unsigned short z0, z1;
+};
+constexpr int kBZTileX = 32, kBZTileY = 8;
+constexpr int kBZPlanes = 32;  // planes per item, at most
+
 struct BatchDev {
   int nb = 0;             // instances
   int ncols = 0;          // global columns
@@ -67,6 +76,12 @@ struct BatchDev {
   const long long* dia_pad = nullptr;
   const double* dval64 = nullptr;
   const float* dval32 = nullptr;
+  // DIA instances of a structured Nx x Ny x Nz grid (upper offsets 1, Nx,
+  // Nx*Ny; zmode[i] = 1) take the FP32 plane-marching step over zitem
+  // (b_cheb_z_kernel); the others the slice kernel
+  const int* zmode = nullptr;
+  const BZItem* zitem = nullptr;
+  long long nzitems = 0;
   // per-column coefficients
   const double* theta_bar = nullptr;
   const double* delta = nullptr;
@@ -105,6 +120,8 @@ struct pp_batch_state {
   std::vector<double> abx;   // host (alpha, beta, xi) per column
   std::vector<double> ritz;  // host: per instance, lanczos Ritz extremes and more
   int lanczos_steps = 0;
+  int nz_inst = 0;  // instances stepped by plane marching
+  long long zclass[4] = {0, 0, 0, 0};  // their item offsets per register class
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap = nullptr;
   int graph_block = 0;
@@ -398,7 +415,8 @@ __device__ __forceinline__ void b_cheb_dia3_chunk(const BatchDev& d, int i, long
   }
 }
 
-template <typename TV, typename TX, int MODE>
+// TZ: some instances are stepped by b_cheb_z_kernel and skipped here.
+template <typename TV, typename TX, int MODE, bool TZ>
 __global__ void __launch_bounds__(kBlock, std::is_same<TX, float>::value ? 3 : 2) b_cheb_dia3_kernel(BatchDev d, const TV* __restrict__ val,
                                                              const TX* __restrict__ x, const TX* __restrict__ xold,
                                                              const TX* __restrict__ rin, TX* __restrict__ y,
@@ -416,6 +434,7 @@ __global__ void __launch_bounds__(kBlock, std::is_same<TX, float>::value ? 3 : 2
     if (!whole) {  // an item that spans instances (or is short): slice by slice
       for (long long s = s0; s < s1; ++s) {
         const int is = d.s_inst[s];
+        if (TZ && d.zmode[is]) continue;  // stepped by b_cheb_z_kernel
         const int Rs = d.R[is];
         const unsigned as = active_mask(done, d.cbase[is], Rs);
         if (!as) continue;
@@ -432,7 +451,7 @@ __global__ void __launch_bounds__(kBlock, std::is_same<TX, float>::value ? 3 : 2
       }
       continue;
     }
-    if (!act) continue;
+    if (!act || (TZ && d.zmode[i])) continue;
     const long long row0 = d.s_row0[s0];
     switch (R) {
       case 1: b_cheb_dia3_chunk<TV, TX, 1, MODE>(d, i, row0, val, x, xold, rin, y, coef, act, pol_first, pol_last); break;
@@ -446,6 +465,128 @@ __global__ void __launch_bounds__(kBlock, std::is_same<TX, float>::value ? 3 : 2
     }
   }
 }
+
+// Plane marching for the instances of a structured grid (FP32 values and
+// vectors): a thread owns one grid column (x, y) of a 32 x 8 tile with all R
+// right-hand sides and walks z through the item's planes, so the z-neighbours
+// x(z - 1), x(z + 1) and the lower z-entry come from registers (the planes it
+// loaded before) and the in-plane neighbours from L1 (loaded by the
+// neighbouring threads of the same step); the slice kernel reads those from
+// L2.  Neighbour rows are clipped to the instance's padded rows like the
+// slice kernel's; their matrix entries are 0.  The same sums as the slice
+// kernel: A x = x + sum over the three diagonals of (upper, lower) terms.
+template <int R, int MODE>
+__device__ __forceinline__ void b_z_item(const BatchDev& d, const BZItem it, const float* __restrict__ val,
+                                         const float* __restrict__ x, const float* __restrict__ xold,
+                                         const float* __restrict__ rin, float* __restrict__ y,
+                                         const double* __restrict__ coef, unsigned act, uint64_t pol_first,
+                                         uint64_t pol_last) {
+  const int i = it.inst;
+  const int Nx = d.dia_off[i * kBDiag + 1];
+  const long long nxy = d.dia_off[i * kBDiag + 2];
+  const int Ny = (int)(nxy / Nx);
+  const int xx = it.x0 + (int)(threadIdx.x & 31), yy = it.y0 + (int)(threadIdx.x >> 5);
+  if (xx >= Nx || yy >= Ny) return;
+  const long long vo = d.voff[i];
+  const float* X = x + vo;
+  const long long last = (d.sbase[i + 1] - d.sbase[i]) * 32 - 1;
+  const long long str = d.dia_stride[i];
+  const float* U0 = val + d.dia_base[i] + d.dia_pad[i];
+  const float* U1 = U0 + str;
+  const float* U2 = U1 + str;
+  float ca[R], cb[R], cc[R];
+  const double* cf0 = coef + (long long)d.cbase[i] * 3;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    ca[r] = (float)__ldg(cf0 + 3 * r);
+    cb[r] = (float)__ldg(cf0 + 3 * r + 1);
+    cc[r] = (float)__ldg(cf0 + 3 * r + 2);
+  }
+  auto clip = [&](long long j) { return j < 0 ? 0LL : (j > last ? last : j); };
+  long long row = xx + (long long)Nx * yy + nxy * it.z0;
+  RowVec<float, R> xm, xc;
+  xm.load(X + clip(row - nxy) * R);
+  xc.load(X + row * R);
+  float l2 = ld_pol<float>(U2 + row - nxy, pol_first);  // a(row - nxy, row); 0 in the front pad
+#pragma unroll 1
+  for (int z = it.z0; z < it.z1; ++z, row += nxy) {
+    RowVec<float, R> xp, xw, xe, xs, xn;
+    xp.load(X + clip(row + nxy) * R);
+    const float u0 = ld_pol<float>(U0 + row, pol_first);
+    const float u1 = ld_pol<float>(U1 + row, pol_first);
+    const float u2 = ld_pol<float>(U2 + row, pol_first);
+    const float l0 = __ldg(U0 + row - 1);
+    const float l1 = __ldg(U1 + row - Nx);
+    xw.load(X + clip(row - 1) * R);
+    xe.load(X + clip(row + 1) * R);
+    xs.load(X + clip(row - Nx) * R);
+    xn.load(X + clip(row + Nx) * R);
+    const long long e0 = vo + row * R;
+    float rs[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) rs[r] = ld_pol<float>(rin + e0 + r, pol_last);
+    RowVec<float, R> xo;
+    if (MODE == kChebK) xo.load(xold + e0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float acc = xc.v[r];
+      acc = fmaf(u0, xe.v[r], fmaf(l0, xw.v[r], acc));
+      acc = fmaf(u1, xn.v[r], fmaf(l1, xs.v[r], acc));
+      acc = fmaf(u2, xp.v[r], fmaf(l2, xm.v[r], acc));
+      float out;
+      if (MODE == kCheb1)
+        out = fmaf(cb[r], acc, ca[r] * rs[r]);
+      else if (MODE == kCheb2)
+        out = fmaf(cc[r], rs[r] - acc, fmaf(cb[r], rs[r], ca[r] * xc.v[r]));
+      else
+        out = fmaf(cc[r], rs[r] - acc, fmaf(cb[r], xo.v[r], ca[r] * xc.v[r]));
+      if ((act >> r) & 1u) y[e0 + r] = out;
+    }
+    xm = xc;
+    xc = xp;
+    l2 = u2;
+  }
+}
+
+// One plane-marching item per block, items item0 + blockIdx.x of the
+// instances with RLO..RHI right-hand sides (one launch per register class:
+// the R = 8 path needs three times the registers of R = 1).  Within a class
+// the items are ordered by decreasing work, so the block scheduler hands the
+// large ones out first.  No barriers.
+template <int RLO, int RHI, int MODE>
+__global__ void __launch_bounds__(kBlock) b_cheb_z_kernel(BatchDev d, long long item0, const float* __restrict__ val,
+                                                          const float* __restrict__ x,
+                                                          const float* __restrict__ xold,
+                                                          const float* __restrict__ rin, float* __restrict__ y,
+                                                          const int* __restrict__ done,
+                                                          const double* __restrict__ coef) {
+  const BZItem it = d.zitem[item0 + blockIdx.x];
+  const int R = d.R[it.inst];
+  const unsigned act = active_mask(done, d.cbase[it.inst], R);
+  if (!act || R < RLO || R > RHI) return;
+  const uint64_t pol_first = b_policy(false), pol_last = b_policy(true);
+#define PP_BZ_CASE(RR)                                                                           \
+  case RR:                                                                                       \
+    if constexpr (RR >= RLO && RR <= RHI)                                                        \
+      b_z_item<RR, MODE>(d, it, val, x, xold, rin, y, coef, act, pol_first, pol_last);           \
+    break;
+  switch (R) {
+    PP_BZ_CASE(1)
+    PP_BZ_CASE(2)
+    PP_BZ_CASE(3)
+    PP_BZ_CASE(4)
+    PP_BZ_CASE(5)
+    PP_BZ_CASE(6)
+    PP_BZ_CASE(7)
+    PP_BZ_CASE(8)
+    default: break;
+  }
+#undef PP_BZ_CASE
+}
+
+// The register classes of the plane-marching step: R in [kBZClass[c], kBZClass[c + 1]).
+constexpr int kBZClasses = 3;
+constexpr int kBZClass[kBZClasses + 1] = {1, 3, 5, kBR + 1};
 
 template <typename TV, typename TX, int MODE>
 __global__ void __launch_bounds__(kBlock) b_cheb_kernel(BatchDev d, const TV* __restrict__ val, const TX* __restrict__ x,
@@ -913,7 +1054,57 @@ struct BPlan {
   long long dia_total = 0;
   std::vector<int> dia_nd, dia_off;
   std::vector<long long> dia_base, dia_stride, dia_pad;
+  std::vector<int> zmode;
+  std::vector<BZItem> zitems;
+  std::vector<long long> zclass;  // item offsets of the register classes
+  int nz_inst = 0;
 };
+
+// Plane-marching items (FP32 apply, DIA): every instance whose upper offsets
+// are 1, Nx, Nx*Ny with n = Nx*Ny*Nz (a structured grid in natural order) is
+// cut into 32 x 8 tiles and z chunks of at most kBZPlanes planes; the items
+// are sorted by decreasing work so that one block per item balances.
+void plan_z_items(BPlan& P) {
+  P.zmode.assign(P.nb, 0);
+  std::vector<std::pair<double, BZItem>> it;
+  for (int i = 0; i < P.nb; ++i) {
+    if (P.dia_nd[i] != 3) continue;
+    const long long o0 = P.dia_off[(size_t)i * kBDiag], o1 = P.dia_off[(size_t)i * kBDiag + 1],
+                    o2 = P.dia_off[(size_t)i * kBDiag + 2];
+    if (o0 != 1 || o1 < 2 || o2 <= o1 || o2 % o1 != 0 || P.n[i] % o2 != 0) continue;
+    const long long Nx = o1, Ny = o2 / o1, Nz = P.n[i] / o2;
+    if (Nz > 65535) continue;
+    P.zmode[i] = 1;
+    P.nz_inst += 1;
+    const long long chunks = (Nz + kBZPlanes - 1) / kBZPlanes;
+    const long long zc = (Nz + chunks - 1) / chunks;
+    for (long long y0 = 0; y0 < Ny; y0 += kBZTileY)
+      for (long long x0 = 0; x0 < Nx; x0 += kBZTileX)
+        for (long long z0 = 0; z0 < Nz; z0 += zc) {
+          const long long z1 = std::min(Nz, z0 + zc);
+          BZItem b{i, (int)x0, (int)y0, (unsigned short)z0, (unsigned short)z1};
+          const double rows = (double)std::min<long long>(kBZTileX, Nx - x0) *
+                              std::min<long long>(kBZTileY, Ny - y0) * (z1 - z0);
+          it.push_back({rows * (12.0 + 16.0 * P.R[i]), b});
+        }
+  }
+  auto cls = [&](const BZItem& b) {
+    int c = 0;
+    while (c + 1 < kBZClasses && P.R[b.inst] >= kBZClass[c + 1]) ++c;
+    return c;
+  };
+  std::stable_sort(it.begin(), it.end(), [&](const auto& a, const auto& b) {
+    const int ca = cls(a.second), cb = cls(b.second);
+    return ca != cb ? ca < cb : a.first > b.first;
+  });
+  P.zitems.clear();
+  P.zclass.assign(kBZClasses + 1, 0);
+  for (const auto& e : it) {
+    P.zitems.push_back(e.second);
+    P.zclass[cls(e.second) + 1] += 1;
+  }
+  for (int c = 0; c < kBZClasses; ++c) P.zclass[c + 1] += P.zclass[c];
+}
 
 // DIA mode: the upper offsets of instance i are those of its first row
 // (for a Dirichlet stencil every offset occurs there); pp_batch_setup then
@@ -989,6 +1180,7 @@ int plan_batch(const pp_batch_item* items, int count, BPlan& P, cudaStream_t s, 
   P.nnz_pad = P.sptr.back();
   P.vec_elems = vo;
   P.rows_pad = wo;
+  if (dia) plan_z_items(P);
   return PP_OK;
 }
 
@@ -1016,6 +1208,10 @@ size_t layout_batch(pp_ctx* c, pp_batch_state* B, const BPlan& P, void* base) {
     d.dia_pad = M.take<long long>(P.nb);
     d.dval64 = M.take<double>(P.dia_total);
     d.dval32 = B->apply_prec == PP_PREC_F32 ? M.take<float>(P.dia_total) : nullptr;
+    d.zmode = M.take<int>(P.nb);
+    d.zitem = M.take<BZItem>((long long)P.zitems.size());
+    // the plane-marching step is FP32 only
+    d.nzitems = B->apply_prec == PP_PREC_F32 ? (long long)P.zitems.size() : 0;
   } else {
     d.col = M.take<int>(P.nnz_pad);
     d.val64 = M.take<double>(P.nnz_pad);
@@ -1116,9 +1312,37 @@ cudaError_t b_cheb_steps(pp_batch_state* B, cudaStream_t s) {
     using TX = std::remove_cv_t<std::remove_pointer_t<decltype(tx)>>;
     const TV* v = reinterpret_cast<const TV*>(val);
     if (d.dia) {
-      if (mode == kCheb1) b_cheb_dia3_kernel<TV, TX, kCheb1><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
-      else if (mode == kCheb2) b_cheb_dia3_kernel<TV, TX, kCheb2><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
-      else b_cheb_dia3_kernel<TV, TX, kChebK><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+      bool tz = false;  // plane-marching instances present (FP32 only)
+      if constexpr (std::is_same<TX, float>::value) {
+        if (d.nzitems > 0) {
+          tz = true;
+          auto zl = [&](auto lo, auto hi, int c) {
+            constexpr int RLO = decltype(lo)::value, RHI = decltype(hi)::value;
+            const long long i0 = B->zclass[c], cnt = B->zclass[c + 1] - i0;
+            if (cnt <= 0) return;
+            const unsigned gz = (unsigned)cnt;
+            if (mode == kCheb1)
+              b_cheb_z_kernel<RLO, RHI, kCheb1><<<gz, kBlock, 0, s>>>(d, i0, v, xin, xo, rin, yout, B->c.done, cj);
+            else if (mode == kCheb2)
+              b_cheb_z_kernel<RLO, RHI, kCheb2><<<gz, kBlock, 0, s>>>(d, i0, v, xin, xo, rin, yout, B->c.done, cj);
+            else
+              b_cheb_z_kernel<RLO, RHI, kChebK><<<gz, kBlock, 0, s>>>(d, i0, v, xin, xo, rin, yout, B->c.done, cj);
+          };
+          zl(std::integral_constant<int, kBZClass[0]>(), std::integral_constant<int, kBZClass[1] - 1>(), 0);
+          zl(std::integral_constant<int, kBZClass[1]>(), std::integral_constant<int, kBZClass[2] - 1>(), 1);
+          zl(std::integral_constant<int, kBZClass[2]>(), std::integral_constant<int, kBZClass[3] - 1>(), 2);
+          if (B->nz_inst == d.nb) return cudaGetLastError();  // every instance plane-marched
+        }
+      }
+      if (tz) {
+        if (mode == kCheb1) b_cheb_dia3_kernel<TV, TX, kCheb1, true><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+        else if (mode == kCheb2) b_cheb_dia3_kernel<TV, TX, kCheb2, true><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+        else b_cheb_dia3_kernel<TV, TX, kChebK, true><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+      } else {
+        if (mode == kCheb1) b_cheb_dia3_kernel<TV, TX, kCheb1, false><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+        else if (mode == kCheb2) b_cheb_dia3_kernel<TV, TX, kCheb2, false><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+        else b_cheb_dia3_kernel<TV, TX, kChebK, false><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
+      }
     } else {
       if (mode == kCheb1) b_cheb_kernel<TV, TX, kCheb1><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
       else if (mode == kCheb2) b_cheb_kernel<TV, TX, kCheb2><<<g, kBlock, 0, s>>>(d, v, xin, xo, rin, yout, B->c.done, cj);
@@ -1376,6 +1600,8 @@ extern "C" int pp_batch_setup(pp_ctx** out, const pp_batch_item* items, int coun
   B->woff_h = P.woff;
   B->vec_elems = P.vec_elems;
   B->rows_pad = P.rows_pad;
+  B->nz_inst = B->d.nzitems > 0 ? P.nz_inst : 0;
+  for (int q = 0; q < 4 && q < (int)P.zclass.size(); ++q) B->zclass[q] = P.zclass[q];
   BatchDev& d = B->d;
   B->c.maxit = opt->maxit;
   B->c.flexible = opt->flexible;
@@ -1413,6 +1639,8 @@ extern "C" int pp_batch_setup(pp_ctx** out, const pp_batch_item* items, int coun
              {d.dia_pad, P.dia_pad.data(), sizeof(long long) * P.dia_pad.size()},
              {d_rp, rps.data(), sizeof(void*) * count},
              {d_ci, cis.data(), sizeof(void*) * count},
+             {d.zmode, P.zmode.data(), sizeof(int) * P.zmode.size()},
+             {d.zitem, P.zitems.data(), sizeof(BZItem) * P.zitems.size()},
              {d_va, vas.data(), sizeof(void*) * count}};
   cudaError_t e = cudaSuccess;
   for (const Up& u : ups)

@@ -83,14 +83,26 @@ def test_batch_f64_matches_oracle_per_column(problem, graphs, k, fmt):
         assert abx[c0, 0] == pytest.approx(lo, rel=1e-9) and abx[c0, 1] == pytest.approx(hi, rel=1e-9)
 
 
+def oracle_intervals(mats, seed, steps):
+    """Per column (alpha, beta) from the oracle's Lanczos on each instance."""
+    out = []
+    for i, (A, s) in enumerate(zip(mats, SPECS)):
+        vh, _ = O.jacobi_scale(A)
+        a, b = O.lanczos(A, I.lanczos_start(A.n, seed + i), steps, val=vh)
+        lo, hi = O.tridiag_extremes(a, b)
+        out += [(lo, hi)] * s.nrhs
+    return np.array(out)
+
+
 @pytest.mark.parametrize("fmt", FMTS)
 def test_batch_per_column_intervals(problem, fmt):
     mats, rhs = problem
     S = P.BatchSolver(mats, [s.nrhs for s in SPECS], k=5, rtol=1e-10, format=fmt)
-    abx = S.intervals()
+    ab = oracle_intervals(mats, 0, 10)
     u = I.uniform(7, 9, 3 * S.ncols)
-    abx[:, 0] *= 0.3 + u[0::3]        # different interval and xi in every column
-    abx[:, 1] *= 1.0 + 0.2 * u[1::3]
+    abx = np.zeros((S.ncols, 3))
+    abx[:, 0] = ab[:, 0] * (0.3 + u[0::3])  # different interval and xi in every column
+    abx[:, 1] = ab[:, 1] * (1.0 + 0.2 * u[1::3])
     abx[:, 2] = 10.0 ** (-5 + 3 * u[2::3])
     S.intervals(abx)
     x, it, stv, st = S.solve(S.pack(rhs))
@@ -182,3 +194,64 @@ def test_batch_autotune_and_step_timer(problem, prec):
             else:
                 assert_close(xs[i][:, r], xo, 1e-7)
             g += 1
+
+
+# Instances for the FP32 DIA apply: grids with two 32-wide tiles in x, five
+# 8-row tiles in y and two z chunks (N = 40), and R = 1..8 right-hand sides
+# (all three register classes of the plane-marching step).
+ZSPECS = [I.BatchSpec(40, 2.0, 5, 21), I.BatchSpec(6, 1.0, 1, 22), I.BatchSpec(12, 1.5, 7, 23),
+          I.BatchSpec(9, 0.5, 2, 24), I.BatchSpec(7, 1.0, 4, 25), I.BatchSpec(5, 1.0, 3, 26),
+          I.BatchSpec(8, 2.0, 8, 27), I.BatchSpec(4, 1.0, 6, 28)]
+
+
+def banded_spd(n, offs, seed):
+    """Symmetric banded matrix with the given upper offsets, every band entry
+    nonzero and negative, made SPD by diagonal dominance."""
+    D = np.zeros((n, n))
+    u = I.uniform(seed, 5, n * len(offs))
+    for t, o in enumerate(offs):
+        v = -(0.1 + 0.8 * u[t * n:(t + 1) * n])[: n - o]
+        D[np.arange(n - o), np.arange(o, n)] = v
+        D[np.arange(o, n), np.arange(n - o)] = v
+    D[np.arange(n), np.arange(n)] = np.abs(D).sum(axis=1) + 0.5
+    return I.dense_to_csr(D)
+
+
+def round_f32(x):
+    return x.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("with_other", [0, 1])
+def test_batch_f32_dia_apply_matches_rounded_oracle(with_other):
+    """One FCG iteration from x0 = 0 gives x1 = (b, z) / (z, A z) z with
+    z = W p_k(A_hat) W b, so every column's x1 checks the FP32 DIA apply of
+    Algorithm 2 (plane marching for the grid instances; with_other adds
+    instances it does not take, a 1-diagonal band and a 3-diagonal band whose
+    size is not a grid, which the slice kernel steps in the same launch
+    sequence) against the oracle run on the same FP32-rounded values, with
+    the intervals given per column."""
+    mats = [I.batch_instance(s) for s in ZSPECS]
+    nrhs = [s.nrhs for s in ZSPECS]
+    rhs = [I.batch_rhs(s) for s in ZSPECS]
+    if with_other:
+        mats += [banded_spd(300, [1], 31), banded_spd(100, [1, 5, 12], 32)]
+        nrhs += [2, 3]
+        rhs += [I.normal(33, 1, 600).reshape(300, 2), I.normal(34, 1, 300).reshape(100, 3)]
+    k = 5
+    S = P.BatchSolver(mats, nrhs, k=k, rtol=0.0, maxit=1, apply_prec="f32", flexible=1, format="dia")
+    u = I.uniform(8, 9, 3 * S.ncols)
+    abx = np.stack([0.02 + 0.05 * u[0::3], 1.9 + 0.1 * u[1::3], 10.0 ** (-4 + 2 * u[2::3])], axis=1)
+    S.intervals(abx)
+    x, it, stv, _ = S.solve(S.pack(rhs), allow=(P.PP_OK, P.PP_MAXIT))
+    xs = S.unpack(x)
+    g = 0
+    for A, B, Xi in zip(mats, rhs, xs):
+        vh, w = O.jacobi_scale(A)
+        for r in range(B.shape[1]):
+            a, b, xi = abx[g]
+            z = w * O.cheb_apply(A, a, b, xi, k, w * B[:, r], val=round_f32(vh))
+            x1 = (B[:, r] @ z) / (z @ A.matvec(z)) * z
+            assert it[g] == 1
+            assert_close(Xi[:, r], x1, 2e-5)
+            g += 1
+    S.close()
