@@ -912,7 +912,7 @@ def run_variants(args, A, rp, ci, va, bt, opts, x_oracle, fp64_peak, fp64_s, dev
                "iterations": int(stats[-1]["iterations"]), "rel_res": stats[-1]["rel_res"],
                "speedup_vs_fp64_k5": round(fp64_s / t, 3), "steps_timed": reps,
                "step_roofline": {kk2: roof[kk2] for kk2 in ("bound", "achieved", "peak", "unit", "frac",
-                                                           "avg_launch_us")} if roof else None}
+                                                           "avg_launch_us", "traffic")} if roof else None}
         if x_oracle is not None:
             xv = x.cpu().numpy()
             d = xv - x_oracle
