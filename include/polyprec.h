@@ -460,6 +460,10 @@ int pp_mlp_create(pp_mlp** mlp, int max_batch, unsigned long long seed, void* wo
                   size_t ws_bytes);
 /* Copy the FP32 master parameters out (get_host) and/or in (set_host). */
 int pp_mlp_params(pp_mlp* mlp, float* get_host, const float* set_host);
+/* y = MLP(x) for batch rows.  Synchronous.  The products run on tcgen05
+ * tensor cores (accumulators in tensor memory); every wait of those kernels
+ * is bounded, and an expired one is returned as PP_ETIMEOUT by this call,
+ * pp_mlp_grad or a pp_mlp_train_step given loss_host. */
 int pp_mlp_forward(pp_mlp* mlp, const float* x, float* y, int batch, void* stream);
 /* Loss (1/(2 batch)) sum ||y - t||^2 and its gradient (host, PP_MLP_NPARAM),
  * parameters unchanged.  Synchronous. */

@@ -1,9 +1,9 @@
 // The learned part: a 3-layer MLP (8 -> 128 -> 128 -> 3, ReLU) that maps
 // cheap per-instance statistics to the spectral interval multipliers and xi
 // of the polynomial preconditioner.  BF16 weights and activations, FP32
-// accumulation on the tensor cores (warp-level mma m16n8k16), FP32 master
-// parameters updated by Adam -- forward, backward and the update all run in
-// the kernels below.
+// accumulation on the tensor cores (tcgen05.mma with the accumulator in
+// tensor memory), FP32 master parameters updated by Adam -- forward,
+// backward and the update all run in the kernels below.
 //
 // Computation (rounding points are part of the definition):
 //   x0 = bf16(x);  h1 = relu(x0 W1^T + b1);  h2 = relu(bf16(h1) W2^T + b2)
@@ -36,57 +36,169 @@ __device__ __forceinline__ unsigned short bf_bits(float f) {
 }
 __device__ __forceinline__ float bf_float(unsigned short u) { return __uint_as_float(((unsigned int)u) << 16); }
 
-// Generic strided BF16 GEMM on the tensor cores: C[m][n] = sum_k A(m,k) B(k,n)
-// with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn] (BF16, zero
-// outside M x K / K x N), FP32 accumulation.  One warp per 16 x 8 tile.
+// ---------------------------------------------------------------- tcgen05 --
+// Strided BF16 GEMM on the 5th-generation tensor cores: C[m][n] = sum_k
+// A(m,k) B(k,n) with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]
+// (BF16, zero outside M x K / K x N), FP32 accumulation in tensor memory.
 // Epilogue: + bias[n], ReLU, FP32 store (ldc), optional BF16 copy (ldcb).
-__global__ void mma_gemm_kernel(int M, int N, int K, const unsigned short* __restrict__ A, long long sam,
-                                long long sak, const unsigned short* __restrict__ B, long long sbk, long long sbn,
-                                const float* __restrict__ bias, int relu, float* __restrict__ C, int ldc,
-                                unsigned short* __restrict__ Cb, int ldcb) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int tiles_n = (N + 7) / 8;
-  const int tm = warp / tiles_n, tn = warp % tiles_n;
-  if (tm * 16 >= M) return;
-  const int g = lane >> 2, t = lane & 3;
-  auto ldA = [&](int m, int k) -> unsigned int {
-    unsigned int lo = (m < M && k < K) ? A[m * sam + k * sak] : 0u;
-    unsigned int hi = (m < M && k + 1 < K) ? A[m * sam + (k + 1) * sak] : 0u;
-    return lo | (hi << 16);
-  };
-  auto ldB = [&](int k, int n) -> unsigned int {
-    unsigned int lo = (k < K && n < N) ? B[k * sbk + n * sbn] : 0u;
-    unsigned int hi = (k + 1 < K && n < N) ? B[(k + 1) * sbk + n * sbn] : 0u;
-    return lo | (hi << 16);
-  };
-  float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-  const int m0 = tm * 16, n0 = tn * 8;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    const unsigned int a0 = ldA(m0 + g, k0 + 2 * t);
-    const unsigned int a1 = ldA(m0 + g + 8, k0 + 2 * t);
-    const unsigned int a2 = ldA(m0 + g, k0 + 2 * t + 8);
-    const unsigned int a3 = ldA(m0 + g + 8, k0 + 2 * t + 8);
-    const unsigned int b0 = ldB(k0 + 2 * t, n0 + g);
-    const unsigned int b1 = ldB(k0 + 2 * t + 8, n0 + g);
+//
+// One CTA of 4 warps per 128 x NT tile of C (NT = N rounded up to 16, at
+// most 128).  K runs in chunks of 32 through two shared-memory stages; all
+// threads stage a chunk in the canonical K-major layout without swizzle
+// (core matrices of 8 rows x 16 bytes: row group g, k group j at g*512 +
+// j*128 bytes), then thread 0 issues two tcgen05.mma (K = 16 each) and
+// commits them to the stage's mbarrier, which releases the stage two chunks
+// later.  Warp 0 allocates the accumulator's TMEM columns; in the epilogue
+// warp w reads rows 32w..32w+31 of the tile (TMEM lanes) with tcgen05.ld.
+// Every mbarrier wait is bounded: on expiry the CTA sets *err, skips the
+// rest of its work, frees its TMEM and returns.
+constexpr int kTcM = 128, kTcNmax = 128, kTcKC = 32, kTcThreads = 128;
+constexpr int kTcRowGroupBytes = (kTcKC / 8) * 128;  // SBO: next 8 rows
+constexpr int kTcKGroupBytes = 128;                  // LBO: next 8 k
+constexpr long long kTcSpin = 1LL << 22;
+
+__device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets in 16-byte units, descriptor version 1 (bit 46), no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kTcKGroupBytes >> 4) << 16) |
+         ((uint64_t)(kTcRowGroupBytes >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kTcSpin; ++it) {
+    uint32_t ok;
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(tc_smem(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
   }
-  const float cv[4] = {c0, c1, c2, c3};
+  return false;
+}
+
+// bf16 element (row i, k j) of a staged chunk, in 16-bit units
+__device__ __forceinline__ int tc_off(int i, int j) { return (i >> 3) * (kTcRowGroupBytes / 2) + (j >> 3) * 64 + (i & 7) * 8 + (j & 7); }
+
+__global__ void __launch_bounds__(kTcThreads) tc_gemm_kernel(int M, int N, int K, const unsigned short* __restrict__ A,
+                                                             long long sam, long long sak,
+                                                             const unsigned short* __restrict__ B, long long sbk,
+                                                             long long sbn, const float* __restrict__ bias, int relu,
+                                                             float* __restrict__ C, int ldc,
+                                                             unsigned short* __restrict__ Cb, int ldcb, int* err) {
+  __shared__ __align__(1024) unsigned short sA[2][kTcM * kTcKC];
+  __shared__ __align__(1024) unsigned short sB[2][kTcNmax * kTcKC];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * kTcNmax;
+  const int NT = min(kTcNmax, (N - n0 + 15) / 16 * 16);
+  const uint32_t ncols = NT <= 32 ? 32u : (NT <= 64 ? 64u : 128u);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&s_tmem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = tc_idesc(kTcM, NT);
+  const int nch = max(1, (K + kTcKC - 1) / kTcKC);
+  bool bad = false;
+  int issued = 0;  // chunks whose MMAs were committed
+  for (int c = 0; c < nch && !bad; ++c) {
+    const int st = c & 1, k0 = c * kTcKC;
+    bool ok = true;
+    if (c >= 2) ok = tc_wait(&bar[st], ((c - 2) >> 1) & 1);  // the MMAs of chunk c - 2 have read stage st
+    if (__syncthreads_or(!ok)) {
+      bad = true;
+      break;
+    }
+    // stage A rows m0.., B rows (= output columns) n0.., k in [k0, k0 + 32)
+    for (int e = tid; e < kTcM * kTcKC; e += kTcThreads) {
+      const int i = sak == 1 ? e / kTcKC : e % kTcM, j = sak == 1 ? e % kTcKC : e / kTcM;
+      const int m = m0 + i, k = k0 + j;
+      sA[st][tc_off(i, j)] = (m < M && k < K) ? A[m * sam + k * sak] : (unsigned short)0;
+    }
+    for (int e = tid; e < NT * kTcKC; e += kTcThreads) {
+      const int i = sbk == 1 ? e / kTcKC : e % NT, j = sbk == 1 ? e % kTcKC : e / NT;
+      const int n = n0 + i, k = k0 + j;
+      sB[st][tc_off(i, j)] = (n < N && k < K) ? B[k * sbk + n * sbn] : (unsigned short)0;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int m = m0 + g + (q >= 2 ? 8 : 0);
-    const int n = n0 + 2 * t + (q & 1);
-    if (m >= M || n >= N) continue;
-    float v = cv[q];
-    if (bias) v += bias[n];
-    if (relu) v = v > 0.f ? v : 0.f;
-    if (C) C[(long long)m * ldc + n] = v;
-    if (Cb) Cb[(long long)m * ldcb + n] = bf_bits(v);
+      for (int kk = 0; kk < kTcKC / 16; ++kk) {
+        const uint64_t ad = tc_desc(tc_smem(&sA[st][0]) + kk * 2 * kTcKGroupBytes);
+        const uint64_t bd = tc_desc(tc_smem(&sB[st][0]) + kk * 2 * kTcKGroupBytes);
+        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       tc_smem(&bar[st]))
+                   : "memory");
+    }
+    issued = c + 1;
   }
+  // the last commit covers every MMA issued before it
+  if (!bad) {
+    const bool ok = tc_wait(&bar[(nch - 1) & 1], ((nch - 1) >> 1) & 1);
+    bad = __syncthreads_or(!ok);
+  }
+  if (!bad) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int m = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < NT; c0 += 8) {
+      uint32_t r[8];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < M) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int n = n0 + c0 + q;
+          if (n >= N) continue;
+          float v = __uint_as_float(r[q]);
+          if (bias) v += bias[n];
+          if (relu) v = v > 0.f ? v : 0.f;
+          if (C) C[(long long)m * ldc + n] = v;
+          if (Cb) Cb[(long long)m * ldcb + n] = bf_bits(v);
+        }
+      }
+    }
+  } else {
+    if (tid == 0) atomicExch(err, 1);
+    // let the MMAs still in flight finish (bounded) before their TMEM is freed
+    if (issued > 0) tc_wait(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
 __global__ void pack_input_kernel(int B, int Bp, const float* __restrict__ x, unsigned short* __restrict__ x0) {
@@ -181,6 +293,7 @@ struct pp_mlp {
   unsigned short *x0 = nullptr, *h1b = nullptr, *h2b = nullptr, *dyb = nullptr, *dz2b = nullptr, *dz1b = nullptr;
   float *h1 = nullptr, *h2 = nullptr, *y = nullptr, *dy = nullptr, *dh2 = nullptr, *dz2 = nullptr, *dh1 = nullptr,
         *dz1 = nullptr, *loss = nullptr;
+  int* err = nullptr;  // set on the device when a tensor-core wait expires
 };
 
 namespace {
@@ -226,15 +339,15 @@ size_t mlp_layout(pp_mlp* M, void* base, int max_batch) {
   M->dz1 = B.take<float>((long long)bp * NH);
   M->dz1b = B.take<unsigned short>((long long)bp * NH);
   M->loss = B.take<float>(1);
+  M->err = B.take<int>(1);
   return B.off + 256;
 }
 
-int warps_grid(int M, int N) { return ((M + 15) / 16 * ((N + 7) / 8) + 3) / 4; }
-
-cudaError_t gemm(cudaStream_t s, int M, int N, int K, const unsigned short* A, long long sam, long long sak,
-                 const unsigned short* B, long long sbk, long long sbn, const float* bias, int relu, float* C, int ldc,
-                 unsigned short* Cb, int ldcb) {
-  mma_gemm_kernel<<<warps_grid(M, N), 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, relu, C, ldc, Cb, ldcb);
+cudaError_t gemm(cudaStream_t s, int* err, int M, int N, int K, const unsigned short* A, long long sam,
+                 long long sak, const unsigned short* B, long long sbk, long long sbn, const float* bias, int relu,
+                 float* C, int ldc, unsigned short* Cb, int ldcb) {
+  const dim3 grid((unsigned)((M + kTcM - 1) / kTcM), (unsigned)((N + kTcNmax - 1) / kTcNmax));
+  tc_gemm_kernel<<<grid, kTcThreads, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, relu, C, ldc, Cb, ldcb, err);
   return cudaGetLastError();
 }
 
@@ -243,9 +356,9 @@ cudaError_t forward(pp_mlp* M, const float* x, int B, cudaStream_t s) {
   weights_bf16_kernel<<<80, 256, 0, s>>>(M->p, M->w1, M->w2, M->w3);
   pack_input_kernel<<<(bp * NINP + 255) / 256, 256, 0, s>>>(B, bp, x, M->x0);
   // layer 1: [B x 16] W1^T (W1 stored [128 x 16]): B(k,n) = W1[n*16 + k]
-  cudaError_t e = gemm(s, bp, NH, NINP, M->x0, NINP, 1, M->w1, 1, NINP, M->p + OB1, 1, M->h1, NH, M->h1b, NH);
-  if (e == cudaSuccess) e = gemm(s, bp, NH, NH, M->h1b, NH, 1, M->w2, 1, NH, M->p + OB2, 1, M->h2, NH, M->h2b, NH);
-  if (e == cudaSuccess) e = gemm(s, bp, NOUTP, NH, M->h2b, NH, 1, M->w3, 1, NH, M->p + OB3, 0, M->y, NOUTP, nullptr, 0);
+  cudaError_t e = gemm(s, M->err, bp, NH, NINP, M->x0, NINP, 1, M->w1, 1, NINP, M->p + OB1, 1, M->h1, NH, M->h1b, NH);
+  if (e == cudaSuccess) e = gemm(s, M->err, bp, NH, NH, M->h1b, NH, 1, M->w2, 1, NH, M->p + OB2, 1, M->h2, NH, M->h2b, NH);
+  if (e == cudaSuccess) e = gemm(s, M->err, bp, NOUTP, NH, M->h2b, NH, 1, M->w3, 1, NH, M->p + OB3, 0, M->y, NOUTP, nullptr, 0);
   return e;
 }
 
@@ -253,22 +366,37 @@ cudaError_t backward(pp_mlp* M, const float* t, int B, cudaStream_t s) {
   const int bp = (B + 15) / 16 * 16;
   loss_grad_kernel<<<1, 256, 0, s>>>(B, bp, M->y, t, M->dy, M->dyb, M->loss);
   // dW3 [8 x 128] = dY^T [8 x B] h2 [B x 128]: A(m=n_out, k=b) = dyb[b*8 + m], B(k=b, n) = h2b[b*128 + n]
-  cudaError_t e = gemm(s, NOUTP, NH, B, M->dyb, 1, NOUTP, M->h2b, NH, 1, nullptr, 0, M->g + OW3, NH, nullptr, 0);
+  cudaError_t e = gemm(s, M->err, NOUTP, NH, B, M->dyb, 1, NOUTP, M->h2b, NH, 1, nullptr, 0, M->g + OW3, NH, nullptr, 0);
   bias_grad_kernel<<<1, 32, 0, s>>>(B, NOUTP, NOUTP, M->dy, M->g + OB3);
   // dH2 [B x 128] = dY [B x 8] W3 [8 x 128]: A(m, k) = dyb[m*8 + k], B(k, n) = w3[k*128 + n]
-  if (e == cudaSuccess) e = gemm(s, bp, NH, NOUTP, M->dyb, NOUTP, 1, M->w3, NH, 1, nullptr, 0, M->dh2, NH, nullptr, 0);
+  if (e == cudaSuccess) e = gemm(s, M->err, bp, NH, NOUTP, M->dyb, NOUTP, 1, M->w3, NH, 1, nullptr, 0, M->dh2, NH, nullptr, 0);
   relu_back_kernel<<<(bp * NH + 255) / 256, 256, 0, s>>>(bp * NH, M->dh2, M->h2, M->dz2, M->dz2b);
   // dW2 [128 x 128] = dZ2^T h1
-  if (e == cudaSuccess) e = gemm(s, NH, NH, B, M->dz2b, 1, NH, M->h1b, NH, 1, nullptr, 0, M->g + OW2, NH, nullptr, 0);
+  if (e == cudaSuccess) e = gemm(s, M->err, NH, NH, B, M->dz2b, 1, NH, M->h1b, NH, 1, nullptr, 0, M->g + OW2, NH, nullptr, 0);
   bias_grad_kernel<<<4, 32, 0, s>>>(B, NH, NH, M->dz2, M->g + OB2);
   // dH1 = dZ2 W2 (W2 stored [out x in] = [n x k]): B(k=j, n=i) = w2[j*128 + i]
-  if (e == cudaSuccess) e = gemm(s, bp, NH, NH, M->dz2b, NH, 1, M->w2, NH, 1, nullptr, 0, M->dh1, NH, nullptr, 0);
+  if (e == cudaSuccess) e = gemm(s, M->err, bp, NH, NH, M->dz2b, NH, 1, M->w2, NH, 1, nullptr, 0, M->dh1, NH, nullptr, 0);
   relu_back_kernel<<<(bp * NH + 255) / 256, 256, 0, s>>>(bp * NH, M->dh1, M->h1, M->dz1, M->dz1b);
   // dW1 [128 x 16] = dZ1^T x0
-  if (e == cudaSuccess) e = gemm(s, NH, NINP, B, M->dz1b, 1, NH, M->x0, NINP, 1, nullptr, 0, M->g + OW1, NINP, nullptr, 0);
+  if (e == cudaSuccess) e = gemm(s, M->err, NH, NINP, B, M->dz1b, 1, NH, M->x0, NINP, 1, nullptr, 0, M->g + OW1, NINP, nullptr, 0);
   bias_grad_kernel<<<4, 32, 0, s>>>(B, NH, NH, M->dz1, M->g + OB1);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;
+}
+
+// Reads the device flag of an expired tensor-core wait (synchronises the
+// stream) and clears it: PP_ETIMEOUT if it was set.
+int mlp_status(pp_mlp* M, cudaStream_t s, const char* where) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, M->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && h) {
+    e = cudaMemsetAsync(M->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) return fail(nullptr, PP_ETIMEOUT, std::string(where) + ": a tensor-core wait expired");
+  }
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, where);
+  return PP_OK;
 }
 
 int check_batch(pp_mlp* M, int B) {
@@ -314,6 +442,7 @@ extern "C" int pp_mlp_create(pp_mlp** out, int max_batch, unsigned long long see
   if (e == cudaSuccess) e = cudaMemset(M->m, 0, sizeof(float) * NPARAM);
   if (e == cudaSuccess) e = cudaMemset(M->v, 0, sizeof(float) * NPARAM);
   if (e == cudaSuccess) e = cudaMemset(M->g, 0, sizeof(float) * NPARAM);
+  if (e == cudaSuccess) e = cudaMemset(M->err, 0, sizeof(int));
   if (e != cudaSuccess) {
     delete M;
     return cuda_fail(nullptr, e, "pp_mlp_create");
@@ -342,7 +471,7 @@ extern "C" int pp_mlp_forward(pp_mlp* M, const float* x, float* y, int batch, vo
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "pp_mlp_forward");
-  return PP_OK;
+  return mlp_status(M, s, "pp_mlp_forward");
 }
 
 extern "C" int pp_mlp_grad(pp_mlp* M, const float* x, const float* t, int batch, float* loss_host, float* grad_host,
@@ -358,7 +487,7 @@ extern "C" int pp_mlp_grad(pp_mlp* M, const float* x, const float* t, int batch,
     e = cudaMemcpyAsync(grad_host, M->g, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "pp_mlp_grad");
-  return PP_OK;
+  return mlp_status(M, s, "pp_mlp_grad");
 }
 
 extern "C" int pp_mlp_train_step(pp_mlp* M, const float* x, const float* t, int batch, float lr, float* loss_host,
@@ -379,7 +508,7 @@ extern "C" int pp_mlp_train_step(pp_mlp* M, const float* x, const float* t, int 
   if (e == cudaSuccess && loss_host) e = cudaMemcpyAsync(loss_host, M->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && loss_host) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "pp_mlp_train_step");
-  return PP_OK;
+  return loss_host ? mlp_status(M, s, "pp_mlp_train_step") : PP_OK;
 }
 
 extern "C" int pp_mlp_destroy(pp_mlp* M) {

@@ -2,8 +2,8 @@
 
 The paper picks xi by hand sweeps per problem (Section 6) and the interval
 from an eigenvalue estimate.  Here a small MLP predicts, from cheap
-statistics of an instance (pp_batch_features: size, diagonal statistics,
-Gershgorin bounds, extreme Ritz values of a short Lanczos run), three
+statistics of an instance (pp_batch_features without the size: diagonal
+statistics, Gershgorin bounds, extreme Ritz values of a short Lanczos run), three
 numbers: multipliers s_alpha, s_beta of the Lanczos interval and xi.  Its
 training labels are found by the method itself: every training instance is
 solved for a grid of (s_alpha, s_beta, xi) settings in one batched solve
@@ -34,6 +34,23 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mlp_weights.
 # the most frequent label of the sweep the shipped weights were trained on
 # (1292 of 2000 instances): the best single constant setting of that sweep
 FIXED_BEST = (0.3, 1.1, 1e-4)
+
+
+# Feature columns the network sees.  Column 0 (log10 n) is left out, so the
+# inputs are size-free statistics (diagonal, Gershgorin and Ritz values of
+# the seed-scaled matrix) and the model applies to instances larger than the
+# ones it was trained on without extrapolating in an input.
+INPUTS = (1, 2, 3, 4, 5, 6, 7)
+
+
+def model_inputs(feats):
+    """The network's input columns of pp_batch_features rows (the unused
+    column is held at zero, so the input width stays PP_MLP_NIN)."""
+    f = np.array(feats, dtype=np.float64, copy=True)
+    keep = np.zeros(f.shape[1], dtype=bool)
+    keep[list(INPUTS)] = True
+    f[:, ~keep] = 0.0
+    return f
 
 
 def auto_xi(alpha, beta):
@@ -112,12 +129,13 @@ class Model:
     def predict(self, feats, device="cuda"):
         net = P.Mlp(max_batch=max(16, len(feats)), device=device)
         net.params(self.params)
-        y = net.forward((feats - self.mu_x) / self.sd_x)
+        y = net.forward((model_inputs(feats) - self.mu_x) / self.sd_x)
         net.close()
         return y * self.sd_y + self.mu_y
 
 
 def train(feats, targets, steps: int = 1500, lr: float = 3e-3, seed: int = 0, device="cuda"):
+    feats = model_inputs(feats)
     mu_x = feats.mean(axis=0)
     sd_x = feats.std(axis=0) + 1e-6
     mu_y = targets.mean(axis=0)
