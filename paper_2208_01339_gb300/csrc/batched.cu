@@ -91,6 +91,7 @@ struct BatchDev {
 
 struct BatchCols {
   double *rz, *rz_new, *pq, *zq, *rr, *bb, *rtol2;
+  double *al, *be;  // alpha = (r,z)/(p,q) and beta per column, formed once by the reductions
   int *done, *iter, *status;
   int* n_active;
   int maxit, flexible;
@@ -125,6 +126,10 @@ struct pp_batch_state {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap = nullptr;
   int graph_block = 0;
+  // the plane-marching register classes run as concurrent branches: two side
+  // streams forked from and joined back into the solver's stream by events
+  cudaStream_t zs[2] = {nullptr, nullptr};
+  cudaEvent_t zfork = nullptr, zjoin[2] = {nullptr, nullptr};
 };
 
 namespace pp {
@@ -160,6 +165,47 @@ struct RowVec {
     } else {
 #pragma unroll
       for (int e = 0; e < R; ++e) v[e] = __ldg(p + e);
+    }
+  }
+  // plain (cached) load, for vectors the same kernel also writes
+  __device__ __forceinline__ void load_rw(const T* p) {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+#pragma unroll
+      for (int q = 0; q < (int)(sizeof(T) * R / 16); ++q) {
+        const uint4 u = reinterpret_cast<const uint4*>(p)[q];
+        const T* t = reinterpret_cast<const T*>(&u);
+#pragma unroll
+        for (int e = 0; e < (int)(16 / sizeof(T)); ++e) v[q * (16 / sizeof(T)) + e] = t[e];
+      }
+    } else if constexpr (sizeof(T) * R == 8) {
+      const uint2 u = *reinterpret_cast<const uint2*>(p);
+      const T* t = reinterpret_cast<const T*>(&u);
+#pragma unroll
+      for (int e = 0; e < R; ++e) v[e] = t[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < R; ++e) v[e] = p[e];
+    }
+  }
+  __device__ __forceinline__ void store(T* p) const {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+#pragma unroll
+      for (int q = 0; q < (int)(sizeof(T) * R / 16); ++q) {
+        uint4 u;
+        T* t = reinterpret_cast<T*>(&u);
+#pragma unroll
+        for (int e = 0; e < (int)(16 / sizeof(T)); ++e) t[e] = v[q * (16 / sizeof(T)) + e];
+        reinterpret_cast<uint4*>(p)[q] = u;
+      }
+    } else if constexpr (sizeof(T) * R == 8) {
+      uint2 u;
+      T* t = reinterpret_cast<T*>(&u);
+#pragma unroll
+      for (int e = 0; e < R; ++e) t[e] = v[e];
+      *reinterpret_cast<uint2*>(p) = u;
+    } else {
+#pragma unroll
+      for (int e = 0; e < R; ++e) p[e] = v[e];
     }
   }
 };
@@ -208,6 +254,40 @@ __device__ __forceinline__ unsigned active_mask(const int* done, int g0, int R) 
   return m;
 }
 
+// Column sums of one slice: lane l holds row l's R values v[0..R-1]; the sum
+// of each column over the 32 lanes is written to out[0..R-1] by the lanes
+// whose low bits are zero.  Recursive halving: each exchange with the lane
+// 16, 8, ... apart halves the columns a lane keeps (it adds the half it
+// keeps to the partner's copy of it), so a lane does (Rp - 1) + (5 - log2 Rp)
+// FP64 additions (Rp = R rounded up to a power of 2) instead of 5 per column
+// -- FP64 additions are scarce on this GPU.  The order of the additions is
+// fixed, so the sums are deterministic.
+template <int R>
+__device__ __forceinline__ void slice_col_sums(const double (&v)[R], double* out, int lane) {
+  constexpr int Rp = R <= 1 ? 1 : (R <= 2 ? 2 : (R <= 4 ? 4 : 8));
+  constexpr int L = Rp == 1 ? 0 : (Rp == 2 ? 1 : (Rp == 4 ? 2 : 3));
+  double w[Rp];
+#pragma unroll
+  for (int c = 0; c < Rp; ++c) w[c] = c < R ? v[c] : 0.0;
+  int col = 0;
+#pragma unroll
+  for (int st = 0; st < L; ++st) {
+    const int off = 16 >> st, h = Rp >> (st + 1);
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int c = 0; c < h; ++c) {
+      const double keep = up ? w[c + h] : w[c];
+      const double send = up ? w[c] : w[c + h];
+      w[c] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+    if (up) col += h;
+  }
+  double t = w[0];
+#pragma unroll
+  for (int off = 16 >> L; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  if ((lane & ((32 >> L) - 1)) == 0 && col < R) out[col] = t;
+}
+
 // FP64 product of one slice for R right-hand sides: y = A x with partials
 // (x, y) (kSpmv), or the Lanczos step on column 0 (R = 1 view).
 template <int R, int MODE>
@@ -235,19 +315,19 @@ __device__ __forceinline__ void b_spmv_slice(const BatchDev& d, long long s, int
       for (int r = 0; r < R; ++r) acc[r] = fma(v, xv.v[r], acc[r]);
     }
   }
+  double pr[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    double pr = 0.0;
+    pr[r] = 0.0;
     const long long e = d.voff[i] + row * RS + r;
     if ((act >> r) & 1u) {
       double yv = acc[r];
       if (MODE == kLanczos && xold) yv -= coef * xold[e];
       y[e] = yv;
-      if (in) pr = x[e] * yv;
+      if (in) pr[r] = x[e] * yv;
     }
-    pr = warp_sum(pr);
-    if (lane == 0) part[s * kBR + r] = pr;
   }
+  slice_col_sums<R>(pr, part + s * kBR, lane);
 }
 
 template <int MODE>
@@ -614,99 +694,186 @@ __global__ void __launch_bounds__(kBlock) b_cheb_kernel(BatchDev d, const TV* __
 // ------------------------------------------------------------ vectors -----
 // Per-element loops walk slices too (lane = row, r < R) so that partial sums
 // line up with the product kernels.
+// With the FP32 preconditioner the iteration uses the fused forms: kBUpdXR32
+// also writes r32 (no separate kBTo32 pass), kBDots32 forms (r, z) and (q, z)
+// from z32 without storing z in FP64, and kBUpdP32 reads z32.
 enum BVec { kBScaleIn = 0, kBUpdXR = 1, kBTo32 = 2, kBFrom32 = 3, kBUpdP = 4, kBScaleOut = 5, kBZtoP = 6,
-            kBDeg0 = 7 };
+            kBDeg0 = 7, kBUpdXR32 = 8, kBDots32 = 9, kBUpdP32 = 10 };
 
+// ns consecutive slices s0.. of instance i (lane = row): every row's R
+// entries of a vector are loaded and stored as one row vector (16-byte
+// accesses where R allows), and the per-column partial sums of all ns slices
+// are accumulated per lane and reduced once (slice_col_sums) into the
+// chunk's first slice; the other slices of the chunk get zeros, so the
+// segmented reduction's sum over the instance's slices is unchanged.
 template <int OP, int R>
-__device__ __forceinline__ void b_vec_slice(const BatchDev& d, const BatchCols& cc, long long s, int i, unsigned act,
-                                            const double* bin, double* xout, double* x, double* r, double* z,
-                                            double* p, const double* q, float* r32, const float* z32, double* part0,
-                                            double* part1, int first) {
+__device__ __forceinline__ void b_vec_rows(const BatchDev& d, const BatchCols& cc, long long s0, int ns, int i,
+                                           unsigned act, const double* bin, double* xout, double* x, double* r,
+                                           double* z, double* p, const double* q, float* r32, const float* z32,
+                                           double* part0, double* part1, int first) {
+  constexpr bool sums = OP == kBScaleIn || OP == kBUpdXR || OP == kBUpdXR32 || OP == kBFrom32 || OP == kBDots32 ||
+                        OP == kBZtoP || OP == kBDeg0;
+  constexpr bool two = OP == kBFrom32 || OP == kBDots32 || OP == kBZtoP || OP == kBDeg0;
   const int lane = threadIdx.x & 31;
   const int g0 = d.cbase[i];
-  const long long row = d.s_row0[s] + lane;
-  const bool in = row < d.n[i];
-  const double wr = in ? d.w[d.woff[i] + row] : 1.0;
-  const long long e0 = d.voff[i] + row * R;
   double p0[R], p1[R];
+  double al[R], be[R];
+  bool ok[R];
 #pragma unroll
   for (int rr = 0; rr < R; ++rr) {
     p0[rr] = 0.0;
     p1[rr] = 0.0;
-    const int g = g0 + rr;
-    const long long e = e0 + rr;
     const bool a = (OP == kBScaleIn || OP == kBScaleOut) || ((act >> rr) & 1u);
-    if (!a) continue;
+    ok[rr] = a;
+    al[rr] = 0.0;
+    be[rr] = 0.0;
+    if (OP == kBUpdXR || OP == kBUpdXR32) {
+      const double pq = cc.pq[g0 + rr];
+      ok[rr] = a && pq > 0.0 && isfinite(pq);
+      al[rr] = cc.al[g0 + rr];  // (r, z) / (p, q), formed by the reduction
+    }
+    if ((OP == kBUpdP || OP == kBUpdP32) && !first) be[rr] = cc.be[g0 + rr];
+  }
+  for (int j = 0; j < ns; ++j) {
+    const long long s = s0 + j;
+    const long long row = d.s_row0[s] + lane;
+    const bool in = row < d.n[i];
+    const long long e0 = d.voff[i] + row * R;
     if (OP == kBScaleIn) {
-      const double v = in ? wr * bin[d.uoff[i] + row * R + rr] : 0.0;
-      r[e] = v;
-      x[e] = 0.0;
-      p0[rr] = v * v;
+      const double wr = in ? d.w[d.woff[i] + row] : 1.0;
+      RowVec<double, R> rv, xv;
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        const double v = in ? wr * bin[d.uoff[i] + row * R + rr] : 0.0;
+        rv.v[rr] = v;
+        xv.v[rr] = 0.0;
+        p0[rr] += v * v;
+      }
+      rv.store(r + e0);
+      xv.store(x + e0);
     } else if (OP == kBScaleOut) {
-      if (in) xout[d.uoff[i] + row * R + rr] = wr * x[e];
-    } else if (OP == kBUpdXR) {
-      const double pq = cc.pq[g];
-      if (pq > 0.0 && isfinite(pq)) {
-        const double al = cc.rz[g] / pq;
-        x[e] += al * p[e];
-        const double rv = r[e] - al * q[e];
-        r[e] = rv;
-        p0[rr] = rv * rv;
+      if (in) {
+        const double wr = d.w[d.woff[i] + row];
+        RowVec<double, R> xv;
+        xv.load_rw(x + e0);
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) xout[d.uoff[i] + row * R + rr] = wr * xv.v[rr];
+      }
+    } else if (OP == kBUpdXR || OP == kBUpdXR32) {
+      RowVec<double, R> xv, pv, rv, qv;
+      xv.load_rw(x + e0);
+      pv.load_rw(p + e0);
+      rv.load_rw(r + e0);
+      qv.load_rw(q + e0);
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        if (!ok[rr]) continue;
+        xv.v[rr] = fma(al[rr], pv.v[rr], xv.v[rr]);
+        rv.v[rr] = fma(-al[rr], qv.v[rr], rv.v[rr]);
+        if (in) p0[rr] = fma(rv.v[rr], rv.v[rr], p0[rr]);
+      }
+      xv.store(x + e0);
+      rv.store(r + e0);
+      if (OP == kBUpdXR32) {
+        RowVec<float, R> r3;
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) r3.v[rr] = (float)rv.v[rr];
+        r3.store(r32 + e0);
       }
     } else if (OP == kBTo32) {
-      r32[e] = (float)r[e];
-    } else if (OP == kBFrom32 || OP == kBDeg0) {
-      const double zv = OP == kBFrom32 ? (double)z32[e] : r[e] / d.theta_bar[g];
-      z[e] = zv;
-      p0[rr] = r[e] * zv;
-      p1[rr] = q[e] * zv;
-    } else if (OP == kBUpdP) {
-      double beta = 0.0;
-      if (!first) beta = cc.flexible ? -cc.zq[g] / cc.pq[g] : cc.rz_new[g] / cc.rz[g];
-      p[e] = z[e] + beta * p[e];
-    } else if (OP == kBZtoP) {
-      p0[rr] = r[e] * z[e];
-      p1[rr] = q[e] * z[e];
+      RowVec<double, R> rv;
+      rv.load_rw(r + e0);
+      RowVec<float, R> r3;
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) r3.v[rr] = (float)rv.v[rr];
+      r3.store(r32 + e0);
+    } else if (OP == kBFrom32 || OP == kBDots32 || OP == kBZtoP || OP == kBDeg0) {
+      RowVec<double, R> rv, qv, zv;
+      rv.load_rw(r + e0);
+      qv.load_rw(q + e0);
+      if (OP == kBFrom32 || OP == kBDots32) {
+        RowVec<float, R> z3;
+        z3.load_rw(z32 + e0);
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) zv.v[rr] = (double)z3.v[rr];
+      } else if (OP == kBZtoP) {
+        zv.load_rw(z + e0);
+      } else {
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) zv.v[rr] = rv.v[rr] / d.theta_bar[g0 + rr];
+      }
+      if (OP == kBFrom32 || OP == kBDeg0) zv.store(z + e0);
+      if (in) {
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+          if (!ok[rr]) continue;
+          p0[rr] = fma(rv.v[rr], zv.v[rr], p0[rr]);
+          p1[rr] = fma(qv.v[rr], zv.v[rr], p1[rr]);
+        }
+      }
+    } else if (OP == kBUpdP || OP == kBUpdP32) {
+      RowVec<double, R> pv, zv;
+      pv.load_rw(p + e0);
+      if (OP == kBUpdP32) {
+        RowVec<float, R> z3;
+        z3.load_rw(z32 + e0);
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) zv.v[rr] = (double)z3.v[rr];
+      } else {
+        zv.load_rw(z + e0);
+      }
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr)
+        if (ok[rr]) pv.v[rr] = fma(be[rr], pv.v[rr], zv.v[rr]);
+      pv.store(p + e0);
     }
   }
-  if (OP == kBScaleIn || OP == kBUpdXR || OP == kBFrom32 || OP == kBZtoP || OP == kBDeg0) {
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-      const double a0 = warp_sum(in ? p0[rr] : 0.0);
-      const double a1 = (OP == kBFrom32 || OP == kBZtoP || OP == kBDeg0) ? warp_sum(in ? p1[rr] : 0.0) : 0.0;
-      if (lane == 0) {
-        part0[s * kBR + rr] = a0;
-        if (part1) part1[s * kBR + rr] = a1;
+  if (sums) {
+    slice_col_sums<R>(p0, part0 + s0 * kBR, lane);
+    if (two && part1) slice_col_sums<R>(p1, part1 + s0 * kBR, lane);
+    if (lane < R) {
+      for (int j = 1; j < ns; ++j) {
+        part0[(s0 + j) * kBR + lane] = 0.0;
+        if (two && part1) part1[(s0 + j) * kBR + lane] = 0.0;
       }
     }
   }
 }
 
+// Work items of kBChunk slices; an item that spans instances (or is short)
+// goes slice by slice.
 template <int OP>
 __global__ void __launch_bounds__(kBlock) b_vec_kernel(BatchDev d, BatchCols cc, const double* __restrict__ bin,
                                                        double* __restrict__ xout, double* x, double* r, double* z,
                                                        double* p, const double* q, float* r32, const float* z32,
                                                        double* __restrict__ part0, double* __restrict__ part1,
                                                        int first) {
-  for (long long s = bgw(); s < d.nslices; s += bnw()) {
-    const int i = d.s_inst[s];
-    const int R = d.R[i];
-    const unsigned act = (OP == kBScaleIn || OP == kBScaleOut) ? 0xffu : active_mask(cc.done, d.cbase[i], R);
-    if (!act) continue;
-#define PP_BV(RR)                                                                                             \
-  b_vec_slice<OP, RR>(d, cc, s, i, act, bin, xout, x, r, z, p, q, r32, z32, part0, part1, first); \
+  const long long nchunks = (d.nslices + kBChunk - 1) / kBChunk;
+  for (long long c = bgw(); c < nchunks; c += bnw()) {
+    const long long c0 = c * kBChunk;
+    const long long c1 = c0 + kBChunk <= d.nslices ? c0 + kBChunk : d.nslices;
+    const bool whole = c1 - c0 == kBChunk && d.s_inst[c0] == d.s_inst[c1 - 1];
+    for (long long s = c0; s < c1; s += whole ? kBChunk : 1) {
+      const int ns = whole ? kBChunk : 1;
+      const int i = d.s_inst[s];
+      const int R = d.R[i];
+      const unsigned act = (OP == kBScaleIn || OP == kBScaleOut) ? 0xffu : active_mask(cc.done, d.cbase[i], R);
+      if (!act) continue;
+#define PP_BV(RR)                                                                                          \
+  b_vec_rows<OP, RR>(d, cc, s, ns, i, act, bin, xout, x, r, z, p, q, r32, z32, part0, part1, first); \
   break;
-    switch (R) {
-      case 1: PP_BV(1)
-      case 2: PP_BV(2)
-      case 3: PP_BV(3)
-      case 4: PP_BV(4)
-      case 5: PP_BV(5)
-      case 6: PP_BV(6)
-      case 7: PP_BV(7)
-      default: PP_BV(8)
-    }
+      switch (R) {
+        case 1: PP_BV(1)
+        case 2: PP_BV(2)
+        case 3: PP_BV(3)
+        case 4: PP_BV(4)
+        case 5: PP_BV(5)
+        case 6: PP_BV(6)
+        case 7: PP_BV(7)
+        default: PP_BV(8)
+      }
 #undef PP_BV
+    }
   }
 }
 
@@ -756,6 +923,7 @@ __global__ void __launch_bounds__(kBlock) b_reduce_kernel(BatchDev d, BatchCols 
       } else if (OP == kRedPQ) {
         cc.rz[g] = cc.rz_new[g];
         cc.pq[g] = v[0];
+        cc.al[g] = (v[0] > 0.0 && isfinite(v[0])) ? cc.rz[g] / v[0] : 0.0;
         if (!(v[0] > 0.0)) {
           cc.status[g] = isfinite(v[0]) ? -2 : -3;
           cc.done[g] = 1;
@@ -784,6 +952,8 @@ __global__ void __launch_bounds__(kBlock) b_reduce_kernel(BatchDev d, BatchCols 
       } else if (OP == kRedRZ) {
         cc.rz_new[g] = v[0];
         cc.zq[g] = v[1];
+        // beta of the next direction update (unused by the first one)
+        cc.be[g] = cc.flexible ? -v[1] / cc.pq[g] : v[0] / cc.rz[g];
         if (!(v[0] > 0.0)) {
           cc.status[g] = isfinite(v[0]) ? -2 : -3;
           cc.done[g] = 1;
@@ -1243,6 +1413,8 @@ size_t layout_batch(pp_ctx* c, pp_batch_state* B, const BPlan& P, void* base) {
   cc.rr = M.take<double>(P.ncols);
   cc.bb = M.take<double>(P.ncols);
   cc.rtol2 = M.take<double>(P.ncols);
+  cc.al = M.take<double>(P.ncols);
+  cc.be = M.take<double>(P.ncols);
   cc.done = M.take<int>(P.ncols);
   cc.iter = M.take<int>(P.ncols);
   cc.status = M.take<int>(P.ncols);
@@ -1293,7 +1465,7 @@ cudaError_t b_reduce(pp_batch_state* B, int op, double* lan_out, int j, cudaStre
 
 template <int OP>
 cudaError_t b_vec(pp_batch_state* B, const double* bin, double* xout, int first, cudaStream_t s) {
-  b_vec_kernel<OP><<<grid_b(B->d.nslices), kBlock, 0, s>>>(B->d, B->c, bin, xout, B->x, B->r, B->z, B->p, B->q,
+  b_vec_kernel<OP><<<grid_b((B->d.nslices + kBChunk - 1) / kBChunk), kBlock, 0, s>>>(B->d, B->c, bin, xout, B->x, B->r, B->z, B->p, B->q,
                                                           B->r32, B->z32, B->part0, B->part1, first);
   return cudaGetLastError();
 }
@@ -1316,21 +1488,43 @@ cudaError_t b_cheb_steps(pp_batch_state* B, cudaStream_t s) {
       if constexpr (std::is_same<TX, float>::value) {
         if (d.nzitems > 0) {
           tz = true;
-          auto zl = [&](auto lo, auto hi, int c) {
+          // the classes touch disjoint instances: the largest runs on s, the
+          // others on the side streams, so a small class does not leave the
+          // GPU part-empty for a launch of its own
+          int nonempty = 0;
+          for (int c = 0; c < 3; ++c) nonempty += B->zclass[c + 1] > B->zclass[c] ? 1 : 0;
+          const bool fork = nonempty > 1 && B->zs[0] && B->zs[1];
+          cudaError_t fe = cudaSuccess;
+          if (fork) {
+            fe = cudaEventRecord(B->zfork, s);
+            for (int q = 0; q < 2 && fe == cudaSuccess; ++q) fe = cudaStreamWaitEvent(B->zs[q], B->zfork, 0);
+            if (fe != cudaSuccess) return fe;
+          }
+          auto zl = [&](auto lo, auto hi, int c, cudaStream_t ls) {
             constexpr int RLO = decltype(lo)::value, RHI = decltype(hi)::value;
             const long long i0 = B->zclass[c], cnt = B->zclass[c + 1] - i0;
             if (cnt <= 0) return;
             const unsigned gz = (unsigned)cnt;
             if (mode == kCheb1)
-              b_cheb_z_kernel<RLO, RHI, kCheb1><<<gz, kBlock, 0, s>>>(d, i0, v, xin, xo, rin, yout, B->c.done, cj);
+              b_cheb_z_kernel<RLO, RHI, kCheb1><<<gz, kBlock, 0, ls>>>(d, i0, v, xin, xo, rin, yout, B->c.done, cj);
             else if (mode == kCheb2)
-              b_cheb_z_kernel<RLO, RHI, kCheb2><<<gz, kBlock, 0, s>>>(d, i0, v, xin, xo, rin, yout, B->c.done, cj);
+              b_cheb_z_kernel<RLO, RHI, kCheb2><<<gz, kBlock, 0, ls>>>(d, i0, v, xin, xo, rin, yout, B->c.done, cj);
             else
-              b_cheb_z_kernel<RLO, RHI, kChebK><<<gz, kBlock, 0, s>>>(d, i0, v, xin, xo, rin, yout, B->c.done, cj);
+              b_cheb_z_kernel<RLO, RHI, kChebK><<<gz, kBlock, 0, ls>>>(d, i0, v, xin, xo, rin, yout, B->c.done, cj);
           };
-          zl(std::integral_constant<int, kBZClass[0]>(), std::integral_constant<int, kBZClass[1] - 1>(), 0);
-          zl(std::integral_constant<int, kBZClass[1]>(), std::integral_constant<int, kBZClass[2] - 1>(), 1);
-          zl(std::integral_constant<int, kBZClass[2]>(), std::integral_constant<int, kBZClass[3] - 1>(), 2);
+          zl(std::integral_constant<int, kBZClass[2]>(), std::integral_constant<int, kBZClass[3] - 1>(), 2, s);
+          zl(std::integral_constant<int, kBZClass[1]>(), std::integral_constant<int, kBZClass[2] - 1>(), 1,
+             fork ? B->zs[0] : s);
+          zl(std::integral_constant<int, kBZClass[0]>(), std::integral_constant<int, kBZClass[1] - 1>(), 0,
+             fork ? B->zs[1] : s);
+          if (fork) {
+            // join before anything else reads the step's output
+            for (int q = 0; q < 2 && fe == cudaSuccess; ++q) {
+              fe = cudaEventRecord(B->zjoin[q], B->zs[q]);
+              if (fe == cudaSuccess) fe = cudaStreamWaitEvent(s, B->zjoin[q], 0);
+            }
+            if (fe != cudaSuccess) return fe;
+          }
           if (B->nz_inst == d.nb) return cudaGetLastError();  // every instance plane-marched
         }
       }
@@ -1377,7 +1571,9 @@ cudaError_t b_cheb_steps(pp_batch_state* B, cudaStream_t s) {
 }
 
 // z = p_k(A_hat) r for every active column, then (r,z), (q,z) -> rz_new, zq.
-cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
+// FP32 preconditioner: z stays in z32 (the p update reads it there); r32 is
+// written here unless the r update already wrote it (r32_ready).
+cudaError_t b_precond(pp_batch_state* B, cudaStream_t s, bool r32_ready) {
   const int k = B->d.k;
   cudaError_t e = cudaSuccess;
   if (k == 0) {
@@ -1385,9 +1581,9 @@ cudaError_t b_precond(pp_batch_state* B, cudaStream_t s) {
     return e == cudaSuccess ? b_reduce(B, kRedRZ, nullptr, 0, s) : e;
   }
   if (B->apply_prec == PP_PREC_F32) {
-    e = b_vec<kBTo32>(B, nullptr, nullptr, 0, s);
+    if (!r32_ready) e = b_vec<kBTo32>(B, nullptr, nullptr, 0, s);
     if (e == cudaSuccess) e = b_cheb_steps(B, s);
-    if (e == cudaSuccess) e = b_vec<kBFrom32>(B, nullptr, nullptr, 0, s);
+    if (e == cudaSuccess) e = b_vec<kBDots32>(B, nullptr, nullptr, 0, s);
   } else {
     e = b_cheb_steps(B, s);
     if (e == cudaSuccess) e = b_vec<kBZtoP>(B, nullptr, nullptr, 0, s);
@@ -1399,11 +1595,12 @@ cudaError_t b_iteration(pp_batch_state* B, cudaStream_t s) {
   const BatchDev& d = B->d;
   b_spmv64_kernel<kSpmv><<<grid_b(d.nslices), kBlock, 0, s>>>(d, B->p, nullptr, B->q, B->c.done, nullptr, 0, B->part0);
   cudaError_t e = cudaGetLastError();
+  const bool lp = B->apply_prec == PP_PREC_F32 && B->d.k > 0;
   if (e == cudaSuccess) e = b_reduce(B, kRedPQ, nullptr, 0, s);
-  if (e == cudaSuccess) e = b_vec<kBUpdXR>(B, nullptr, nullptr, 0, s);
+  if (e == cudaSuccess) e = lp ? b_vec<kBUpdXR32>(B, nullptr, nullptr, 0, s) : b_vec<kBUpdXR>(B, nullptr, nullptr, 0, s);
   if (e == cudaSuccess) e = b_reduce(B, kRedRR, nullptr, 0, s);
-  if (e == cudaSuccess) e = b_precond(B, s);
-  if (e == cudaSuccess) e = b_vec<kBUpdP>(B, nullptr, nullptr, 0, s);
+  if (e == cudaSuccess) e = b_precond(B, s, lp);
+  if (e == cudaSuccess) e = lp ? b_vec<kBUpdP32>(B, nullptr, nullptr, 0, s) : b_vec<kBUpdP>(B, nullptr, nullptr, 0, s);
   return e;
 }
 
@@ -1503,6 +1700,11 @@ void batch_free(pp_batch_state* B) {
   if (!B) return;
   if (B->graph) cudaGraphExecDestroy(B->graph);
   if (B->cap) cudaStreamDestroy(B->cap);
+  for (int q = 0; q < 2; ++q) {
+    if (B->zs[q]) cudaStreamDestroy(B->zs[q]);
+    if (B->zjoin[q]) cudaEventDestroy(B->zjoin[q]);
+  }
+  if (B->zfork) cudaEventDestroy(B->zfork);
   delete B;
 }
 
@@ -1602,6 +1804,14 @@ extern "C" int pp_batch_setup(pp_ctx** out, const pp_batch_item* items, int coun
   B->rows_pad = P.rows_pad;
   B->nz_inst = B->d.nzitems > 0 ? P.nz_inst : 0;
   for (int q = 0; q < 4 && q < (int)P.zclass.size(); ++q) B->zclass[q] = P.zclass[q];
+  if (B->d.nzitems > 0) {
+    cudaError_t se = cudaEventCreateWithFlags(&B->zfork, cudaEventDisableTiming);
+    for (int q = 0; q < 2 && se == cudaSuccess; ++q) {
+      se = cudaStreamCreateWithFlags(&B->zs[q], cudaStreamNonBlocking);
+      if (se == cudaSuccess) se = cudaEventCreateWithFlags(&B->zjoin[q], cudaEventDisableTiming);
+    }
+    if (se != cudaSuccess) return bail(cuda_fail(c, se, "pp_batch_setup: side streams"));
+  }
   BatchDev& d = B->d;
   B->c.maxit = opt->maxit;
   B->c.flexible = opt->flexible;
@@ -1805,14 +2015,23 @@ extern "C" int pp_batch_solve(pp_ctx* c, const double* b, double* x, int* iters,
   if (e == cudaSuccess) e = cudaMemsetAsync(B->c.done, 0, sizeof(int) * nc, s);
   if (e == cudaSuccess) e = b_vec<kBScaleIn>(B, b, nullptr, 0, s);
   if (e == cudaSuccess) e = b_reduce(B, kRedBB, nullptr, 0, s);
-  if (e == cudaSuccess) e = b_precond(B, s);
-  if (e == cudaSuccess) e = b_vec<kBUpdP>(B, nullptr, nullptr, 1, s);
+  const bool lp = B->apply_prec == PP_PREC_F32 && d.k > 0;
+  if (e == cudaSuccess) e = b_precond(B, s, false);
+  if (e == cudaSuccess) e = lp ? b_vec<kBUpdP32>(B, nullptr, nullptr, 1, s) : b_vec<kBUpdP>(B, nullptr, nullptr, 1, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pp_batch_solve start");
+  // kernel launches: every degree step launches one kernel per non-empty
+  // plane-marching class plus the slice kernel when other instances remain
+  long long per_step = 1;
+  if (d.dia && B->apply_prec == PP_PREC_F32 && d.nzitems > 0) {
+    per_step = B->nz_inst < d.nb ? 1 : 0;
+    for (int q = 0; q < 3; ++q) per_step += B->zclass[q + 1] > B->zclass[q] ? 1 : 0;
+  }
   long long launches = 0;
   const long long k = c->opt.k;
-  const long long pre = k == 0 ? 2 : (B->apply_prec == PP_PREC_F32 ? k + 3 : k + 2);
+  // preconditioner: k steps, the dots (and the r32 copy at the start), the reduction
+  const long long pre = k == 0 ? 2 : k * per_step + 2;
   const long long per_it = 5 + pre;
-  launches += 3 + pre + 1;
+  launches += 3 + pre + (lp ? 1 : 0) + 1;
   for (int guard = 0;; ++guard) {
     if (graphs) {
       e = cudaGraphLaunch(B->graph, s);
