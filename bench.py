@@ -53,6 +53,7 @@ WORKLOADS = {
     "dfn200_f32": dict(dfn=True, seed=2, k=15, lanczos=30, prec="f32", flexible=1),
     # its first 40 fractures with the closed-form blocks: a small case of the S_u kernels for profiler captures
     "dfn40": dict(dfn=True, seed=2, n_f=40, k=3, lanczos=30, prec="f64"),
+    "dfn40_f32": dict(dfn=True, seed=2, n_f=40, k=15, lanczos=30, prec="f32", flexible=1),
     # the same network with general fracture blocks (P1 stiffness on jittered triangulations,
     # lognormal coefficients): A^{-1} from banded Cholesky factors built on the GPU
     "dfn200_p1": dict(dfn=True, seed=2, k=3, lanczos=30, prec="f64", general="p1"),
@@ -373,7 +374,7 @@ def batch_step_kernel(fmt: str, prec: str) -> str:
     return "b_cheb_z_kernel (plane marching)" if prec == "f32" else "b_cheb_dia3_kernel"
 
 
-def run_batch(args, w, specs, k, dev, world, rank):
+def run_batch(args, w, specs, k, dev, world, rank, emit=True):
     """Config-5 shape: many uneven instances with several RHS each, solved by
     the batched solver (FP32 p_k, FP64 flexible CG, CUDA graphs) in the
     layout pp_batch_autotune picks and, for comparison, one column at a
@@ -490,7 +491,29 @@ def run_batch(args, w, specs, k, dev, world, rank):
                             "traffic": None, "peak_source": peak_src, "avg_launch_us": round(step_us, 2),
                             "algorithmic_bytes_per_launch": int(bytes_step)},
                "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
-        print(json.dumps(out), flush=True)
+        if emit:
+            print(json.dumps(out), flush=True)
+        return out
+    return None
+
+
+def batch_summary(args, dev):
+    """The batched workload (64 uneven instances, FP32 p_k, MLP intervals,
+    one graph-replayed solve) measured inside the default line: its time to
+    rtol 1e-8 against the plain FP64 solver run on every column alone, the
+    interval arms and the step roofline.  One timed solve after 3 warm-ups."""
+    w = dict(WORKLOADS["batched64"])
+    specs, _ = build_problem(w)
+    sub = argparse.Namespace(**{**vars(args), "steps": 1, "warmup": 3})
+    out = run_batch(sub, w, specs, w["k"], dev, 1, 0, emit=False)
+    keys = ("value", "sequential_f64_s", "speedup_vs_sequential_f64", "max_rel_diff_vs_f64", "iterations_max",
+            "iterations_f64_max", "interval_arms", "roofline")
+    res = {k2: out[k2] for k2 in keys}
+    res["time_s"] = res.pop("value")
+    res["config"] = {k2: out["config"][k2] for k2 in ("instances", "rows", "columns", "k", "apply", "outer",
+                                                       "interval", "layout", "autotune", "sequential_baseline")}
+    res["steps_timed"] = 1
+    return res
 
 
 def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
@@ -587,7 +610,29 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
                "trace_block_bytes": m_bytes, "roofline": roof32 if w["prec"] == "f32" else roof,
                "operator_roofline": roof if w["prec"] == "f32" else None,
                "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
-        print(json.dumps(out), flush=True)
+        if emit:
+            print(json.dumps(out), flush=True)
+        return out
+    return None
+
+
+def batch_summary(args, dev):
+    """The batched workload (64 uneven instances, FP32 p_k, MLP intervals,
+    one graph-replayed solve) measured inside the default line: its time to
+    rtol 1e-8 against the plain FP64 solver run on every column alone, the
+    interval arms and the step roofline.  One timed solve after 3 warm-ups."""
+    w = dict(WORKLOADS["batched64"])
+    specs, _ = build_problem(w)
+    sub = argparse.Namespace(**{**vars(args), "steps": 1, "warmup": 3})
+    out = run_batch(sub, w, specs, w["k"], dev, 1, 0, emit=False)
+    keys = ("value", "sequential_f64_s", "speedup_vs_sequential_f64", "max_rel_diff_vs_f64", "iterations_max",
+            "iterations_f64_max", "interval_arms", "roofline")
+    res = {k2: out[k2] for k2 in keys}
+    res["time_s"] = res.pop("value")
+    res["config"] = {k2: out["config"][k2] for k2 in ("instances", "rows", "columns", "k", "apply", "outer",
+                                                       "interval", "layout", "autotune", "sequential_baseline")}
+    res["steps_timed"] = 1
+    return res
 
 
 def main():
@@ -606,6 +651,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=0, help="PCG iterations per host check (default: per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave the batched workload's summary out of the default line")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32/BF16 and k = 80 comparison solves of the default workload")
     ap.add_argument("--k-sweep", default="", help="comma-separated degrees: time one solve per degree instead")
@@ -782,6 +829,11 @@ def main():
     variants = None
     if not args.no_variants and args.workload == "diffusion192":
         variants = run_variants(args, A, rp, ci, va, bt, opts, x_oracle, fp64_peak, ms / 1e3, dev)
+    batched = None
+    if not args.no_batch and args.workload == "diffusion192" and world == 1:
+        S.close()
+        del S
+        batched = batch_summary(args, dev)
 
     out = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -801,7 +853,7 @@ def main():
         "one_shot_s": round(one_shot, 4),
         "alpha_hat": info["alpha_hat"], "beta_hat": info["beta_hat"], "xi": info["xi"],
         "err_vs_oracle": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-        "north_star": variants,
+        "north_star": variants, "batched": batched,
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks,
     }
     print(json.dumps(out), flush=True)
