@@ -610,29 +610,7 @@ def run_dfn(args, w, net, S, bt, k, dev, world, rank, dist):
                "trace_block_bytes": m_bytes, "roofline": roof32 if w["prec"] == "f32" else roof,
                "operator_roofline": roof if w["prec"] == "f32" else None,
                "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
-        if emit:
-            print(json.dumps(out), flush=True)
-        return out
-    return None
-
-
-def batch_summary(args, dev):
-    """The batched workload (64 uneven instances, FP32 p_k, MLP intervals,
-    one graph-replayed solve) measured inside the default line: its time to
-    rtol 1e-8 against the plain FP64 solver run on every column alone, the
-    interval arms and the step roofline.  One timed solve after 3 warm-ups."""
-    w = dict(WORKLOADS["batched64"])
-    specs, _ = build_problem(w)
-    sub = argparse.Namespace(**{**vars(args), "steps": 1, "warmup": 3})
-    out = run_batch(sub, w, specs, w["k"], dev, 1, 0, emit=False)
-    keys = ("value", "sequential_f64_s", "speedup_vs_sequential_f64", "max_rel_diff_vs_f64", "iterations_max",
-            "iterations_f64_max", "interval_arms", "roofline")
-    res = {k2: out[k2] for k2 in keys}
-    res["time_s"] = res.pop("value")
-    res["config"] = {k2: out["config"][k2] for k2 in ("instances", "rows", "columns", "k", "apply", "outer",
-                                                       "interval", "layout", "autotune", "sequential_baseline")}
-    res["steps_timed"] = 1
-    return res
+        print(json.dumps(out), flush=True)
 
 
 def main():
