@@ -298,7 +298,7 @@ struct MVec<float> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) m_apply_kernel(int n_T, const long long* __restrict__ toff,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 8) m_apply_kernel(int n_T, const long long* __restrict__ toff,
                                                          const long long* __restrict__ moff,
                                                          const int* __restrict__ tfrac, const T* __restrict__ M,
                                                          const T* __restrict__ x, T* __restrict__ y) {
@@ -320,6 +320,34 @@ __global__ void __launch_bounds__(kBlock) m_apply_kernel(int n_T, const long lon
       if (l == 0)
         for (int j = 0; j < head; ++j) acc0 = fma(__ldcs(row + j), __ldg(xf + j), acc0);
       int j = head + l * W;
+      if constexpr (sizeof(T) == 4) {
+        // FP32 (bound by load latency, not by the FMAs): four 16-byte loads
+        // in flight per lane per step
+        for (; j + 3 * kMG * W + W <= t; j += 4 * kMG * W) {
+          T m0[W], m1[W], m2[W], m3[W], x0[W], x1[W], x2[W], x3[W];
+          MVec<T>::ld(row + j, m0);
+          MVec<T>::ld(row + j + kMG * W, m1);
+          MVec<T>::ld(row + j + 2 * kMG * W, m2);
+          MVec<T>::ld(row + j + 3 * kMG * W, m3);
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            x0[u] = __ldg(xf + j + u);
+            x1[u] = __ldg(xf + j + kMG * W + u);
+            x2[u] = __ldg(xf + j + 2 * kMG * W + u);
+            x3[u] = __ldg(xf + j + 3 * kMG * W + u);
+          }
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            acc0 = fma(m0[u], x0[u], acc0);
+            acc1 = fma(m1[u], x1[u], acc1);
+          }
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            acc0 = fma(m2[u], x2[u], acc0);
+            acc1 = fma(m3[u], x3[u], acc1);
+          }
+        }
+      }
       // two 16-byte loads in flight per lane per step
       for (; j + kMG * W + W <= t; j += 2 * kMG * W) {
         T m0[W], m1[W];
