@@ -86,6 +86,17 @@ cudaError_t cheb_core(pp_ctx* c, const Scalars* skip, const void* rin, void* zou
 // p update and the plain x update.
 bool fuse_x_update(const pp_ctx* c) { return c->fcg_m == 0; }
 
+// Records a timing event on s; while s is being captured into a graph the
+// record becomes a node of the graph (an external event record), so every
+// replay records it and the per-iteration step times stay measurable.
+cudaError_t record_timing(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &st);
+  if (e != cudaSuccess) return e;
+  return st == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, s);
+}
+
 // z = p_k(A_hat) r on the internal FP64 vectors r, z, with (r, z) -> rz_new
 // and, for flexible CG, (q, z) -> zq.  With a low-rank correction in use
 // (Section 3.1) c = G^{-1} V^T r is formed first and z += V c, fused with
@@ -105,26 +116,26 @@ cudaError_t precond(pp_ctx* c, const Scalars* skip, cudaStream_t s, cudaEvent_t 
   cudaError_t e = lr ? lowrank_coefs(c, skip, c->r, s) : cudaSuccess;
   if (e != cudaSuccess) return e;
   if (c->opt.poly == PP_POLY_NEWTON) {
-    if (ev0) e = cudaEventRecord(ev0, s);
+    if (ev0) e = record_timing(ev0, s);
     if (e == cudaSuccess) e = newton_apply(c, skip, c->r, c->z, s);
-    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess && ev1) e = record_timing(ev1, s);
     if (e == cudaSuccess && !nodot) e = newton_dots(c, skip, c->z, c->r, qd, rz, &sc->zq, s);
   } else if (c->opt.k == 0) {
-    if (ev0) e = cudaEventRecord(ev0, s);
+    if (ev0) e = record_timing(ev0, s);
     if (e == cudaSuccess)
       e = vec_scale_dot(L, c->n, skip, c->r, c->z, kF64, 1.0 / c->theta_bar, c->r, qd, rz, &sc->zq,
                         &sc->counters[kCntVec]);
-    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess && ev1) e = record_timing(ev1, s);
   } else if (!c->mixed) {
-    if (ev0) e = cudaEventRecord(ev0, s);
+    if (ev0) e = record_timing(ev0, s);
     if (e == cudaSuccess)
       e = cheb_core(c, skip, c->r, c->z, nd, rz, qd, &sc->zq, s);
-    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess && ev1) e = record_timing(ev1, s);
   } else {
     e = vec_convert(L, c->n, c->r, kF64, c->r32, kF32, skip);
-    if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, s);
+    if (e == cudaSuccess && ev0) e = record_timing(ev0, s);
     if (e == cudaSuccess) e = cheb_core(c, skip, c->r32, c->z32, 0, nullptr, nullptr, nullptr, s);
-    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess && ev1) e = record_timing(ev1, s);
     if (e == cudaSuccess)
       e = vec_from32_dot(L, c->n, skip, c->z32, c->z, c->r, qd, rz, &sc->zq, &sc->counters[kCntVec]);
   }
@@ -216,7 +227,11 @@ int build_graph(pp_ctx* c, int B) {
   e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
   cudaError_t e2 = cudaSuccess;
-  for (int b = 0; b < B && e2 == cudaSuccess; ++b) e2 = pcg_iteration(c, c->cap_stream, nullptr, nullptr, b);
+  // the first iteration of the block records its step-time events (made
+  // by ensure_events) through the graph's own nodes at every replay: one
+  // sample per block keeps the event nodes off the other iterations
+  for (int b = 0; b < B && e2 == cudaSuccess; ++b)
+    e2 = pcg_iteration(c, c->cap_stream, b == 0 ? c->events[2] : nullptr, b == 0 ? c->events[3] : nullptr, b);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(c->cap_stream, &g);
   if (e2 != cudaSuccess) {
@@ -461,7 +476,7 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
     if (e == cudaSuccess) e = op_step(c, false, p, nullptr, &sc->counters[kCntStep], s);
   }
   if (e == cudaSuccess) e = pcg_init(sc, c->opt.rtol, c->opt.maxit, c->opt.flexible, s);
-  if (e == cudaSuccess) e = precond(c, sc, s, graphs ? nullptr : ev_pair(B, 0), graphs ? nullptr : ev_pair(B, 1));
+  if (e == cudaSuccess) e = precond(c, sc, s, ev_pair(B, 0), ev_pair(B, 1));
   if (e == cudaSuccess)
     e = c->fcg_m ? fcg_update_p(c, 0, 0, 1, s) : vec_update_p(L, c->n, sc, c->z, c->p, 1);
   if (e != cudaSuccess) return cuda_fail(c, e, "pcg_solve start");
@@ -483,7 +498,7 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, &sc->done, sizeof(host), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "pcg_solve iteration");
-    if (!graphs) {
+    {  // step times of the iterations this block ran (a graph replay records its first one)
       float ms = 0.f;
       if (first_block && host[2] >= 1) {
         cudaEventElapsedTime(&ms, ev_pair(B, 0), ev_pair(B, 1));
@@ -492,6 +507,7 @@ extern "C" int pcg_solve(pp_ctx* c, const double* b, double* x, pp_stats* st, vo
       }
       int executed = host[2] - iter_before;
       int applied = executed - (host[0] ? 1 : 0);
+      if (graphs) applied = applied > 0 ? 1 : 0;  // the block's sampled first iteration
       for (int bi = 0; bi < applied; ++bi) {
         cudaEventElapsedTime(&ms, ev_pair(bi, 0), ev_pair(bi, 1));
         t_apply += ms;
