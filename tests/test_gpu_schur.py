@@ -108,6 +108,25 @@ def test_pcg_on_scaled_schur(pair, k):
     assert st["mvp"] == st["iterations"] * (k + 1)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_pcg_on_schur_with_graphs_matches_launches(pair, prec):
+    """Blocks of PCG iterations on S_hat replayed as CUDA graphs give the
+    launched-one-by-one solve exactly: the same kernels in the same order
+    (FP64 and the FP32 preconditioner inside FCG(1))."""
+    net, ref = pair
+    steps = min(10, net.n_u)
+    r = dev(ref.rhs(net.q))
+    out = []
+    for graphs in (0, 1):
+        S = P.SchurSolver(net, k=6, lanczos_steps=steps, rtol=1e-10, maxit=500, use_graphs=graphs, check_every=4,
+                          apply_prec=prec, flexible=1 if prec == "f32" else 0)
+        u, st = S.solve(r)
+        assert st["status"] == 0
+        out.append((to_np(u), st["iterations"]))
+    assert out[0][1] == out[1][1]
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+
+
 def test_polyprec_apply_on_schur(pair):
     """p_k(S_hat) by Algorithm 2 with the composite operator."""
     net, ref = pair
