@@ -150,3 +150,25 @@ def test_mixed_plain_cg_also_converges_f32():
     S = P.Solver.from_host(A, k=10, rtol=1e-8, format="sell", apply_prec="f32")
     _, st = S.solve(torch.as_tensor(b, device="cuda"), allow=(0, 1, -2))
     assert st["status"] in (0, 1, -2)
+
+
+@pytest.mark.parametrize("fmt", ["dia", "sell"])
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_fcg_with_graphs_matches_launches_and_times_steps(prec, fmt):
+    """FCG(1) with the low-precision preconditioner: blocks of iterations
+    replayed as CUDA graphs give the launched solve bit for bit, and the
+    step-time events recorded by the graph's nodes give a positive time for
+    the degree steps."""
+    A = I.diffusion3d(20, 2.0, seed=4)
+    b = torch.as_tensor(I.rhs_normal(A.n, 5), device="cuda")
+    out = []
+    for graphs in (0, 1):
+        S = P.Solver.from_host(A, k=12, lanczos_steps=20, rtol=1e-8, apply_prec=prec, flexible=1, format=fmt,
+                               use_graphs=graphs, check_every=5)
+        x, st = S.solve(b)
+        assert st["status"] == 0
+        assert st["t_apply_ms"] > 0 and st["apply_launches"] > 0
+        out.append((to_np(x), st["iterations"]))
+        S.close()
+    assert out[0][1] == out[1][1]
+    np.testing.assert_array_equal(out[0][0], out[1][0])
