@@ -32,8 +32,9 @@ XIS = (1e-4, 1e-3, 1e-2, 5e-2)
 SETTINGS = [(a, b, x) for a in S_ALPHA for b in S_BETA for x in XIS]  # 32 settings, 4 items x 8 columns
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mlp_weights.npz")
 # the most frequent label of the sweep the shipped weights were trained on
-# (1292 of 2000 instances): the best single constant setting of that sweep
-FIXED_BEST = (0.3, 1.1, 1e-4)
+# (891 of 2000 instances, grids 12..64): the best single constant setting of
+# that sweep
+FIXED_BEST = (0.1, 1.1, 1e-4)
 
 
 # Feature columns the network sees.  Column 0 (log10 n) is left out, so the
@@ -57,7 +58,7 @@ def auto_xi(alpha, beta):
     return float(min(max(10.0 * alpha / beta, 1e-6), 1e-2))
 
 
-def training_specs(count: int, seed: int = 5, nmin: int = 12, nmax: int = 40):
+def training_specs(count: int, seed: int = 5, nmin: int = 12, nmax: int = 64):
     specs = I.batch_specs(count, seed=seed, nmin=nmin, nmax=nmax, rmin=8, rmax=8)
     return specs
 
@@ -222,6 +223,8 @@ def evaluate(specs, model: Model | None, k: int = 20, device="cuda", apply_prec=
 def main():
     ap = argparse.ArgumentParser(description="sweep, train and evaluate the interval/xi predictor")
     ap.add_argument("--count", type=int, default=2000)
+    ap.add_argument("--nmin", type=int, default=12, help="smallest training grid side")
+    ap.add_argument("--nmax", type=int, default=64, help="largest training grid side")
     ap.add_argument("--eval-count", type=int, default=64)
     ap.add_argument("--k", type=int, default=20)
     ap.add_argument("--steps", type=int, default=2000)
@@ -229,7 +232,7 @@ def main():
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
     t0 = time.perf_counter()
-    specs = training_specs(args.count)
+    specs = training_specs(args.count, nmin=args.nmin, nmax=args.nmax)
     feats, iters, base = sweep(specs, k=args.k)
     y, best = labels(iters)
     t_sweep = time.perf_counter() - t0
@@ -238,7 +241,7 @@ def main():
     ev_specs = I.batch_specs(args.eval_count, seed=4)
     fixed = most_frequent_setting(iters)
     ev = evaluate(ev_specs, model, k=args.k, apply_prec="f32", fixed=fixed)
-    rep = {"instances": len(specs), "sweep_s": t_sweep, "loss_first": losses[0], "loss_last": losses[-1],
+    rep = {"instances": len(specs), "sizes": [args.nmin, args.nmax], "sweep_s": t_sweep, "loss_first": losses[0], "loss_last": losses[-1],
            "label_histogram": np.bincount(best, minlength=len(SETTINGS)).tolist(),
            "fallback_iters_mean_train": float(iters[:, SETTINGS.index((1.0, 1.0, 1e-3))].mean()),
            "best_iters_mean_train": float(iters.min(axis=1).mean()), "fixed_setting": fixed,
