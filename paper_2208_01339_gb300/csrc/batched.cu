@@ -437,6 +437,25 @@ __device__ __forceinline__ T ld_pol(const T* p, uint64_t pol) {
   }
 }
 
+// R consecutive floats of a row vector with an L2 cache hint, as 16- or
+// 8-byte accesses where the row allows (the RowVec rule: a multiple of 16
+// bytes per row from a 32-element aligned base; 8 bytes for R = 2).
+template <int R>
+__device__ __forceinline__ void ld_pol_row(const float* p, uint64_t pol, float (&o)[R]) {
+  if constexpr (R % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q)
+      asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+          : "=f"(o[4 * q]), "=f"(o[4 * q + 1]), "=f"(o[4 * q + 2]), "=f"(o[4 * q + 3])
+          : "l"(p + 4 * q), "l"(pol));
+  } else if constexpr (R == 2) {
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(o[0]), "=f"(o[1]) : "l"(p), "l"(pol));
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) o[r] = ld_pol<float>(p + r, pol);
+  }
+}
+
 template <typename TV, typename TX, int R, int MODE>
 __device__ __forceinline__ void b_cheb_dia3_chunk(const BatchDev& d, int i, long long row0, const TV* val,
                                                   const TX* x, const TX* xold, const TX* rin, TX* y,
@@ -603,8 +622,7 @@ __device__ __forceinline__ void b_z_item(const BatchDev& d, const BZItem it, con
     xn.load(X + clip(row + Nx) * R);
     const long long e0 = vo + row * R;
     float rs[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) rs[r] = ld_pol<float>(rin + e0 + r, pol_last);
+    ld_pol_row<R>(rin + e0, pol_last, rs);
     RowVec<float, R> xo;
     if (MODE == kChebK) xo.load(xold + e0);
 #pragma unroll
